@@ -1,0 +1,193 @@
+/*
+ * pcv.h -- C ABI of the GB300 (sm_103a) parallel cross-validation library.
+ *
+ * The library evaluates the parallel cross-validation loss of Gerber & Nychka,
+ * "Parallel cross-validation: a scalable fitting method for Gaussian process
+ * models" (arXiv 1912.13132), for batches of covariance-parameter
+ * configurations, and kriging predictions at new locations.
+ *
+ * Model (Sec. 2.1, Eq. 1; exponential covariance of Sec. 3):
+ *     y ~ N(0, sigma2 * Sigma(rho) + tau2 * I),   Sigma_ab = exp(-||s_a - s_b|| / rho).
+ * The paper names the nugget variance "tau"; this ABI calls it tau2.  Kriging
+ * depends only on lambda = tau2 / sigma2 and rho (Eq. 3 and the remark after it).
+ *
+ * Subsets (Sec. 2.3, Eq. 5-6; Fig. 1): the domain D is cut into disjoint
+ * rectangles D_1..D_N ("cores").  Subset i predicts the VALID points of D_i from
+ * the TRAIN points of D_i and of its shell of width delta.  The loss of one
+ * configuration is Eq. 6:   CV~ = sum_i CV(y~_T^i, y_V^i, zeta),
+ * CV(.) being the sum of squared prediction errors (SSPE, Eq. 4).  Algorithm 1
+ * (parallel evaluation) maps to one persistent GPU launch over all
+ * (subset, configuration) tasks followed by a fixed-order device sum.
+ *
+ * Readings of points the paper leaves open (fixed by this ABI):
+ *   - cores are half-open [x0, x1) x [y0, y1), closed on D's upper edges;
+ *   - the shell is the closed L-infinity band: the training window of subset i
+ *     is [x0 - delta, x1 + delta] x [y0 - delta, y1 + delta];
+ *   - only TRAIN points enter training sets; VALID points are predicted only by
+ *     the subset whose core holds them; IGNORE points are never used;
+ *   - regular layouts cut [X0, X1] at X0 + ((X1 - X0) * c) / nx, evaluated in
+ *     FP64 in that order (c = 1..nx-1), subset index i = cy * nx + cx;
+ *   - subsets without validation data are skipped (Sec. 4.3.1): their local SSPE
+ *     is 0 and they are not factorised;
+ *   - membership lists are in ascending input-index order.
+ *
+ * Conventions:
+ *   - every function returns a pcv_status; no exceptions cross the ABI;
+ *     pcv_last_error() gives a message for the calling thread's last failure;
+ *   - host buffers belong to the caller; the library copies what it needs and
+ *     keeps no caller pointer after a call returns;
+ *   - device buffers passed to *_device functions belong to the caller and must
+ *     stay valid until the work queued on `stream` has finished;
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream);
+ *   - one pcv_ctx must not be used by two threads at the same time.
+ */
+#ifndef PCV_H
+#define PCV_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pcv_ctx pcv_ctx;
+typedef struct pcv_plan pcv_plan;
+
+typedef enum {
+    PCV_OK = 0,
+    PCV_ERR_ARG = 1,          /* invalid argument (message in pcv_last_error) */
+    PCV_ERR_OOM = 2,          /* host or device allocation failed */
+    PCV_ERR_CUDA = 3,         /* a CUDA call failed */
+    PCV_ERR_TIMEOUT = 4,      /* a bounded device wait ran out */
+    PCV_ERR_BUSY = 5,         /* the context is in use */
+    PCV_NOT_SPD = 6,          /* a subset matrix was not numerically positive definite */
+    PCV_REFINE_FALLBACK = 7,  /* mixed precision: refinement needed the FP64 fallback (warning) */
+    PCV_ERR_UNSUPPORTED = 8   /* feature not available in this build / on this device */
+} pcv_status;
+
+enum { PCV_ROLE_TRAIN = 0, PCV_ROLE_VALID = 1, PCV_ROLE_IGNORE = 2 };
+
+/* Arithmetic of the hot path.
+ *   PCV_PREC_FP64:  every step in FP64 (reference GPU path).
+ *   PCV_PREC_MIXED: matrix factorised in a lower precision, solution refined
+ *                   against double-float residuals; same results to the stated
+ *                   tolerance (1e-6 relative on losses, 1e-5 on predictions). */
+enum { PCV_PREC_FP64 = 0, PCV_PREC_MIXED = 1 };
+
+enum { PCV_LAYOUT_RECTS = 0, PCV_LAYOUT_GRID = 1 };
+
+typedef struct { double x0, x1, y0, y1; } pcv_rect;
+
+/* Subset layout (Sec. 2.3).
+ *   kind = PCV_LAYOUT_GRID:  regular nx x ny cores over the domain.
+ *   kind = PCV_LAYOUT_RECTS: n_cores explicit cores (caller's array, copied).
+ *   has_domain = 0: the domain is the bounding box of all n points.
+ *   delta >= 0: shell width. */
+typedef struct {
+    int32_t kind;
+    int32_t nx, ny;
+    const pcv_rect* cores;
+    int32_t n_cores;
+    int32_t has_domain;
+    pcv_rect domain;
+    double delta;
+} pcv_layout;
+
+/* Tuning knobs; pass NULL for defaults.  Zero fields take defaults. */
+typedef struct {
+    int32_t struct_size;       /* sizeof(pcv_options) */
+    int32_t max_slots;         /* concurrent tasks on the device (default: SM count) */
+    double workspace_fraction; /* share of free device memory for workspaces (default 0.5) */
+    int32_t refine_max_iter;   /* mixed path: maximum refinement steps (default 6) */
+    double refine_tol;         /* mixed path: stop when ||r||_inf <= tol * ||y_T||_inf (default 1e-12) */
+} pcv_options;
+
+/* ---------------------------------------------------------------- host-only */
+
+/* Build the subset membership of `layout` on the host (no device needed).
+ *   xy:   n x 2 row-major point coordinates (FP64), finite.
+ *   role: n entries in {PCV_ROLE_TRAIN, PCV_ROLE_VALID, PCV_ROLE_IGNORE}.
+ * On success *out owns CSR arrays (see pcv_plan_info).  Errors: PCV_ERR_ARG for
+ * n < 0, NULL pointers with n > 0, a bad role, non-finite coordinates, an empty
+ * or inverted domain, nx/ny < 1, delta < 0 or non-finite; PCV_ERR_OOM. */
+pcv_status pcv_plan_create(const double* xy, const uint8_t* role, int64_t n,
+                           const pcv_layout* layout, pcv_plan** out);
+
+/* Read-only views of the membership, valid until pcv_plan_destroy:
+ *   subset i trains on T_idx[T_off[i] .. T_off[i+1]) and validates
+ *   V_idx[V_off[i] .. V_off[i+1]), indices into the input arrays, ascending.
+ * pcv_plan_cores writes the N core rectangles (x0, x1, y0, y1) to the caller's
+ * array `cores` of N = *n_subsets entries. */
+pcv_status pcv_plan_info(const pcv_plan* plan, int32_t* n_subsets, const int64_t** T_off,
+                         const int64_t** T_idx, const int64_t** V_off, const int64_t** V_idx);
+pcv_status pcv_plan_cores(const pcv_plan* plan, pcv_rect* cores);
+void pcv_plan_destroy(pcv_plan* plan);
+
+/* ------------------------------------------------------------ device context */
+
+/* Create a context on CUDA device `device`: builds the plan (as pcv_plan_create),
+ * copies locations, values and membership to device memory, where they stay
+ * resident for the context's lifetime.  Work buffers are allocated on first use.
+ *   v: n observed values (FP64), finite.
+ * Errors: as pcv_plan_create, plus PCV_ERR_CUDA / PCV_ERR_OOM. */
+pcv_status pcv_create(const double* xy, const double* v, const uint8_t* role, int64_t n,
+                      const pcv_layout* layout, int32_t device, const pcv_options* opts,
+                      pcv_ctx** out);
+
+/* Membership of a context (same views as pcv_plan_info). */
+pcv_status pcv_subset_info(const pcv_ctx* ctx, int32_t* n_subsets, const int64_t** T_off,
+                           const int64_t** T_idx, const int64_t** V_off, const int64_t** V_idx);
+
+/* Parallel-CV loss (Eq. 6) for B parameter configurations; host buffers.
+ *   params:          B x 3 row-major (sigma2, rho, tau2).
+ *   precision:       PCV_PREC_FP64 or PCV_PREC_MIXED.
+ *   sspe:            out, B sums of local SSPEs (Eq. 6), FP64.
+ *   sspe_per_subset: out or NULL, B x N local SSPEs z_i (0 for skipped subsets).
+ *   yhat_valid:      out or NULL, B x n_valid predictions of the validation points
+ *                    in membership order (subset 0's V list, then subset 1's, ...).
+ *   n_valid:         out or NULL, number of validation points in all cores.
+ *   status:          out or NULL, B per-configuration statuses: PCV_OK,
+ *                    PCV_ERR_ARG (sigma2 <= 0, rho <= 0, tau2 < 0 or non-finite;
+ *                    sspe = NaN), PCV_NOT_SPD (sspe = NaN), PCV_REFINE_FALLBACK.
+ * Synchronises `stream`.  Returns PCV_OK unless the call itself failed. */
+pcv_status pcv_cv_loss(pcv_ctx* ctx, const double* params, int32_t B, int32_t precision,
+                       double* sspe, double* sspe_per_subset, double* yhat_valid,
+                       int64_t* n_valid, int32_t* status, void* stream);
+
+/* Same on device buffers (params, outputs in device memory); asynchronous on
+ * `stream`: nothing is copied between host and device.  Any output may be NULL
+ * except d_sspe. */
+pcv_status pcv_cv_loss_device(pcv_ctx* ctx, const double* d_params, int32_t B,
+                              int32_t precision, double* d_sspe, double* d_sspe_per_subset,
+                              double* d_yhat_valid, int32_t* d_status, void* stream);
+
+/* Kriging predictions (Eq. 3) at m new locations with one configuration.
+ * Each location is predicted by the subset whose core contains it (locations
+ * outside D are first clamped onto D), from that subset's training data (core
+ * and shell).  xy_new: m x 2 host array; yhat: m host outputs.  Synchronises. */
+pcv_status pcv_predict(pcv_ctx* ctx, const double* params3, const double* xy_new, int64_t m,
+                       int32_t precision, double* yhat, void* stream);
+
+/* Kernel timing for benchmarks.  When enabled, pcv_cv_loss* records CUDA events
+ * on the launching stream around the task kernel and around the combine kernel;
+ * pcv_kernel_time waits for the most recent call's end events and returns the
+ * two durations in milliseconds.  PCV_ERR_ARG if timing is off or nothing ran. */
+pcv_status pcv_set_timing(pcv_ctx* ctx, int32_t enable);
+pcv_status pcv_kernel_time(pcv_ctx* ctx, double* task_ms, double* combine_ms);
+
+/* Destroy a context and free its device memory (synchronises the device). */
+void pcv_destroy(pcv_ctx* ctx);
+
+/* ----------------------------------------------------------------- utilities */
+const char* pcv_status_str(int32_t status);
+const char* pcv_last_error(void);
+int32_t pcv_version(void);
+
+/* Number of kernels of this library launched by the calling thread since the
+ * last reset (for launch accounting in benchmarks); reset when reset != 0. */
+int64_t pcv_launch_count(int32_t reset);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PCV_H */

@@ -1,0 +1,528 @@
+// api.cu -- the C ABI of include/pcv.h: plans, device contexts and dispatch.
+//
+// pcv_create builds the subset membership (Sec. 2.3) once on the host and keeps
+// the data and the membership resident in device memory (Algorithm 1: "dividing
+// and reading the data have to be done once" for many parameter configurations).
+// pcv_cv_loss then runs one persistent launch over all (subset, configuration)
+// tasks and the fixed-order combine (Eq. 6).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <mutex>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "pcv_internal.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+pcv_status fail(pcv_status s, const std::string& msg) {
+    g_err = msg;
+    return s;
+}
+
+pcv_status cuda_fail(cudaError_t e, const char* where) {
+    g_err = std::string(where) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? PCV_ERR_OOM : PCV_ERR_CUDA;
+}
+
+#define CUDA_TRY(expr)                                              \
+    do {                                                            \
+        cudaError_t e_ = (expr);                                    \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #expr);         \
+    } while (0)
+
+template <class T>
+struct DevBuf {
+    T* p = nullptr;
+    size_t n = 0;
+    ~DevBuf() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+    cudaError_t reserve(size_t want) {
+        if (want <= n && p) return cudaSuccess;
+        release();
+        size_t bytes = std::max<size_t>(want, 1) * sizeof(T);
+        cudaError_t e = cudaMalloc(&p, bytes);
+        if (e == cudaSuccess) n = std::max<size_t>(want, 1);
+        return e;
+    }
+};
+
+struct Workspace {
+    DevBuf<unsigned char> mem;
+    int grid = 0;
+    int32_t ld = 0;
+    int64_t slot_bytes = 0;
+};
+
+}  // namespace
+
+struct pcv_plan {
+    pcv::Plan p;
+};
+
+struct pcv_ctx {
+    int device = 0;
+    int sms = 0;
+    pcv::Plan plan;
+    pcv_options opts{};
+    DevBuf<double> X, Y, V;                 // all points
+    DevBuf<int64_t> Toff, Voff;
+    DevBuf<int32_t> Tidx;
+    DevBuf<double> Vx, Vy, Vv;              // validation points in membership order
+    DevBuf<int32_t> order;                  // subsets with validation data, longest first
+    int32_t n_active = 0;
+    int32_t kmax = 0;
+    int64_t mmax = 0;
+    int64_t nV = 0;
+    // per-call buffers
+    DevBuf<double> z, params, sspe;
+    DevBuf<int32_t> tst, status;
+    DevBuf<unsigned int> counter;
+    Workspace ws[2];
+    // prediction buffers
+    DevBuf<double> Px, Py, Pyhat;
+    DevBuf<int64_t> Poff;
+    DevBuf<int32_t> Porder;
+    // optional kernel timing (events on the launching stream)
+    bool timing = false;
+    bool timed_task = false, timed_combine = false;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    ~pcv_ctx() {
+        for (auto& e : ev)
+            if (e) cudaEventDestroy(e);
+    }
+};
+
+namespace {
+
+pcv_options default_options(const pcv_options* o) {
+    pcv_options d{};
+    d.struct_size = sizeof(pcv_options);
+    d.max_slots = 0;
+    d.workspace_fraction = 0.5;
+    d.refine_max_iter = 6;
+    d.refine_tol = 1e-12;
+    if (o) {
+        if (o->struct_size != 0 && o->struct_size != (int32_t)sizeof(pcv_options)) return d;
+        if (o->max_slots > 0) d.max_slots = o->max_slots;
+        if (o->workspace_fraction > 0 && o->workspace_fraction <= 0.95) d.workspace_fraction = o->workspace_fraction;
+        if (o->refine_max_iter > 0) d.refine_max_iter = o->refine_max_iter;
+        if (o->refine_tol > 0) d.refine_tol = o->refine_tol;
+    }
+    return d;
+}
+
+int32_t round_up(int64_t v, int64_t m) { return (int32_t)(((std::max<int64_t>(v, 1) + m - 1) / m) * m); }
+
+// Allocate the per-CTA workspace slots of one precision (once per context).
+pcv_status ensure_workspace(pcv_ctx* c, int prec, int64_t ntask_hint) {
+    Workspace& w = c->ws[prec];
+    if (w.grid > 0) return PCV_OK;
+    const int32_t ld = round_up(c->kmax, 128);
+    const int64_t sb = prec == PCV_PREC_FP64 ? pcv::slot_bytes_fp64(ld, c->mmax) : pcv::slot_bytes_mixed(ld, c->mmax);
+    size_t free_b = 0, total_b = 0;
+    CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+    const double budget = c->opts.workspace_fraction * (double)free_b;
+    int64_t g = c->opts.max_slots > 0 ? c->opts.max_slots : c->sms;
+    g = std::min<int64_t>(g, (int64_t)(budget / (double)sb));
+    (void)ntask_hint;
+    if (g < 1) return fail(PCV_ERR_OOM, "workspace for one task does not fit in device memory");
+    cudaError_t e = w.mem.reserve((size_t)(g * sb));
+    if (e != cudaSuccess) return cuda_fail(e, "workspace allocation");
+    w.grid = (int)g;
+    w.ld = ld;
+    w.slot_bytes = sb;
+    return PCV_OK;
+}
+
+bool bad_precision(int32_t p) { return p != PCV_PREC_FP64 && p != PCV_PREC_MIXED; }
+
+}  // namespace
+
+// ----------------------------------------------------------------- plans
+
+PCV_API pcv_status pcv_plan_create(const double* xy, const uint8_t* role, int64_t n, const pcv_layout* layout,
+                                   pcv_plan** out) {
+    if (!out) return fail(PCV_ERR_ARG, "NULL out");
+    *out = nullptr;
+    std::unique_ptr<pcv_plan> p(new (std::nothrow) pcv_plan);
+    if (!p) return fail(PCV_ERR_OOM, "host allocation");
+    std::string err;
+    try {
+        pcv_status s = pcv::build_plan(xy, role, n, layout, p->p, err);
+        if (s != PCV_OK) return fail(s, err);
+    } catch (const std::bad_alloc&) {
+        return fail(PCV_ERR_OOM, "host allocation");
+    }
+    *out = p.release();
+    return PCV_OK;
+}
+
+static pcv_status plan_views(const pcv::Plan& P, int32_t* N, const int64_t** To, const int64_t** Ti,
+                             const int64_t** Vo, const int64_t** Vi) {
+    if (N) *N = P.N;
+    if (To) *To = P.T_off.data();
+    if (Ti) *Ti = P.T_idx.data();
+    if (Vo) *Vo = P.V_off.data();
+    if (Vi) *Vi = P.V_idx.data();
+    return PCV_OK;
+}
+
+PCV_API pcv_status pcv_plan_info(const pcv_plan* plan, int32_t* N, const int64_t** T_off, const int64_t** T_idx,
+                                 const int64_t** V_off, const int64_t** V_idx) {
+    if (!plan) return fail(PCV_ERR_ARG, "NULL plan");
+    return plan_views(plan->p, N, T_off, T_idx, V_off, V_idx);
+}
+
+PCV_API pcv_status pcv_plan_cores(const pcv_plan* plan, pcv_rect* cores) {
+    if (!plan || !cores) return fail(PCV_ERR_ARG, "NULL argument");
+    std::copy(plan->p.cores.begin(), plan->p.cores.end(), cores);
+    return PCV_OK;
+}
+
+PCV_API void pcv_plan_destroy(pcv_plan* plan) { delete plan; }
+
+// ----------------------------------------------------------------- contexts
+
+PCV_API pcv_status pcv_create(const double* xy, const double* v, const uint8_t* role, int64_t n,
+                              const pcv_layout* layout, int32_t device, const pcv_options* opts, pcv_ctx** out) {
+    if (!out) return fail(PCV_ERR_ARG, "NULL out");
+    *out = nullptr;
+    if (n > 0 && !v) return fail(PCV_ERR_ARG, "NULL values");
+    for (int64_t j = 0; j < n; ++j)
+        if (!std::isfinite(v[j])) return fail(PCV_ERR_ARG, "non-finite value");
+    std::unique_ptr<pcv_ctx> c(new (std::nothrow) pcv_ctx);
+    if (!c) return fail(PCV_ERR_OOM, "host allocation");
+    std::string err;
+    try {
+        pcv_status s = pcv::build_plan(xy, role, n, layout, c->plan, err);
+        if (s != PCV_OK) return fail(s, err);
+    } catch (const std::bad_alloc&) {
+        return fail(PCV_ERR_OOM, "host allocation");
+    }
+    int ndev = 0;
+    CUDA_TRY(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) return fail(PCV_ERR_ARG, "bad device index");
+    CUDA_TRY(cudaSetDevice(device));
+    c->device = device;
+    CUDA_TRY(cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device));
+    c->opts = default_options(opts);
+    const pcv::Plan& P = c->plan;
+    const int32_t N = P.N;
+
+    // points as SoA
+    std::vector<double> hx(n), hy(n);
+    for (int64_t j = 0; j < n; ++j) { hx[j] = xy[2 * j]; hy[j] = xy[2 * j + 1]; }
+    CUDA_TRY(c->X.reserve(n));
+    CUDA_TRY(c->Y.reserve(n));
+    CUDA_TRY(c->V.reserve(n));
+    if (n) {
+        CUDA_TRY(cudaMemcpy(c->X.p, hx.data(), n * sizeof(double), cudaMemcpyHostToDevice));
+        CUDA_TRY(cudaMemcpy(c->Y.p, hy.data(), n * sizeof(double), cudaMemcpyHostToDevice));
+        CUDA_TRY(cudaMemcpy(c->V.p, v, n * sizeof(double), cudaMemcpyHostToDevice));
+    }
+    // membership
+    std::vector<int32_t> tidx(P.T_idx.begin(), P.T_idx.end());
+    CUDA_TRY(c->Toff.reserve(N + 1));
+    CUDA_TRY(c->Voff.reserve(N + 1));
+    CUDA_TRY(c->Tidx.reserve(tidx.size()));
+    CUDA_TRY(cudaMemcpy(c->Toff.p, P.T_off.data(), (N + 1) * sizeof(int64_t), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(c->Voff.p, P.V_off.data(), (N + 1) * sizeof(int64_t), cudaMemcpyHostToDevice));
+    if (!tidx.empty()) CUDA_TRY(cudaMemcpy(c->Tidx.p, tidx.data(), tidx.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    // validation points in membership order
+    const int64_t nV = P.V_off[N];
+    c->nV = nV;
+    std::vector<double> vx(nV), vy(nV), vv(nV);
+    for (int64_t q = 0; q < nV; ++q) {
+        const int64_t j = P.V_idx[q];
+        vx[q] = xy[2 * j];
+        vy[q] = xy[2 * j + 1];
+        vv[q] = v[j];
+    }
+    CUDA_TRY(c->Vx.reserve(nV));
+    CUDA_TRY(c->Vy.reserve(nV));
+    CUDA_TRY(c->Vv.reserve(nV));
+    if (nV) {
+        CUDA_TRY(cudaMemcpy(c->Vx.p, vx.data(), nV * sizeof(double), cudaMemcpyHostToDevice));
+        CUDA_TRY(cudaMemcpy(c->Vy.p, vy.data(), nV * sizeof(double), cudaMemcpyHostToDevice));
+        CUDA_TRY(cudaMemcpy(c->Vv.p, vv.data(), nV * sizeof(double), cudaMemcpyHostToDevice));
+    }
+    // active subsets (with validation data, Sec. 4.3.1), longest first
+    std::vector<int32_t> ord;
+    for (int32_t i = 0; i < N; ++i)
+        if (P.V_off[i + 1] > P.V_off[i]) ord.push_back(i);
+    std::stable_sort(ord.begin(), ord.end(), [&](int32_t a, int32_t b) {
+        return (P.T_off[a + 1] - P.T_off[a]) > (P.T_off[b + 1] - P.T_off[b]);
+    });
+    c->n_active = (int32_t)ord.size();
+    c->kmax = 0;
+    c->mmax = 0;
+    for (int32_t i : ord) {
+        c->kmax = std::max<int32_t>(c->kmax, (int32_t)(P.T_off[i + 1] - P.T_off[i]));
+        c->mmax = std::max<int64_t>(c->mmax, P.V_off[i + 1] - P.V_off[i]);
+    }
+    CUDA_TRY(c->order.reserve(ord.size()));
+    if (!ord.empty()) CUDA_TRY(cudaMemcpy(c->order.p, ord.data(), ord.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    CUDA_TRY(c->counter.reserve(1));
+    *out = c.release();
+    return PCV_OK;
+}
+
+PCV_API pcv_status pcv_subset_info(const pcv_ctx* c, int32_t* N, const int64_t** T_off, const int64_t** T_idx,
+                                   const int64_t** V_off, const int64_t** V_idx) {
+    if (!c) return fail(PCV_ERR_ARG, "NULL ctx");
+    return plan_views(c->plan, N, T_off, T_idx, V_off, V_idx);
+}
+
+static pcv_status run_tasks(pcv_ctx* c, const double* d_params, int32_t B, int32_t prec, const int64_t* P_off,
+                            const double* Px, const double* Py, const double* Pv, const int32_t* order,
+                            int32_t n_order, double* d_yhat, int64_t yhat_stride, void* stream) {
+    const int32_t N = c->plan.N;
+    CUDA_TRY(c->z.reserve((size_t)B * N));
+    CUDA_TRY(c->tst.reserve((size_t)B * N));
+    cudaStream_t s = (cudaStream_t)stream;
+    CUDA_TRY(cudaMemsetAsync(c->z.p, 0, (size_t)B * N * sizeof(double), s));
+    CUDA_TRY(cudaMemsetAsync(c->tst.p, 0, (size_t)B * N * sizeof(int32_t), s));
+    if ((int64_t)n_order * B == 0) return PCV_OK;
+    pcv_status st = ensure_workspace(c, prec, (int64_t)n_order * B);
+    if (st != PCV_OK) return st;
+    if (prec == PCV_PREC_MIXED) {
+        int e = pcv::mixed_prepare(c->device);
+        if (e) return cuda_fail((cudaError_t)e, "mixed-path set-up");
+    }
+    Workspace& w = c->ws[prec];
+    CUDA_TRY(cudaMemsetAsync(c->counter.p, 0, sizeof(unsigned int), s));
+    pcv::TaskArgs a{};
+    a.X = c->X.p;
+    a.Y = c->Y.p;
+    a.Vals = c->V.p;
+    a.T_off = c->Toff.p;
+    a.T_idx = c->Tidx.p;
+    a.P_off = P_off;
+    a.Px = Px;
+    a.Py = Py;
+    a.Pv = Pv;
+    a.order = order;
+    a.n_order = n_order;
+    a.params = d_params;
+    a.B = B;
+    a.N = N;
+    a.z = c->z.p;
+    a.tstatus = c->tst.p;
+    a.yhat = d_yhat;
+    a.yhat_stride = yhat_stride;
+    a.counter = c->counter.p;
+    a.work = reinterpret_cast<double*>(w.mem.p);
+    a.slot_bytes = w.slot_bytes;
+    a.ld = w.ld;
+    a.refine_max_iter = c->opts.refine_max_iter;
+    a.refine_tol = c->opts.refine_tol;
+    const int grid = (int)std::min<int64_t>(w.grid, (int64_t)n_order * B);
+    if (c->timing) CUDA_TRY(cudaEventRecord(c->ev[0], s));
+    int e = prec == PCV_PREC_FP64 ? pcv::launch_task_fp64(a, grid, stream) : pcv::launch_task_mixed(a, grid, stream);
+    if (e) return cuda_fail((cudaError_t)e, "task kernel launch");
+    if (c->timing) {
+        CUDA_TRY(cudaEventRecord(c->ev[1], s));
+        c->timed_task = true;
+    }
+    return PCV_OK;
+}
+
+PCV_API pcv_status pcv_cv_loss_device(pcv_ctx* c, const double* d_params, int32_t B, int32_t prec, double* d_sspe,
+                                      double* d_sspe_per_subset, double* d_yhat_valid, int32_t* d_status,
+                                      void* stream) {
+    if (!c) return fail(PCV_ERR_ARG, "NULL ctx");
+    if (B < 0) return fail(PCV_ERR_ARG, "B < 0");
+    if (B == 0) return PCV_OK;
+    if (!d_params || !d_sspe) return fail(PCV_ERR_ARG, "NULL params or sspe");
+    if (bad_precision(prec)) return fail(PCV_ERR_ARG, "unknown precision");
+    CUDA_TRY(cudaSetDevice(c->device));
+    pcv_status st = run_tasks(c, d_params, B, prec, c->Voff.p, c->Vx.p, c->Vy.p, c->Vv.p, c->order.p, c->n_active,
+                              d_yhat_valid, c->nV, stream);
+    if (st != PCV_OK) return st;
+    const int32_t N = c->plan.N;
+    if (c->timing) CUDA_TRY(cudaEventRecord(c->ev[2], (cudaStream_t)stream));
+    int e = pcv::launch_combine(c->z.p, c->tst.p, d_params, B, N, d_sspe, d_status, stream);
+    if (e) return cuda_fail((cudaError_t)e, "combine launch");
+    if (c->timing) {
+        CUDA_TRY(cudaEventRecord(c->ev[3], (cudaStream_t)stream));
+        c->timed_combine = true;
+    }
+    if (d_sspe_per_subset)
+        CUDA_TRY(cudaMemcpyAsync(d_sspe_per_subset, c->z.p, (size_t)B * N * sizeof(double), cudaMemcpyDeviceToDevice,
+                                 (cudaStream_t)stream));
+    return PCV_OK;
+}
+
+PCV_API pcv_status pcv_cv_loss(pcv_ctx* c, const double* params, int32_t B, int32_t prec, double* sspe,
+                               double* sspe_per_subset, double* yhat_valid, int64_t* n_valid, int32_t* status,
+                               void* stream) {
+    if (!c) return fail(PCV_ERR_ARG, "NULL ctx");
+    if (B < 0) return fail(PCV_ERR_ARG, "B < 0");
+    if (n_valid) *n_valid = c->nV;
+    if (B == 0) return PCV_OK;
+    if (!params || !sspe) return fail(PCV_ERR_ARG, "NULL params or sspe");
+    if (bad_precision(prec)) return fail(PCV_ERR_ARG, "unknown precision");
+    CUDA_TRY(cudaSetDevice(c->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    const int32_t N = c->plan.N;
+    CUDA_TRY(c->params.reserve((size_t)3 * B));
+    CUDA_TRY(c->sspe.reserve(B));
+    CUDA_TRY(c->status.reserve(B));
+    DevBuf<double> yv;
+    if (yhat_valid) CUDA_TRY(yv.reserve((size_t)B * c->nV));
+    CUDA_TRY(cudaMemcpyAsync(c->params.p, params, (size_t)3 * B * sizeof(double), cudaMemcpyHostToDevice, s));
+    pcv_status st = pcv_cv_loss_device(c, c->params.p, B, prec, c->sspe.p, nullptr, yhat_valid ? yv.p : nullptr,
+                                       c->status.p, stream);
+    if (st != PCV_OK) return st;
+    CUDA_TRY(cudaMemcpyAsync(sspe, c->sspe.p, B * sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (status) CUDA_TRY(cudaMemcpyAsync(status, c->status.p, B * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    if (sspe_per_subset)
+        CUDA_TRY(cudaMemcpyAsync(sspe_per_subset, c->z.p, (size_t)B * N * sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (yhat_valid && c->nV)
+        CUDA_TRY(cudaMemcpyAsync(yhat_valid, yv.p, (size_t)B * c->nV * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return PCV_OK;
+}
+
+PCV_API pcv_status pcv_predict(pcv_ctx* c, const double* params3, const double* xy_new, int64_t m, int32_t prec,
+                               double* yhat, void* stream) {
+    if (!c) return fail(PCV_ERR_ARG, "NULL ctx");
+    if (m < 0) return fail(PCV_ERR_ARG, "m < 0");
+    if (m == 0) return PCV_OK;
+    if (!params3 || !xy_new || !yhat) return fail(PCV_ERR_ARG, "NULL argument");
+    if (bad_precision(prec)) return fail(PCV_ERR_ARG, "unknown precision");
+    const pcv::Plan& P = c->plan;
+    const int32_t N = P.N;
+    // core containing each point, after clamping onto D
+    std::vector<int32_t> core(m);
+    for (int64_t j = 0; j < m; ++j) {
+        double x = xy_new[2 * j], y = xy_new[2 * j + 1];
+        if (!std::isfinite(x) || !std::isfinite(y)) return fail(PCV_ERR_ARG, "non-finite location");
+        x = std::min(std::max(x, P.domain.x0), P.domain.x1);
+        y = std::min(std::max(y, P.domain.y0), P.domain.y1);
+        int32_t best = -1;
+        double bestd = INFINITY;
+        for (int32_t i = 0; i < N; ++i) {
+            const pcv_rect& r = P.cores[i];
+            const bool xc = (r.x1 == P.domain.x1), yc = (r.y1 == P.domain.y1);
+            const bool in = x >= r.x0 && (xc ? x <= r.x1 : x < r.x1) && y >= r.y0 && (yc ? y <= r.y1 : y < r.y1);
+            if (in) { best = i; break; }
+            const double dx = std::max(std::max(r.x0 - x, 0.0), x - r.x1);
+            const double dy = std::max(std::max(r.y0 - y, 0.0), y - r.y1);
+            const double dd = dx * dx + dy * dy;
+            if (dd < bestd) { bestd = dd; best = i; }
+        }
+        core[j] = best;
+    }
+    std::vector<int64_t> off(N + 1, 0);
+    for (int64_t j = 0; j < m; ++j) off[core[j] + 1]++;
+    for (int32_t i = 0; i < N; ++i) off[i + 1] += off[i];
+    std::vector<int64_t> pos(off.begin(), off.end() - 1), perm(m);
+    std::vector<double> px(m), py(m);
+    for (int64_t j = 0; j < m; ++j) {
+        const int64_t q = pos[core[j]]++;
+        perm[q] = j;
+        px[q] = xy_new[2 * j];
+        py[q] = xy_new[2 * j + 1];
+    }
+    std::vector<int32_t> ord;
+    for (int32_t i = 0; i < N; ++i)
+        if (off[i + 1] > off[i]) ord.push_back(i);
+    std::stable_sort(ord.begin(), ord.end(), [&](int32_t a, int32_t b) {
+        return (P.T_off[a + 1] - P.T_off[a]) > (P.T_off[b + 1] - P.T_off[b]);
+    });
+    CUDA_TRY(cudaSetDevice(c->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    CUDA_TRY(c->Px.reserve(m));
+    CUDA_TRY(c->Py.reserve(m));
+    CUDA_TRY(c->Pyhat.reserve(m));
+    CUDA_TRY(c->Poff.reserve(N + 1));
+    CUDA_TRY(c->Porder.reserve(ord.size()));
+    CUDA_TRY(c->params.reserve(3));
+    CUDA_TRY(cudaMemcpyAsync(c->Px.p, px.data(), m * sizeof(double), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(c->Py.p, py.data(), m * sizeof(double), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(c->Poff.p, off.data(), (N + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(c->Porder.p, ord.data(), ord.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(c->params.p, params3, 3 * sizeof(double), cudaMemcpyHostToDevice, s));
+    // predictions need the slot for matrices as large as the largest training set
+    pcv_status st = run_tasks(c, c->params.p, 1, prec, c->Poff.p, c->Px.p, c->Py.p, nullptr, c->Porder.p,
+                              (int32_t)ord.size(), c->Pyhat.p, 0, stream);
+    if (st != PCV_OK) return st;
+    std::vector<double> out(m);
+    std::vector<int32_t> tst(N);
+    CUDA_TRY(cudaMemcpyAsync(out.data(), c->Pyhat.p, m * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(tst.data(), c->tst.p, N * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    for (int64_t q = 0; q < m; ++q) yhat[perm[q]] = out[q];
+    pcv_status worst = PCV_OK;
+    for (int32_t i : ord)
+        if (tst[i] != PCV_OK && tst[i] != PCV_REFINE_FALLBACK) worst = (pcv_status)tst[i];
+    if (worst != PCV_OK) return fail(worst, "prediction failed for at least one subset");
+    return PCV_OK;
+}
+
+PCV_API pcv_status pcv_set_timing(pcv_ctx* c, int32_t enable) {
+    if (!c) return fail(PCV_ERR_ARG, "NULL ctx");
+    CUDA_TRY(cudaSetDevice(c->device));
+    for (auto& e : c->ev)
+        if (!e) CUDA_TRY(cudaEventCreate(&e));
+    c->timing = enable != 0;
+    c->timed_task = c->timed_combine = false;
+    return PCV_OK;
+}
+
+PCV_API pcv_status pcv_kernel_time(pcv_ctx* c, double* task_ms, double* combine_ms) {
+    if (!c) return fail(PCV_ERR_ARG, "NULL ctx");
+    if (!c->timing || !c->timed_task) return fail(PCV_ERR_ARG, "no timed launch");
+    float t = 0.f;
+    CUDA_TRY(cudaEventSynchronize(c->ev[1]));
+    CUDA_TRY(cudaEventElapsedTime(&t, c->ev[0], c->ev[1]));
+    if (task_ms) *task_ms = t;
+    if (combine_ms) {
+        *combine_ms = 0.0;
+        if (c->timed_combine) {
+            CUDA_TRY(cudaEventSynchronize(c->ev[3]));
+            CUDA_TRY(cudaEventElapsedTime(&t, c->ev[2], c->ev[3]));
+            *combine_ms = t;
+        }
+    }
+    return PCV_OK;
+}
+
+PCV_API void pcv_destroy(pcv_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    delete c;
+}
+
+PCV_API const char* pcv_status_str(int32_t s) {
+    switch (s) {
+        case PCV_OK: return "ok";
+        case PCV_ERR_ARG: return "invalid argument";
+        case PCV_ERR_OOM: return "out of memory";
+        case PCV_ERR_CUDA: return "CUDA error";
+        case PCV_ERR_TIMEOUT: return "device wait timed out";
+        case PCV_ERR_BUSY: return "context busy";
+        case PCV_NOT_SPD: return "matrix not positive definite";
+        case PCV_REFINE_FALLBACK: return "refinement fell back to FP64";
+        case PCV_ERR_UNSUPPORTED: return "unsupported";
+        default: return "unknown status";
+    }
+}
+
+PCV_API const char* pcv_last_error(void) { return g_err.c_str(); }
+
+PCV_API int32_t pcv_version(void) { return 1; }

@@ -1,0 +1,74 @@
+// pcv_internal.h -- structures shared by the host side of the library and its kernels.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/pcv.h"
+
+#if defined(__GNUC__)
+#define PCV_API extern "C" __attribute__((visibility("default")))
+#else
+#define PCV_API extern "C"
+#endif
+
+namespace pcv {
+
+// Subset membership in CSR form (host).  Built by plan.cpp.
+struct Plan {
+    int64_t n = 0;
+    int32_t N = 0;
+    std::vector<int64_t> T_off, T_idx, V_off, V_idx;
+    std::vector<pcv_rect> cores;
+    pcv_rect domain{};
+    double delta = 0.0;
+};
+
+pcv_status build_plan(const double* xy, const uint8_t* role, int64_t n, const pcv_layout* layout,
+                      Plan& out, std::string& err);
+
+// Everything one launch of the task kernel needs.  Task t of a launch is the pair
+// (subset order[t / B], configuration t % B): all configurations of the largest
+// subset first, so that the persistent CTAs finish together (longest first).
+struct TaskArgs {
+    const double* X;        // all n points, SoA
+    const double* Y;
+    const double* Vals;
+    const int64_t* T_off;   // N + 1
+    const int32_t* T_idx;   // training membership (indices into X/Y/Vals)
+    const int64_t* P_off;   // N + 1: prediction points of subset i are P[P_off[i] .. P_off[i+1])
+    const double* Px;
+    const double* Py;
+    const double* Pv;       // observed values at the prediction points (NULL: no loss)
+    const int32_t* order;   // subsets to process, longest first
+    int32_t n_order;
+    const double* params;   // B x 3 (sigma2, rho, tau2), device
+    int32_t B;
+    int32_t N;
+    double* z;              // B x N local SSPE
+    int32_t* tstatus;       // B x N task status
+    double* yhat;           // predictions: yhat[b * yhat_stride + P_off[i] + j], or NULL
+    int64_t yhat_stride;
+    unsigned int* counter;  // task counter (zeroed before the launch)
+    double* work;           // per-CTA workspace slots
+    int64_t slot_bytes;     // bytes per slot
+    int32_t ld;             // leading dimension of the slot matrix (multiple of 128)
+    int32_t refine_max_iter;
+    double refine_tol;
+};
+
+// Kernel launchers (one per precision); return the cudaError_t as int.
+int launch_task_fp64(const TaskArgs& a, int grid, void* stream);
+int64_t slot_bytes_fp64(int32_t ld, int64_t mmax);
+int launch_task_mixed(const TaskArgs& a, int grid, void* stream);
+int64_t slot_bytes_mixed(int32_t ld, int64_t mmax);
+int mixed_prepare(int device);   // one-time per-device set-up of the mixed path
+
+// Fixed-order sum of the local SSPEs of each configuration, plus its status.
+int launch_combine(const double* z, const int32_t* tstatus, const double* params, int32_t B,
+                   int32_t N, double* sspe, int32_t* status, void* stream);
+
+void count_launch(int n = 1);
+
+}  // namespace pcv

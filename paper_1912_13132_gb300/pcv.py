@@ -1,0 +1,282 @@
+"""Python binding of the C ABI in include/pcv.h (argument marshalling only).
+
+Every step of the hot path runs in the CUDA library ``_lib/libpcv.so``; this
+module converts numpy arrays / torch tensors to pointers and status codes to
+exceptions.  It never computes anything itself and it has no fallback: if the
+library is missing or cannot be loaded, importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build_ext
+
+PCV_OK, PCV_ERR_ARG, PCV_ERR_OOM, PCV_ERR_CUDA, PCV_ERR_TIMEOUT = 0, 1, 2, 3, 4
+PCV_ERR_BUSY, PCV_NOT_SPD, PCV_REFINE_FALLBACK, PCV_ERR_UNSUPPORTED = 5, 6, 7, 8
+PCV_PREC_FP64, PCV_PREC_MIXED = 0, 1
+PCV_LAYOUT_RECTS, PCV_LAYOUT_GRID = 0, 1
+PRECISIONS = {"fp64": PCV_PREC_FP64, "mixed": PCV_PREC_MIXED}
+
+
+class pcv_rect(ctypes.Structure):
+    _fields_ = [("x0", ctypes.c_double), ("x1", ctypes.c_double), ("y0", ctypes.c_double),
+                ("y1", ctypes.c_double)]
+
+
+class pcv_layout(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
+                ("cores", ctypes.POINTER(pcv_rect)), ("n_cores", ctypes.c_int32),
+                ("has_domain", ctypes.c_int32), ("domain", pcv_rect), ("delta", ctypes.c_double)]
+
+
+class pcv_options(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_int32), ("max_slots", ctypes.c_int32),
+                ("workspace_fraction", ctypes.c_double), ("refine_max_iter", ctypes.c_int32),
+                ("refine_tol", ctypes.c_double)]
+
+
+class PcvError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_u8p = ctypes.POINTER(ctypes.c_uint8)
+_vp = ctypes.c_void_p
+
+_SIGS = {
+    "pcv_plan_create": (ctypes.c_int, [_dp, _u8p, ctypes.c_int64, ctypes.POINTER(pcv_layout),
+                                       ctypes.POINTER(_vp)]),
+    "pcv_plan_info": (ctypes.c_int, [_vp, _i32p, ctypes.POINTER(_i64p), ctypes.POINTER(_i64p),
+                                     ctypes.POINTER(_i64p), ctypes.POINTER(_i64p)]),
+    "pcv_plan_cores": (ctypes.c_int, [_vp, ctypes.POINTER(pcv_rect)]),
+    "pcv_plan_destroy": (None, [_vp]),
+    "pcv_create": (ctypes.c_int, [_dp, _dp, _u8p, ctypes.c_int64, ctypes.POINTER(pcv_layout),
+                                  ctypes.c_int32, ctypes.POINTER(pcv_options), ctypes.POINTER(_vp)]),
+    "pcv_subset_info": (ctypes.c_int, [_vp, _i32p, ctypes.POINTER(_i64p), ctypes.POINTER(_i64p),
+                                       ctypes.POINTER(_i64p), ctypes.POINTER(_i64p)]),
+    "pcv_cv_loss": (ctypes.c_int, [_vp, _dp, ctypes.c_int32, ctypes.c_int32, _dp, _dp, _dp, _i64p,
+                                   _i32p, _vp]),
+    "pcv_cv_loss_device": (ctypes.c_int, [_vp, _vp, ctypes.c_int32, ctypes.c_int32, _vp, _vp, _vp,
+                                          _vp, _vp]),
+    "pcv_predict": (ctypes.c_int, [_vp, _dp, _dp, ctypes.c_int64, ctypes.c_int32, _dp, _vp]),
+    "pcv_set_timing": (ctypes.c_int, [_vp, ctypes.c_int32]),
+    "pcv_kernel_time": (ctypes.c_int, [_vp, _dp, _dp]),
+    "pcv_destroy": (None, [_vp]),
+    "pcv_status_str": (ctypes.c_char_p, [ctypes.c_int32]),
+    "pcv_last_error": (ctypes.c_char_p, []),
+    "pcv_version": (ctypes.c_int32, []),
+    "pcv_launch_count": (ctypes.c_int64, [ctypes.c_int32]),
+}
+EXPORTS = tuple(_SIGS)
+
+
+def load_library(path: str | None = None) -> ctypes.CDLL:
+    """Load libpcv.so (building it in-tree first when it is absent or stale)."""
+    path = path or build_ext.build()
+    if not os.path.exists(path):
+        raise ImportError(f"CUDA library not found at {path}")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+_lib = load_library()
+LIB_PATH = build_ext.LIB
+
+
+def _check(st: int, what: str):
+    if st != PCV_OK:
+        raise PcvError(st, f"{what}: {_lib.pcv_status_str(st).decode()}: {_lib.pcv_last_error().decode()}")
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _ptr(a: np.ndarray, t):
+    return a.ctypes.data_as(t)
+
+
+def make_layout(layout: dict) -> tuple[pcv_layout, object]:
+    """dict {'kind': 'grid'|'rects', 'nx', 'ny', 'cores', 'delta', 'domain'} -> pcv_layout."""
+    L = pcv_layout()
+    keep = None
+    if layout["kind"] == "grid":
+        L.kind = PCV_LAYOUT_GRID
+        L.nx, L.ny = int(layout["nx"]), int(layout["ny"])
+    elif layout["kind"] == "rects":
+        L.kind = PCV_LAYOUT_RECTS
+        rects = (pcv_rect * len(layout["cores"]))(*[pcv_rect(*map(float, r)) for r in layout["cores"]])
+        L.cores = ctypes.cast(rects, ctypes.POINTER(pcv_rect))
+        L.n_cores = len(layout["cores"])
+        keep = rects
+    else:
+        raise ValueError(layout["kind"])
+    if layout.get("domain") is not None:
+        L.has_domain = 1
+        L.domain = pcv_rect(*map(float, layout["domain"]))
+    L.delta = float(layout["delta"])
+    return L, keep
+
+
+def _csr_views(fn, handle):
+    N = ctypes.c_int32()
+    ptrs = [_i64p() for _ in range(4)]
+    _check(fn(handle, ctypes.byref(N), *[ctypes.byref(p) for p in ptrs]), "subset info")
+    n = N.value
+    To = np.ctypeslib.as_array(ptrs[0], shape=(n + 1,)).copy()
+    Vo = np.ctypeslib.as_array(ptrs[2], shape=(n + 1,)).copy()
+    def view(p, cnt):
+        cnt = int(cnt)
+        return np.ctypeslib.as_array(p, shape=(cnt,)).copy() if cnt else np.empty(0, np.int64)
+    return To, view(ptrs[1], To[-1]), Vo, view(ptrs[3], Vo[-1])
+
+
+def pcv_plan_create(xy, role, layout: dict):
+    """Host-only membership (no device).  Returns (T_off, T_idx, V_off, V_idx, cores)."""
+    xy = _f64(xy).reshape(-1, 2)
+    role = np.ascontiguousarray(role, dtype=np.uint8)
+    L, keep = make_layout(layout)
+    h = _vp()
+    _check(_lib.pcv_plan_create(_ptr(xy, _dp), _ptr(role, _u8p), len(role), ctypes.byref(L),
+                                ctypes.byref(h)), "pcv_plan_create")
+    try:
+        To, Ti, Vo, Vi = _csr_views(_lib.pcv_plan_info, h)
+        cores = (pcv_rect * (len(To) - 1))()
+        _check(_lib.pcv_plan_cores(h, cores), "pcv_plan_cores")
+        cores = np.array([[c.x0, c.x1, c.y0, c.y1] for c in cores])
+    finally:
+        _lib.pcv_plan_destroy(h)
+    del keep
+    return To, Ti, Vo, Vi, cores
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except Exception:  # pragma: no cover
+            return None
+        return None
+    return int(getattr(stream, "cuda_stream", stream))
+
+
+class Context:
+    """A device-resident dataset with its subset layout (pcv_create ... pcv_destroy)."""
+
+    def __init__(self, xy, v, role, layout: dict, device: int = 0, max_slots: int = 0,
+                 workspace_fraction: float = 0.0, refine_max_iter: int = 0, refine_tol: float = 0.0):
+        xy = _f64(xy).reshape(-1, 2)
+        v = _f64(v)
+        role = np.ascontiguousarray(role, dtype=np.uint8)
+        L, keep = make_layout(layout)
+        o = pcv_options(ctypes.sizeof(pcv_options), max_slots, workspace_fraction, refine_max_iter,
+                        refine_tol)
+        h = _vp()
+        _check(_lib.pcv_create(_ptr(xy, _dp), _ptr(v, _dp), _ptr(role, _u8p), len(v), ctypes.byref(L),
+                               device, ctypes.byref(o), ctypes.byref(h)), "pcv_create")
+        del keep
+        self._h = h
+        self.device = device
+        self.T_off, self.T_idx, self.V_off, self.V_idx = _csr_views(_lib.pcv_subset_info, h)
+        self.N = len(self.T_off) - 1
+        self.n_valid = int(self.V_off[-1])
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.pcv_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def cv_loss(self, params, precision="mixed", per_subset=False, predictions=False, stream=None):
+        """pcv_cv_loss on host arrays: returns dict(sspe, status, n_valid[, z][, yhat])."""
+        P = _f64(params).reshape(-1, 3)
+        B = len(P)
+        sspe = np.empty(B)
+        status = np.empty(B, dtype=np.int32)
+        z = np.empty((B, self.N)) if per_subset else None
+        yh = np.empty((B, self.n_valid)) if predictions else None
+        nv = ctypes.c_int64()
+        _check(_lib.pcv_cv_loss(self._h, _ptr(P, _dp), B, PRECISIONS[precision], _ptr(sspe, _dp),
+                                _ptr(z, _dp) if z is not None else None,
+                                _ptr(yh, _dp) if yh is not None else None, ctypes.byref(nv),
+                                _ptr(status, _i32p), _stream_ptr(stream)), "pcv_cv_loss")
+        out = dict(sspe=sspe, status=status, n_valid=nv.value)
+        if z is not None:
+            out["z"] = z
+        if yh is not None:
+            out["yhat"] = yh
+        return out
+
+    def cv_loss_device(self, d_params, d_sspe, precision="mixed", d_z=None, d_yhat=None,
+                       d_status=None, stream=None):
+        """pcv_cv_loss_device on torch CUDA tensors (asynchronous on the stream)."""
+        B = int(d_params.shape[0])
+        ptr = lambda t: None if t is None else t.data_ptr()
+        _check(_lib.pcv_cv_loss_device(self._h, ptr(d_params), B, PRECISIONS[precision], ptr(d_sspe),
+                                       ptr(d_z), ptr(d_yhat), ptr(d_status), _stream_ptr(stream)),
+               "pcv_cv_loss_device")
+
+    def set_timing(self, enable: bool = True):
+        _check(_lib.pcv_set_timing(self._h, 1 if enable else 0), "pcv_set_timing")
+
+    def kernel_time(self) -> tuple[float, float]:
+        """(task kernel ms, combine kernel ms) of the most recent timed call."""
+        t, c = ctypes.c_double(), ctypes.c_double()
+        _check(_lib.pcv_kernel_time(self._h, ctypes.byref(t), ctypes.byref(c)), "pcv_kernel_time")
+        return t.value, c.value
+
+    def predict(self, params3, xy_new, precision="mixed", stream=None):
+        p = _f64(params3).reshape(3)
+        q = _f64(xy_new).reshape(-1, 2)
+        out = np.empty(len(q))
+        _check(_lib.pcv_predict(self._h, _ptr(p, _dp), _ptr(q, _dp), len(q), PRECISIONS[precision],
+                                _ptr(out, _dp), _stream_ptr(stream)), "pcv_predict")
+        return out
+
+
+def pcv_create(xy, v, role, layout: dict, device: int = 0, **opts) -> Context:
+    return Context(xy, v, role, layout, device, **opts)
+
+
+def pcv_cv_loss(ctx: Context, params, precision="mixed", **kw):
+    return ctx.cv_loss(params, precision, **kw)
+
+
+def pcv_cv_loss_device(ctx: Context, d_params, d_sspe, precision="mixed", **kw):
+    return ctx.cv_loss_device(d_params, d_sspe, precision, **kw)
+
+
+def pcv_predict(ctx: Context, params3, xy_new, precision="mixed", **kw):
+    return ctx.predict(params3, xy_new, precision, **kw)
+
+
+def pcv_destroy(ctx: Context):
+    ctx.close()
+
+
+def pcv_launch_count(reset: bool = False) -> int:
+    return int(_lib.pcv_launch_count(1 if reset else 0))
+
+
+def pcv_version() -> int:
+    return int(_lib.pcv_version())

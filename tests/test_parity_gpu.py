@@ -1,0 +1,130 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 CPU oracle.
+
+Every test compares element by element on the same seeded inputs: local SSPE of
+each subset, the total (Eq. 6) and every validation prediction (Eq. 3).
+Tolerances (tests/parity_util.py): FP64 path 1e-10 relative; mixed path 1e-6 on
+losses and 1e-5 on predictions.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1912_13132_gb300 import datagen
+from parity_util import TOL, compare, pred_err, rel
+
+pytestmark = pytest.mark.gpu
+PRECS = ["fp64", "mixed"]
+
+
+def _run(gpu_lib, w, params, prec, subsets=None, **ctx_opts):
+    with gpu_lib.Context(w.xy, w.v, w.role, w.layout, **ctx_opts) as ctx:
+        out = ctx.cv_loss(params, precision=prec, per_subset=True, predictions=True)
+        V_off = ctx.V_off.copy()
+    members = oracle.all_members(w.xy, w.role, w.layout)
+    ref = oracle.cv_loss(w.xy, w.v, w.role, w.layout, params, members=members, subsets=subsets)
+    return out, ref, V_off
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_uniform_4096_full(gpu_lib, prec):
+    """4096 TRAIN + 4096 VALID uniform points, 4x4 cores, shell 0.05: every subset,
+    every prediction (k about 370-500, several 64/128-row tiles and a ragged tail)."""
+    w = datagen.config_uniform_4096()
+    P = np.array([[1.0, 0.1, 0.05], [0.7, 0.03, 0.2], [2.0, 0.3, 0.001]])
+    out, ref, V_off = _run(gpu_lib, w, P, prec)
+    assert np.all(out["status"] == 0), out["status"]
+    assert out["n_valid"] == ref["n_valid"]
+    worst = compare(out, ref, V_off, range(16), len(P), prec)
+    print(prec, worst)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_ragged_and_degenerate(gpu_lib, prec):
+    """Subset sizes from 0 to a few hundred, not multiples of any tile: a core with
+    validation data but no training data (yhat = 0), cores without validation data
+    (skipped, z = 0), a single-point subset."""
+    r = np.random.default_rng(17)
+    nT, nV = 900, 400
+    xy = r.random((nT + nV, 2))
+    xy[:nT, 0] *= 0.7                      # no training data right of x = 0.7 + shell
+    role = np.zeros(nT + nV, dtype=np.uint8)
+    role[nT:] = 1
+    xy[nT:nT + 150, 1] *= 0.5              # validation mostly in the lower half
+    role[nT + 150:nT + 300] = 2           # some IGNORE points
+    v = r.standard_normal(nT + nV)
+    xy[0] = [0.95, 0.95]                   # lone training point in the top-right core
+    lay = dict(kind="grid", nx=5, ny=3, delta=0.013, domain=(0.0, 1.0, 0.0, 1.0))
+    w = datagen.Workload("ragged", xy, v, role, lay, None)
+    P = np.array([[1.0, 0.08, 0.05], [1.3, 0.2, 0.3]])
+    out, ref, V_off = _run(gpu_lib, w, P, prec)
+    sizes = [len(T) for T, _ in ref["members"]]
+    assert 0 in sizes and 1 in sizes, sizes
+    assert np.all(out["status"] == 0)
+    compare(out, ref, V_off, range(len(sizes)), len(P), prec)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_bad_parameters(gpu_lib, prec):
+    w = datagen.make_uniform(400, 200, 2, 0.05, seed=5, name="bad")
+    P = np.array([[1.0, 0.1, 0.05], [-1.0, 0.1, 0.05], [1.0, 0.0, 0.05], [1.0, 0.1, -0.1],
+                  [np.nan, 0.1, 0.1], [1.0, 0.1, 0.0]])
+    with gpu_lib.Context(w.xy, w.v, w.role, w.layout) as ctx:
+        out = ctx.cv_loss(P, precision=prec)
+    st = out["status"].tolist()
+    assert st[:5] == [0, 1, 1, 1, 1], st
+    assert np.isnan(out["sspe"][1:5]).all() and np.isfinite(out["sspe"][0])
+    ref = oracle.cv_loss(w.xy, w.v, w.role, w.layout, P[[0, 5]])
+    assert rel(out["sspe"][0], ref["sspe"][0]) <= TOL[prec]["loss"]
+    if st[5] == 0:      # zero nugget is valid; accuracy depends on conditioning
+        assert rel(out["sspe"][5], ref["sspe"][1]) <= 1e-4
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_cluster_batch_sampled(gpu_lib, prec):
+    """Poisson-cluster locations (uneven subsets, many degenerate), a batch of 8
+    configurations in one launch, sampled subsets (smallest, largest, random)."""
+    w = datagen.config_cluster_262k(n_train=65536, n_valid=8192, fine=512, nx=16, delta=0.02)
+    P = w.params[::8]
+    with gpu_lib.Context(w.xy, w.v, w.role, w.layout) as ctx:
+        out = ctx.cv_loss(P, precision=prec, per_subset=True, predictions=True)
+        T_off, V_off = ctx.T_off.copy(), ctx.V_off.copy()
+    k = np.diff(T_off)
+    m = np.diff(V_off)
+    act = np.nonzero(m > 0)[0]
+    pick = sorted(set([int(act[np.argmax(k[act])]), int(act[np.argmin(k[act])])] +
+                      np.random.default_rng(0).choice(act, 6, replace=False).tolist()))
+    members = oracle.all_members(w.xy, w.role, w.layout)
+    ref = oracle.cv_loss(w.xy, w.v, w.role, w.layout, P, members=members, subsets=pick)
+    compare(out, ref, V_off, pick, len(P), prec, check_total=False)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_predict_new_locations(gpu_lib, prec):
+    w = datagen.make_uniform(1200, 300, 3, 0.06, seed=23, name="pred")
+    pts = np.random.default_rng(1).random((700, 2)) * 1.2 - 0.1   # some outside D
+    p = (1.5, 0.12, 0.04)
+    with gpu_lib.Context(w.xy, w.v, w.role, w.layout) as ctx:
+        yh = ctx.predict(p, pts, precision=prec)
+    ref = oracle.predict(w.xy, w.v, w.role, w.layout, p, pts)
+    assert pred_err(yh, ref) <= TOL[prec]["pred"]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_deterministic(gpu_lib, prec):
+    w = datagen.make_uniform(800, 400, 3, 0.05, seed=31, name="det")
+    P = np.array([[1.0, 0.1, 0.05], [1.0, 0.05, 0.01]])
+    with gpu_lib.Context(w.xy, w.v, w.role, w.layout, max_slots=7) as ctx:
+        a = ctx.cv_loss(P, precision=prec)["sspe"]
+        b = ctx.cv_loss(P, precision=prec)["sspe"]
+    assert np.array_equal(a, b)
+
+
+def test_sigma2_invariance_gpu(gpu_lib):
+    """Only lambda = tau2 / sigma2 and rho matter (remark after Eq. 3)."""
+    w = datagen.make_uniform(800, 400, 2, 0.05, seed=37, name="inv")
+    P = np.array([[1.0, 0.1, 0.05], [3.0, 0.1, 0.15], [0.25, 0.1, 0.0125]])
+    with gpu_lib.Context(w.xy, w.v, w.role, w.layout) as ctx:
+        s = ctx.cv_loss(P, precision="fp64")["sspe"]
+    assert np.all(rel(s, s[0]) <= 1e-12)
