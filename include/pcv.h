@@ -44,6 +44,7 @@
 #ifndef PCV_H
 #define PCV_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -177,6 +178,53 @@ pcv_status pcv_kernel_time(pcv_ctx* ctx, double* task_ms, double* combine_ms);
 
 /* Destroy a context and free its device memory (synchronises the device). */
 void pcv_destroy(pcv_ctx* ctx);
+
+/* ------------------------------------------------- allocation-free variant
+ *
+ * The paper has no counterpart to this entry point; it exists for callers that
+ * cannot call cudaMalloc -- for example a host application that owns all device
+ * memory through its own pool and forbids allocations behind its back, or a
+ * latency-critical loop in which cudaMalloc/cudaFree (which may synchronise the
+ * device) are not acceptable.  It evaluates the same FP64 cross-validation loss
+ * as pcv_cv_loss_device with precision PCV_PREC_FP64, without a pcv_ctx and
+ * without allocating: all work memory is one static device array of
+ * PCV_STATIC_SCRATCH_BYTES bytes inside this library, which every GPU that loads
+ * the library holds until the process exits.
+ *
+ * Inputs (caller's memory; d_ = device, h_ = host):
+ *   d_x, d_y, d_v:   the n point coordinates and observed values (FP64);
+ *   N:               number of subsets;
+ *   h_T_off, d_T_idx: training membership in CSR form (as pcv_plan_info gives it),
+ *                    offsets on the host (N + 1 entries), indices on the device
+ *                    as int32;
+ *   h_V_off:         validation offsets (host, N + 1 entries);
+ *   d_Vx, d_Vy, d_Vv: coordinates and values of the validation points in
+ *                    membership order (V_off[N] entries each, device);
+ *   d_params:        B x 3 (sigma2, rho, tau2), device.
+ * Outputs (device): d_sspe (B), d_sspe_per_subset (B x N, or NULL), d_status (B,
+ * or NULL), with the meanings of pcv_cv_loss.  Asynchronous on `stream`.
+ *
+ * Limits: the layout needs 256 + 2 * 8 (N + 1) + 4 N + 12 B N bytes (each region
+ * rounded up to 256) plus one matrix slot of 8 * ld^2 + 8 * (4 ld + m_max + 32)
+ * bytes, ld = largest training set rounded up to 128, to fit in the scratch array;
+ * otherwise PCV_ERR_ARG and nothing runs.  With one slot the largest training
+ * set is about 2800 points; smaller sets run more slots (up to one per SM) in
+ * parallel.
+ *
+ * Sharing: every call on a device uses the same array and finds the previous
+ * call's contents there; the call resets what must start at zero.  Calls whose
+ * work overlaps on the GPU (different streams, or other host threads) race on the
+ * array and give wrong results: serialise them.  The first call on each device
+ * looks up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  The host offset
+ * arrays are read during the call; the device arrays must stay valid until the
+ * queued work has finished. */
+#define PCV_STATIC_SCRATCH_BYTES ((size_t)64 << 20)
+pcv_status pcv_cv_loss_fp64_static(const double* d_x, const double* d_y, const double* d_v, int32_t N,
+                                   const int64_t* h_T_off, const int32_t* d_T_idx, const int64_t* h_V_off,
+                                   const double* d_Vx, const double* d_Vy, const double* d_Vv,
+                                   const double* d_params, int32_t B, double* d_sspe,
+                                   double* d_sspe_per_subset, int32_t* d_status, void* stream);
 
 /* ----------------------------------------------------------------- utilities */
 const char* pcv_status_str(int32_t status);

@@ -68,6 +68,8 @@ _SIGS = {
     "pcv_predict": (ctypes.c_int, [_vp, _dp, _dp, ctypes.c_int64, ctypes.c_int32, _dp, _vp]),
     "pcv_set_timing": (ctypes.c_int, [_vp, ctypes.c_int32]),
     "pcv_kernel_time": (ctypes.c_int, [_vp, _dp, _dp]),
+    "pcv_cv_loss_fp64_static": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int32, _i64p, _vp, _i64p, _vp, _vp,
+                                               _vp, _vp, ctypes.c_int32, _vp, _vp, _vp, _vp]),
     "pcv_destroy": (None, [_vp]),
     "pcv_status_str": (ctypes.c_char_p, [ctypes.c_int32]),
     "pcv_last_error": (ctypes.c_char_p, []),
@@ -272,6 +274,20 @@ def pcv_predict(ctx: Context, params3, xy_new, precision="mixed", **kw):
 
 def pcv_destroy(ctx: Context):
     ctx.close()
+
+
+def pcv_cv_loss_fp64_static(d_x, d_y, d_v, T_off, d_T_idx, V_off, d_Vx, d_Vy, d_Vv, d_params, d_sspe,
+                            d_sspe_per_subset=None, d_status=None, stream=None) -> int:
+    """Allocation-free FP64 cross-validation loss (see include/pcv.h).  Device
+    arguments are torch CUDA tensors; T_off / V_off are host int64 arrays.
+    Returns the pcv_status code (no exception, so callers can test the limits)."""
+    T_off = np.ascontiguousarray(T_off, dtype=np.int64)
+    V_off = np.ascontiguousarray(V_off, dtype=np.int64)
+    ptr = lambda t: None if t is None else t.data_ptr()
+    return int(_lib.pcv_cv_loss_fp64_static(
+        ptr(d_x), ptr(d_y), ptr(d_v), len(T_off) - 1, _ptr(T_off, _i64p), ptr(d_T_idx), _ptr(V_off, _i64p),
+        ptr(d_Vx), ptr(d_Vy), ptr(d_Vv), ptr(d_params), int(d_params.shape[0]), ptr(d_sspe),
+        ptr(d_sspe_per_subset), ptr(d_status), _stream_ptr(stream)))
 
 
 def pcv_launch_count(reset: bool = False) -> int:

@@ -24,7 +24,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def test_exports_match_header():
     hdr = open(os.path.join(ROOT, "include", "pcv.h")).read()
-    declared = set(re.findall(r"\b(pcv_[a-z_]+)\s*\(", hdr))
+    declared = set(re.findall(r"\b(pcv_[a-z0-9_]+)\s*\(", hdr))
     assert declared == set(pcv.EXPORTS), declared ^ set(pcv.EXPORTS)
     lib = pcv.load_library(pcv.LIB_PATH)
     for name in declared:
