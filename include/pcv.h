@@ -99,8 +99,10 @@ typedef struct {
     int32_t struct_size;       /* sizeof(pcv_options) */
     int32_t max_slots;         /* concurrent tasks on the device (default: SM count) */
     double workspace_fraction; /* share of free device memory for workspaces (default 0.5) */
-    int32_t refine_max_iter;   /* mixed path: maximum refinement steps (default 6) */
-    double refine_tol;         /* mixed path: stop when ||r||_inf <= tol * ||y_T||_inf (default 1e-12) */
+    int32_t refine_max_iter;   /* mixed path: maximum refinement corrections (default 6) */
+    double refine_tol;         /* mixed path: stop once a correction d satisfies
+                                  ||d||_inf <= tol * ||x||_inf (default 1e-6); tasks that
+                                  do not get there are recomputed in FP64 */
 } pcv_options;
 
 /* ---------------------------------------------------------------- host-only */
@@ -225,6 +227,17 @@ pcv_status pcv_cv_loss_fp64_static(const double* d_x, const double* d_y, const d
                                    const double* d_Vx, const double* d_Vy, const double* d_Vv,
                                    const double* d_params, int32_t B, double* d_sspe,
                                    double* d_sspe_per_subset, int32_t* d_status, void* stream);
+
+/* ----------------------------------------------------------------- self-tests
+ * The mixed path computes residuals and predictions in double-float arithmetic
+ * (pairs of floats).  These evaluate its primitives elementwise so that tests can
+ * compare them with FP64 references:  op 0: exp(-a) (a >= 0), 1: sqrt(a),
+ * 2: a * b, 3: a + b; each input is first rounded to double-float.
+ * pcv_selftest_df runs on the host (host arrays), pcv_selftest_df_device on the
+ * device (device arrays, asynchronous on `stream`).  b may be NULL for ops 0, 1. */
+pcv_status pcv_selftest_df(int32_t op, const double* a, const double* b, int64_t n, double* out);
+pcv_status pcv_selftest_df_device(int32_t op, const double* d_a, const double* d_b, int64_t n,
+                                  double* d_out, void* stream);
 
 /* ----------------------------------------------------------------- utilities */
 const char* pcv_status_str(int32_t status);

@@ -85,6 +85,9 @@ struct pcv_ctx {
     int32_t kmax = 0;
     int64_t mmax = 0;
     int64_t nV = 0;
+    double coord_scale = 1.0;               // power of two, window offsets scaled below 1
+    DevBuf<int32_t> fb_list;                // mixed path: tasks handed to the FP64 kernel
+    DevBuf<unsigned int> fb_count;
     // per-call buffers
     DevBuf<double> z, params, sspe;
     DevBuf<int32_t> tst, status;
@@ -112,7 +115,7 @@ pcv_options default_options(const pcv_options* o) {
     d.max_slots = 0;
     d.workspace_fraction = 0.5;
     d.refine_max_iter = 6;
-    d.refine_tol = 1e-12;
+    d.refine_tol = 1e-6;
     if (o) {
         if (o->struct_size != 0 && o->struct_size != (int32_t)sizeof(pcv_options)) return d;
         if (o->max_slots > 0) d.max_slots = o->max_slots;
@@ -272,6 +275,11 @@ PCV_API pcv_status pcv_create(const double* xy, const double* v, const uint8_t* 
         c->kmax = std::max<int32_t>(c->kmax, (int32_t)(P.T_off[i + 1] - P.T_off[i]));
         c->mmax = std::max<int64_t>(c->mmax, P.V_off[i + 1] - P.V_off[i]);
     }
+    // power-of-two scale so that offsets between training points of one window are below 1
+    double wmax = 0.0;
+    for (const pcv_rect& r : P.cores) wmax = std::max({wmax, r.x1 - r.x0, r.y1 - r.y0});
+    wmax += 2.0 * P.delta;
+    c->coord_scale = wmax > 0.0 ? std::ldexp(1.0, -std::ilogb(wmax) - 1) : 1.0;
     CUDA_TRY(c->order.reserve(ord.size()));
     if (!ord.empty()) CUDA_TRY(cudaMemcpy(c->order.p, ord.data(), ord.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
     CUDA_TRY(c->counter.reserve(1));
@@ -300,6 +308,11 @@ static pcv_status run_tasks(pcv_ctx* c, const double* d_params, int32_t B, int32
     if (prec == PCV_PREC_MIXED) {
         int e = pcv::mixed_prepare(c->device);
         if (e) return cuda_fail((cudaError_t)e, "mixed-path set-up");
+        st = ensure_workspace(c, PCV_PREC_FP64, 0);   // fallback tasks run in FP64
+        if (st != PCV_OK) return st;
+        CUDA_TRY(c->fb_list.reserve((size_t)n_order * B));
+        CUDA_TRY(c->fb_count.reserve(2));
+        CUDA_TRY(cudaMemsetAsync(c->fb_count.p, 0, 2 * sizeof(unsigned int), s));
     }
     Workspace& w = c->ws[prec];
     CUDA_TRY(cudaMemsetAsync(c->counter.p, 0, sizeof(unsigned int), s));
@@ -328,6 +341,9 @@ static pcv_status run_tasks(pcv_ctx* c, const double* d_params, int32_t B, int32
     a.ld = w.ld;
     a.refine_max_iter = c->opts.refine_max_iter;
     a.refine_tol = c->opts.refine_tol;
+    a.coord_scale = c->coord_scale;
+    a.fb_list = c->fb_list.p;
+    a.fb_count = c->fb_count.p;
     const int grid = (int)std::min<int64_t>(w.grid, (int64_t)n_order * B);
     if (c->timing) CUDA_TRY(cudaEventRecord(c->ev[0], s));
     int e = prec == PCV_PREC_FP64 ? pcv::launch_task_fp64(a, grid, stream) : pcv::launch_task_mixed(a, grid, stream);
@@ -335,6 +351,21 @@ static pcv_status run_tasks(pcv_ctx* c, const double* d_params, int32_t B, int32
     if (c->timing) {
         CUDA_TRY(cudaEventRecord(c->ev[1], s));
         c->timed_task = true;
+    }
+    if (prec == PCV_PREC_MIXED) {
+        // tasks the mixed kernel could not finish run again in FP64 (the list and
+        // its length stay on the device; CTAs beyond the list exit at once)
+        Workspace& w64 = c->ws[PCV_PREC_FP64];
+        pcv::TaskArgs f = a;
+        f.work = reinterpret_cast<double*>(w64.mem.p);
+        f.slot_bytes = w64.slot_bytes;
+        f.ld = w64.ld;
+        f.counter = c->fb_count.p + 1;
+        f.task_list = c->fb_list.p;
+        f.task_count = c->fb_count.p;
+        f.list_status = PCV_REFINE_FALLBACK;
+        e = pcv::launch_task_fp64(f, (int)std::min<int64_t>(w64.grid, (int64_t)n_order * B), stream);
+        if (e) return cuda_fail((cudaError_t)e, "fallback kernel launch");
     }
     return PCV_OK;
 }

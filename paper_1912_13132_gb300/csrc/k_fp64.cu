@@ -263,7 +263,7 @@ __device__ int run_task(Smem64& sm, const TaskArgs& a, int i, int b) {
             a.z[zoff] = zz;
         }
     }
-    if (tid == 0) a.tstatus[zoff] = PCV_OK;
+    if (tid == 0) a.tstatus[zoff] = a.task_list ? a.list_status : PCV_OK;
     __syncthreads();
     return PCV_OK;
 }
@@ -271,13 +271,14 @@ __device__ int run_task(Smem64& sm, const TaskArgs& a, int i, int b) {
 __global__ void __launch_bounds__(NT, 1) k_cv_fp64(TaskArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem64& sm = *reinterpret_cast<Smem64*>(smem_raw);
-    const int ntask = a.n_order * a.B;
+    const int ntask = a.task_list ? (int)*a.task_count : a.n_order * a.B;
     for (;;) {
         if (threadIdx.x == 0) sm.task = (int)atomicAdd(a.counter, 1u);
         __syncthreads();
-        const int t = sm.task;
+        int t = sm.task;
         __syncthreads();
         if (t >= ntask) break;
+        if (a.task_list) t = a.task_list[t];
         run_task(sm, a, a.order[t / a.B], t % a.B);
     }
 }

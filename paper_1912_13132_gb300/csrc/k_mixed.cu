@@ -1,10 +1,608 @@
-// k_mixed.cu -- mixed-precision path (placeholder until the kernels land).
+// k_mixed.cu -- mixed-precision path of parallel cross-validation (arXiv 1912.13132).
+//
+// Same task decomposition as the FP64 path (Algorithm 1's parallel loop over
+// subsets, extended over the batch of configurations), different arithmetic:
+//   gather     training coordinates as scaled offsets from the subset's first
+//              training point, split in double-float (high parts on a 2^-20 grid
+//              so that differences of high parts are exact)
+//   assemble   A32 = Sigma(rho) + lambda I in FP32                  (Eq. 3, Sec. 3)
+//   factor     A32 ~ L L^T in FP32, left-looking, 64-wide block columns
+//   refine     x <- x + L^-T L^-1 r,  r = y - A x with A's entries and the sums
+//              in double-float (exp by Tang's method, see df.cuh), until the last
+//              correction is below refine_tol of the solution
+//   predict    yhat_j = sum_a exp(-||p_j - s_a|| / rho) x_a in double-float (Eq. 3)
+//   loss       z = sum_j (yhat_j - y_V,j)^2 in FP64                  (Eq. 4)
+// A task whose FP32 factorisation breaks down or whose refinement does not
+// converge is appended to a fallback list that the FP64 kernel then runs.
 #include <cuda_runtime.h>
 
+#include <cmath>
+#include <mutex>
+
+#include "df.cuh"
 #include "pcv_internal.h"
 
 namespace pcv {
-int64_t slot_bytes_mixed(int32_t ld, int64_t mmax) { return slot_bytes_fp64(ld, mmax); }
-int mixed_prepare(int) { return 0; }
-int launch_task_mixed(const TaskArgs&, int, void*) { return (int)cudaErrorNotSupported; }
+namespace {
+
+using dfm::df;
+
+constexpr int NB = 64;   // block-column width of the factorisation and of the residual tiles
+constexpr int NT = 256;  // threads per CTA
+constexpr int KC = 16;   // K chunk of the trailing update
+constexpr double QSCALE = 1048576.0;  // 2^20: grid of the high parts of training coordinates
+
+__constant__ dfm::ExpConsts c_exp;
+
+struct SlotM {
+    float* L;      // ld x ld, column-major, lower triangle
+    double* yv;    // training values
+    double* xs;    // solution
+    double* rr;    // residual
+    double* ep;    // squared errors (mmax)
+    float *xh, *xl, *yh, *yl;   // double-float scaled offsets of the training points
+    float* w;      // solve vector
+    float *qh, *ql;             // solution in double-float
+    float *ah, *al;             // residual accumulators
+};
+
+__device__ __forceinline__ SlotM slot_of(const TaskArgs& a) {
+    char* base = reinterpret_cast<char*>(a.work) + (int64_t)blockIdx.x * a.slot_bytes;
+    const int64_t ld = a.ld;
+    SlotM s;
+    s.L = reinterpret_cast<float*>(base);
+    double* d = reinterpret_cast<double*>(base + ld * ld * 4);
+    s.yv = d;
+    s.xs = d + ld;
+    s.rr = d + 2 * ld;
+    float* f = reinterpret_cast<float*>(base + ld * ld * 4 + 3 * ld * 8);
+    s.xh = f;
+    s.xl = f + ld;
+    s.yh = f + 2 * ld;
+    s.yl = f + 3 * ld;
+    s.w = f + 4 * ld;
+    s.qh = f + 5 * ld;
+    s.ql = f + 6 * ld;
+    s.ah = f + 7 * ld;
+    s.al = f + 8 * ld;
+    // ep is placed after the float arrays (its length is mmax, not ld)
+    s.ep = reinterpret_cast<double*>(f + 9 * ld);
+    return s;
+}
+
+struct SmemM {
+    float L[NB][NB + 1];           // diagonal block
+    float Ta[KC][NB + 4];          // trailing-update staging
+    float Tb[KC][NB + 4];
+    float rinv[NB];                // reciprocals of the diagonal of L_JJ
+    float tbl[2 * dfm::kExpTable]; // exp table (copy of c_exp.tbl)
+    float ph[16][NB], pl[16][NB];  // residual partial sums (double-float)
+    float wj[NB];
+    double dred[NT / 32];
+    float fred[NT / 32];
+    int flag;
+    int task;
+};
+
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ float block_max(SmemM& sm, float v) {
+    v = warp_max(v);
+    if ((threadIdx.x & 31) == 0) sm.fred[threadIdx.x >> 5] = v;
+    __syncthreads();
+    float r = sm.fred[0];
+#pragma unroll
+    for (int i = 1; i < NT / 32; ++i) r = fmaxf(r, sm.fred[i]);
+    __syncthreads();
+    return r;
+}
+
+// ---------------------------------------------------------------- factorisation (FP32)
+
+// C[r0:r0+rb, j0:j0+jb] -= L[r0:r0+rb, 0:j0] * L[j0:j0+jb, 0:j0]^T, register prefetch of the next chunk
+__device__ void update_tile32(SmemM& sm, float* A, int64_t ld, int r0, int rb, int j0, int jb) {
+    const int tid = threadIdx.x;
+    const int ty = tid >> 4, tx = tid & 15;
+    float acc[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = 0.0f;
+    float pa[4], pb[4];
+    auto load = [&](int p0) {
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            const int e = tid + NT * s, r = e & (NB - 1), q = e >> 6;
+            pa[s] = r < rb ? A[(int64_t)(r0 + r) + (int64_t)(p0 + q) * ld] : 0.0f;
+            pb[s] = r < jb ? A[(int64_t)(j0 + r) + (int64_t)(p0 + q) * ld] : 0.0f;
+        }
+    };
+    load(0);
+    for (int p0 = 0; p0 < j0; p0 += KC) {
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            const int e = tid + NT * s, r = e & (NB - 1), q = e >> 6;
+            sm.Ta[q][r] = pa[s];
+            sm.Tb[q][r] = pb[s];
+        }
+        __syncthreads();
+        if (p0 + KC < j0) load(p0 + KC);
+#pragma unroll
+        for (int q = 0; q < KC; ++q) {
+            const float4 ar = *reinterpret_cast<const float4*>(&sm.Ta[q][ty * 4]);
+            const float4 bc = *reinterpret_cast<const float4*>(&sm.Tb[q][tx * 4]);
+            const float a4[4] = {ar.x, ar.y, ar.z, ar.w}, b4[4] = {bc.x, bc.y, bc.z, bc.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(a4[u], b4[v], acc[u][v]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int r = ty * 4 + u, c = tx * 4 + v;
+            if (r < rb && c < jb) A[(int64_t)(r0 + r) + (int64_t)(j0 + c) * ld] -= acc[u][v];
+        }
+}
+
+// Left-looking blocked Cholesky of the FP32 matrix in S.L; false if a pivot is not positive.
+__device__ bool factor32(SmemM& sm, const SlotM& S, int k, int64_t ld) {
+    const int tid = threadIdx.x;
+    const int nb = (k + NB - 1) / NB;
+    for (int J = 0; J < nb; ++J) {
+        const int j0 = J * NB, jb = min(NB, k - j0);
+        if (j0 > 0) {
+            for (int R = J; R < nb; ++R) update_tile32(sm, S.L, ld, R * NB, min(NB, k - R * NB), j0, jb);
+            __syncthreads();
+        }
+        for (int e = tid; e < NB * NB; e += NT) {
+            const int r = e & (NB - 1), c = e >> 6;
+            if (r < jb && c <= r) sm.L[r][c] = S.L[(j0 + r) + (int64_t)(j0 + c) * ld];
+        }
+        if (tid == 0) sm.flag = 0;
+        __syncthreads();
+        for (int c = 0; c < jb; ++c) {
+            if (tid == 0) {
+                float s = sm.L[c][c];
+                for (int p = 0; p < c; ++p) s = fmaf(-sm.L[c][p], sm.L[c][p], s);
+                if (!(s > 0.0f)) { sm.flag = 1; s = 1.0f; }
+                const float d = sqrtf(s);
+                sm.L[c][c] = d;
+                sm.rinv[c] = 1.0f / d;
+            }
+            __syncthreads();
+            const float rd = sm.rinv[c];
+            for (int r = c + 1 + tid; r < jb; r += NT) {
+                float s = sm.L[r][c];
+                for (int p = 0; p < c; ++p) s = fmaf(-sm.L[r][p], sm.L[c][p], s);
+                sm.L[r][c] = s * rd;
+            }
+            __syncthreads();
+        }
+        if (sm.flag) return false;
+        for (int e = tid; e < NB * NB; e += NT) {
+            const int r = e & (NB - 1), c = e >> 6;
+            if (r < jb && c <= r) S.L[(j0 + r) + (int64_t)(j0 + c) * ld] = sm.L[r][c];
+        }
+        // rows below: x L_JJ^T = row, one row per thread, the row kept in registers
+        for (int r = j0 + jb + tid; r < k; r += NT) {
+            float x[NB];
+#pragma unroll
+            for (int c = 0; c < NB; ++c) x[c] = c < jb ? S.L[r + (int64_t)(j0 + c) * ld] : 0.0f;
+#pragma unroll
+            for (int c = 0; c < NB; ++c) {
+                float s = x[c];
+#pragma unroll
+                for (int p = 0; p < c; ++p) s = fmaf(-x[p], sm.L[c][p], s);
+                x[c] = c < jb ? s * sm.rinv[c] : 0.0f;
+            }
+#pragma unroll
+            for (int c = 0; c < NB; ++c)
+                if (c < jb) S.L[r + (int64_t)(j0 + c) * ld] = x[c];
+        }
+        __syncthreads();
+    }
+    return true;
+}
+
+// ---------------------------------------------------------------- FP32 triangular solves
+
+// w <- L^-1 w (column-oriented: diagonal block by one warp, rows below by all threads)
+__device__ void forward32(SmemM& sm, const float* L, int64_t ld, float* w, int k) {
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int nb = (k + NB - 1) / NB;
+    for (int J = 0; J < nb; ++J) {
+        const int j0 = J * NB, jb = min(NB, k - j0);
+        for (int e = tid; e < NB * NB; e += NT) {
+            const int r = e & (NB - 1), c = e >> 6;
+            if (r < jb && c <= r) sm.L[r][c] = L[(j0 + r) + (int64_t)(j0 + c) * ld];
+        }
+        __syncthreads();
+        if (tid < 32) {
+            float v0 = lane < jb ? w[j0 + lane] : 0.0f;
+            float v1 = lane + 32 < jb ? w[j0 + lane + 32] : 0.0f;
+            for (int c = 0; c < jb; ++c) {
+                const float vc = __shfl_sync(0xffffffffu, c < 32 ? v0 : v1, c & 31);
+                const float wc = vc / sm.L[c][c];
+                if (lane == (c & 31)) { if (c < 32) v0 = wc; else v1 = wc; }
+                if (lane > c && lane < jb) v0 = fmaf(-sm.L[lane][c], wc, v0);
+                if (lane + 32 > c && lane + 32 < jb) v1 = fmaf(-sm.L[lane + 32][c], wc, v1);
+            }
+            if (lane < jb) { w[j0 + lane] = v0; sm.wj[lane] = v0; }
+            if (lane + 32 < jb) { w[j0 + lane + 32] = v1; sm.wj[lane + 32] = v1; }
+        }
+        __syncthreads();
+        for (int r = j0 + jb + tid; r < k; r += NT) {
+            float s = 0.0f;
+            for (int c = 0; c < jb; ++c) s = fmaf(L[r + (int64_t)(j0 + c) * ld], sm.wj[c], s);
+            w[r] -= s;
+        }
+        __syncthreads();
+    }
+}
+
+// w <- L^-T w
+__device__ void backward32(SmemM& sm, const float* L, int64_t ld, float* w, int k) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nb = (k + NB - 1) / NB;
+    for (int J = nb - 1; J >= 0; --J) {
+        const int j0 = J * NB, jb = min(NB, k - j0);
+        for (int c = warp; c < jb; c += NT / 32) {
+            float s = 0.0f;
+            for (int p = j0 + jb + lane; p < k; p += 32) s = fmaf(L[p + (int64_t)(j0 + c) * ld], w[p], s);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0) sm.wj[c] = w[j0 + c] - s;
+        }
+        for (int e = tid; e < NB * NB; e += NT) {
+            const int r = e & (NB - 1), c = e >> 6;
+            if (r < jb && c <= r) sm.L[r][c] = L[(j0 + r) + (int64_t)(j0 + c) * ld];
+        }
+        __syncthreads();
+        if (tid < 32) {
+            float v0 = lane < jb ? sm.wj[lane] : 0.0f;
+            float v1 = lane + 32 < jb ? sm.wj[lane + 32] : 0.0f;
+            for (int c = jb - 1; c >= 0; --c) {
+                const float vc = __shfl_sync(0xffffffffu, c < 32 ? v0 : v1, c & 31);
+                const float xc = vc / sm.L[c][c];
+                if (lane == (c & 31)) { if (c < 32) v0 = xc; else v1 = xc; }
+                if (lane < c) v0 = fmaf(-sm.L[c][lane], xc, v0);
+                if (lane + 32 < c) v1 = fmaf(-sm.L[c][lane + 32], xc, v1);
+            }
+            if (lane < jb) w[j0 + lane] = v0;
+            if (lane + 32 < jb) w[j0 + lane + 32] = v1;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- double-float kernel entries
+
+struct Pt {
+    float xh, xl, yh, yl;
+};
+
+// t = ||p - q|| / rho in double-float; the high parts of both points lie on the
+// 2^-20 grid (|x| < 1), so their differences are exact
+__device__ __forceinline__ df t_grid(const Pt& p, const Pt& q, df inv_rho) {
+    const df dx = dfm::fast_two_sum(p.xh - q.xh, p.xl - q.xl);
+    const df dy = dfm::fast_two_sum(p.yh - q.yh, p.yl - q.yl);
+    const df sx = dfm::two_prod(dx.h, dx.h), sy = dfm::two_prod(dy.h, dy.h);
+    df d2 = dfm::two_sum(sx.h, sy.h);
+    d2.l += sx.l + sy.l + 2.0f * (dx.h * dx.l + dy.h * dy.l);
+    d2 = dfm::fast_two_sum(d2.h, d2.l);
+    return dfm::mul(dfm::sqrt_df(d2), inv_rho);
+}
+
+// same for arbitrary double-float points (prediction locations)
+__device__ __forceinline__ df t_any(const Pt& p, const Pt& q, df inv_rho) {
+    df dx = dfm::two_sum(p.xh, -q.xh);
+    dx = dfm::fast_two_sum(dx.h, dx.l + (p.xl - q.xl));
+    df dy = dfm::two_sum(p.yh, -q.yh);
+    dy = dfm::fast_two_sum(dy.h, dy.l + (p.yl - q.yl));
+    const df sx = dfm::two_prod(dx.h, dx.h), sy = dfm::two_prod(dy.h, dy.h);
+    df d2 = dfm::two_sum(sx.h, sy.h);
+    d2.l += sx.l + sy.l + 2.0f * (dx.h * dx.l + dy.h * dy.l);
+    d2 = dfm::fast_two_sum(d2.h, d2.l);
+    return dfm::mul(dfm::sqrt_df(d2), inv_rho);
+}
+
+__device__ __forceinline__ df exp_neg_sm(const SmemM& sm, df t) {
+    return dfm::exp_neg(t, sm.tbl, c_exp.inv_c, c_exp.c1, c_exp.c2, c_exp.c3);
+}
+
+// r = y - A x with A = Sigma + lambda I: double-float entries, one pass over the
+// lower triangle in 64 x 64 tiles, each entry feeding its row and its column.
+__device__ void residual_df(SmemM& sm, const SlotM& S, int k, df inv_rho, double lam) {
+    const int tid = threadIdx.x;
+    const int rg = tid >> 4, cg = tid & 15;   // 16 x 16 threads, 4 x 4 entries each
+    for (int a = tid; a < k; a += NT) { S.ah[a] = 0.0f; S.al[a] = 0.0f; }
+    __syncthreads();
+    const int nb = (k + NB - 1) / NB;
+    for (int I = 0; I < nb; ++I) {
+        Pt pa[4];
+        df xa[4];
+        dfm::acc racc[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int a = I * NB + rg * 4 + u;
+            const bool ok = a < k;
+            pa[u] = ok ? Pt{S.xh[a], S.xl[a], S.yh[a], S.yl[a]} : Pt{0, 0, 0, 0};
+            xa[u] = ok ? df{S.qh[a], S.ql[a]} : df{0, 0};
+        }
+        for (int J = 0; J <= I; ++J) {
+            Pt pb[4];
+            df xb[4];
+            dfm::acc cacc[4];
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const int b = J * NB + cg * 4 + v;
+                const bool ok = b < k;
+                pb[v] = ok ? Pt{S.xh[b], S.xl[b], S.yh[b], S.yl[b]} : Pt{0, 0, 0, 0};
+                xb[v] = ok ? df{S.qh[b], S.ql[b]} : df{0, 0};
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    const int a = I * NB + rg * 4 + u, b = J * NB + cg * 4 + v;
+                    if (a < k && b < k && (I != J || a > b)) {
+                        const df e = exp_neg_sm(sm, t_grid(pa[u], pb[v], inv_rho));
+                        racc[u].add_prod(e, xb[v]);
+                        cacc[v].add_prod(e, xa[u]);
+                    }
+                }
+            // column sums of this tile -> columns of block J
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const df c = cacc[v].value();
+                sm.ph[rg][cg * 4 + v] = c.h;
+                sm.pl[rg][cg * 4 + v] = c.l;
+            }
+            __syncthreads();
+            if (tid < NB) {
+                const int b = J * NB + tid;
+                if (b < k) {
+                    dfm::acc s;
+                    s.add_df(df{S.ah[b], S.al[b]});
+                    for (int g = 0; g < 16; ++g) s.add_df(df{sm.ph[g][tid], sm.pl[g][tid]});
+                    const df v = s.value();
+                    S.ah[b] = v.h;
+                    S.al[b] = v.l;
+                }
+            }
+            __syncthreads();
+        }
+        // row sums of block row I
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const df r = racc[u].value();
+            sm.ph[cg][rg * 4 + u] = r.h;
+            sm.pl[cg][rg * 4 + u] = r.l;
+        }
+        __syncthreads();
+        if (tid < NB) {
+            const int a = I * NB + tid;
+            if (a < k) {
+                dfm::acc s;
+                s.add_df(df{S.ah[a], S.al[a]});
+                for (int g = 0; g < 16; ++g) s.add_df(df{sm.ph[g][tid], sm.pl[g][tid]});
+                const df v = s.value();
+                S.ah[a] = v.h;
+                S.al[a] = v.l;
+            }
+        }
+        __syncthreads();
+    }
+    // diagonal (1 + lambda) x and the residual, O(k) FP64 operations
+    for (int a = tid; a < k; a += NT)
+        S.rr[a] = S.yv[a] - ((double)S.ah[a] + (double)S.al[a] + (1.0 + lam) * S.xs[a]);
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------- one task
+
+__device__ void run_task(SmemM& sm, const TaskArgs& a, int t, int i, int b) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const double s2 = a.params[3 * b], rho = a.params[3 * b + 1], tau2 = a.params[3 * b + 2];
+    const int64_t zoff = (int64_t)b * a.N + i;
+    const int64_t p0 = a.P_off[i];
+    const int m = (int)(a.P_off[i + 1] - p0);
+    const bool bad = !(s2 > 0.0) || !(rho > 0.0) || !(tau2 >= 0.0) || !isfinite(s2) || !isfinite(rho) || !isfinite(tau2);
+    if (bad) {
+        if (a.yhat)
+            for (int j = tid; j < m; j += NT) a.yhat[(int64_t)b * a.yhat_stride + p0 + j] = NAN;
+        if (tid == 0) { a.z[zoff] = NAN; a.tstatus[zoff] = PCV_ERR_ARG; }
+        return;
+    }
+    const double lam = tau2 / s2;
+    const int64_t t0 = a.T_off[i];
+    const int k = (int)(a.T_off[i + 1] - t0);
+    const int64_t ld = a.ld;
+    const SlotM S = slot_of(a);
+    const double sc = a.coord_scale;
+    const double inv_rho_s = 1.0 / (rho * sc);      // distances are measured in scaled units
+    const df inv_rho = dfm::from_double(inv_rho_s);
+    const float inv_rho32 = (float)inv_rho_s;
+    const double ox = k > 0 ? a.X[a.T_idx[t0]] : 0.0, oy = k > 0 ? a.Y[a.T_idx[t0]] : 0.0;
+
+    // gather: scaled offsets, high parts on the 2^-20 grid
+    for (int q = tid; q < k; q += NT) {
+        const int g = a.T_idx[t0 + q];
+        const double dx = (a.X[g] - ox) * sc, dy = (a.Y[g] - oy) * sc;
+        const double hx = rint(dx * QSCALE) / QSCALE, hy = rint(dy * QSCALE) / QSCALE;
+        S.xh[q] = (float)hx;
+        S.xl[q] = (float)(dx - hx);
+        S.yh[q] = (float)hy;
+        S.yl[q] = (float)(dy - hy);
+        S.yv[q] = a.Vals[g];
+        S.xs[q] = 0.0;
+        S.rr[q] = a.Vals[g];
+    }
+    __syncthreads();
+
+    // FP32 lower triangle of Sigma + lambda I
+    const float lam32 = (float)lam;
+    const int nb = (k + NB - 1) / NB;
+    for (int bj = 0; bj < nb; ++bj)
+        for (int bi = bj; bi < nb; ++bi)
+            for (int e = tid; e < NB * NB; e += NT) {
+                const int r = bi * NB + (e & (NB - 1)), c = bj * NB + (e >> 6);
+                if (r < k && c <= r) {
+                    float v = 1.0f + lam32;
+                    if (r != c) {
+                        const float dx = (S.xh[r] - S.xh[c]) + (S.xl[r] - S.xl[c]);
+                        const float dy = (S.yh[r] - S.yh[c]) + (S.yl[r] - S.yl[c]);
+                        v = __expf(-sqrtf(fmaf(dx, dx, dy * dy)) * inv_rho32);
+                    }
+                    S.L[r + (int64_t)c * ld] = v;
+                }
+            }
+    __syncthreads();
+
+    bool ok = factor32(sm, S, k, ld);
+    __syncthreads();
+    if (ok) {
+        // iterative refinement: x += L^-T L^-1 r
+        ok = false;
+        for (int it = 0; it <= a.refine_max_iter; ++it) {
+            for (int q = tid; q < k; q += NT) S.w[q] = (float)S.rr[q];
+            __syncthreads();
+            forward32(sm, S.L, ld, S.w, k);
+            backward32(sm, S.L, ld, S.w, k);
+            float dmax = 0.0f, xmax = 0.0f;
+            for (int q = tid; q < k; q += NT) {
+                const double xn = S.xs[q] + (double)S.w[q];
+                S.xs[q] = xn;
+                dmax = fmaxf(dmax, fabsf(S.w[q]));
+                xmax = fmaxf(xmax, fabsf((float)xn));
+            }
+            dmax = block_max(sm, dmax);
+            xmax = block_max(sm, xmax);
+            if (!(dmax == dmax) || !(xmax == xmax)) break;            // NaN: give up
+            if (it >= 1 && dmax <= (float)a.refine_tol * xmax) { ok = true; break; }
+            if (it >= 1 && dmax > 0.5f * xmax) break;                  // not contracting
+            if (it == a.refine_max_iter) break;
+            for (int q = tid; q < k; q += NT) {
+                const df v = dfm::from_double(S.xs[q]);
+                S.qh[q] = v.h;
+                S.ql[q] = v.l;
+            }
+            __syncthreads();
+            residual_df(sm, S, k, inv_rho, lam);
+        }
+        if (k == 0) ok = true;
+    }
+    if (!ok) {
+        // hand the task to the FP64 kernel
+        if (tid == 0) {
+            a.tstatus[zoff] = PCV_REFINE_FALLBACK;
+            const unsigned pos = atomicAdd(a.fb_count, 1u);
+            a.fb_list[pos] = t;
+        }
+        __syncthreads();
+        return;
+    }
+
+    // predict (Eq. 3) in double-float, squared errors in FP64 (Eq. 4)
+    for (int q = tid; q < k; q += NT) {
+        const df v = dfm::from_double(S.xs[q]);
+        S.qh[q] = v.h;
+        S.ql[q] = v.l;
+    }
+    __syncthreads();
+    for (int j = warp; j < m; j += NT / 32) {
+        const df px = dfm::from_double((a.Px[p0 + j] - ox) * sc), py = dfm::from_double((a.Py[p0 + j] - oy) * sc);
+        const Pt P{px.h, px.l, py.h, py.l};
+        dfm::acc s;
+        for (int q = lane; q < k; q += 32) {
+            const Pt Q{S.xh[q], S.xl[q], S.yh[q], S.yl[q]};
+            s.add_prod(exp_neg_sm(sm, t_any(P, Q, inv_rho)), df{S.qh[q], S.ql[q]});
+        }
+        double v = (double)s.h + (double)s.l;
+        v = warp_sum_d(v);
+        if (lane == 0) {
+            if (a.yhat) a.yhat[(int64_t)b * a.yhat_stride + p0 + j] = v;
+            if (a.Pv) {
+                const double e = v - a.Pv[p0 + j];
+                S.ep[j] = e * e;
+            }
+        }
+    }
+    __syncthreads();
+    if (a.Pv) {
+        double s = 0.0;
+        for (int j = tid; j < m; j += NT) s += S.ep[j];
+        s = warp_sum_d(s);
+        if (lane == 0) sm.dred[warp] = s;
+        __syncthreads();
+        if (tid == 0) {
+            double zz = 0.0;
+            for (int w = 0; w < NT / 32; ++w) zz += sm.dred[w];
+            a.z[zoff] = zz;
+        }
+    }
+    if (tid == 0) a.tstatus[zoff] = PCV_OK;
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(NT, 2) k_cv_mixed(TaskArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SmemM& sm = *reinterpret_cast<SmemM*>(smem_raw);
+    for (int e = threadIdx.x; e < 2 * dfm::kExpTable; e += NT) sm.tbl[e] = c_exp.tbl[e];
+    __syncthreads();
+    const int ntask = a.n_order * a.B;
+    for (;;) {
+        if (threadIdx.x == 0) sm.task = (int)atomicAdd(a.counter, 1u);
+        __syncthreads();
+        const int t = sm.task;
+        __syncthreads();
+        if (t >= ntask) break;
+        run_task(sm, a, t, a.order[t / a.B], t % a.B);
+    }
+}
+
+std::mutex g_prep_mu;
+bool g_prepared[64] = {false};
+
+}  // namespace
+
+int64_t slot_bytes_mixed(int32_t ld, int64_t mmax) {
+    const int64_t b = (int64_t)ld * ld * 4 + 3 * (int64_t)ld * 8 + 9 * (int64_t)ld * 4 + (mmax + 32) * 8;
+    return (b + 255) / 256 * 256;
+}
+
+int mixed_prepare(int device) {
+    std::lock_guard<std::mutex> lk(g_prep_mu);
+    if (device < 0 || device >= 64) return (int)cudaErrorInvalidDevice;
+    if (g_prepared[device]) return 0;
+    dfm::ExpConsts k;
+    dfm::exp_constants(k);
+    cudaError_t e = cudaMemcpyToSymbol(c_exp, &k, sizeof(k));
+    if (e != cudaSuccess) return (int)e;
+    e = cudaFuncSetAttribute(k_cv_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SmemM));
+    if (e != cudaSuccess) return (int)e;
+    g_prepared[device] = true;
+    return 0;
+}
+
+int launch_task_mixed(const TaskArgs& a, int grid, void* stream) {
+    k_cv_mixed<<<grid, NT, sizeof(SmemM), (cudaStream_t)stream>>>(a);
+    count_launch();
+    return (int)cudaGetLastError();
+}
+
 }  // namespace pcv

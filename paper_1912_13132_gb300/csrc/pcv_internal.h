@@ -56,6 +56,14 @@ struct TaskArgs {
     int32_t ld;             // leading dimension of the slot matrix (multiple of 128)
     int32_t refine_max_iter;
     double refine_tol;
+    double coord_scale;     // power of two: scaled offsets inside one window are below 1 in magnitude
+    // mixed path: tasks that need the FP64 fallback are appended here
+    int32_t* fb_list;
+    unsigned int* fb_count;
+    // FP64 path in list mode: run only the tasks task_list[0 .. *task_count)
+    const int32_t* task_list;
+    const unsigned int* task_count;
+    int32_t list_status;    // status written for a task finished in list mode
 };
 
 // Kernel launchers (one per precision); return the cudaError_t as int.

@@ -70,6 +70,8 @@ _SIGS = {
     "pcv_kernel_time": (ctypes.c_int, [_vp, _dp, _dp]),
     "pcv_cv_loss_fp64_static": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int32, _i64p, _vp, _i64p, _vp, _vp,
                                                _vp, _vp, ctypes.c_int32, _vp, _vp, _vp, _vp]),
+    "pcv_selftest_df": (ctypes.c_int, [ctypes.c_int32, _dp, _dp, ctypes.c_int64, _dp]),
+    "pcv_selftest_df_device": (ctypes.c_int, [ctypes.c_int32, _vp, _vp, ctypes.c_int64, _vp, _vp]),
     "pcv_destroy": (None, [_vp]),
     "pcv_status_str": (ctypes.c_char_p, [ctypes.c_int32]),
     "pcv_last_error": (ctypes.c_char_p, []),
@@ -288,6 +290,26 @@ def pcv_cv_loss_fp64_static(d_x, d_y, d_v, T_off, d_T_idx, V_off, d_Vx, d_Vy, d_
         ptr(d_x), ptr(d_y), ptr(d_v), len(T_off) - 1, _ptr(T_off, _i64p), ptr(d_T_idx), _ptr(V_off, _i64p),
         ptr(d_Vx), ptr(d_Vy), ptr(d_Vv), ptr(d_params), int(d_params.shape[0]), ptr(d_sspe),
         ptr(d_sspe_per_subset), ptr(d_status), _stream_ptr(stream)))
+
+
+DF_OPS = {"exp_neg": 0, "sqrt": 1, "mul": 2, "add": 3}
+
+
+def pcv_selftest_df(op: str, a, b=None) -> np.ndarray:
+    """Host evaluation of a double-float primitive (see include/pcv.h)."""
+    a = _f64(a)
+    bb = _f64(b) if b is not None else None
+    out = np.empty(len(a))
+    _check(_lib.pcv_selftest_df(DF_OPS[op], _ptr(a, _dp), _ptr(bb, _dp) if bb is not None else None, len(a),
+                                _ptr(out, _dp)), "pcv_selftest_df")
+    return out
+
+
+def pcv_selftest_df_device(op: str, d_a, d_b, d_out, stream=None):
+    """Device evaluation on torch CUDA tensors."""
+    _check(_lib.pcv_selftest_df_device(DF_OPS[op], d_a.data_ptr(), d_b.data_ptr() if d_b is not None else None,
+                                       int(d_a.numel()), d_out.data_ptr(), _stream_ptr(stream)),
+           "pcv_selftest_df_device")
 
 
 def pcv_launch_count(reset: bool = False) -> int:
