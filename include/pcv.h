@@ -239,6 +239,14 @@ pcv_status pcv_selftest_df(int32_t op, const double* a, const double* b, int64_t
 pcv_status pcv_selftest_df_device(int32_t op, const double* d_a, const double* d_b, int64_t n,
                                   double* d_out, void* stream);
 
+/* The tensor-core building block of the mixed path's factorisation on its own:
+ * C (M x 128, row-major) = A (M x K, row-major) * B (128 x K, row-major)^T with
+ * A and B split into three BF16 terms each and six tcgen05 products accumulated
+ * in FP32 (TMA-loaded tiles, TMEM accumulators).  K must be a positive multiple
+ * of 32.  Host arrays; allocates and frees its own device buffers; synchronous.
+ * PCV_ERR_TIMEOUT if one of the kernel's bounded waits ran out. */
+pcv_status pcv_selftest_umma(const float* A, int32_t M, const float* B, int32_t K, float* C);
+
 /* ----------------------------------------------------------------- utilities */
 const char* pcv_status_str(int32_t status);
 const char* pcv_last_error(void);

@@ -49,3 +49,134 @@ PCV_API pcv_status pcv_selftest_df_device(int32_t op, const double* d_a, const d
     pcv::count_launch();
     return cudaGetLastError() == cudaSuccess ? PCV_OK : PCV_ERR_CUDA;
 }
+
+// ---------------------------------------------------------------- tensor-core pipeline self-test
+#include <cudaTypedefs.h>
+
+#include <vector>
+
+#include "umma.cuh"
+
+namespace {
+
+__global__ void k_split(const float* x, int64_t n, __nv_bfloat16* p0, __nv_bfloat16* p1, __nv_bfloat16* p2) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) pcv::umma::split3(x[i], p0[i], p1[i], p2[i]);
+}
+
+struct UmmaTestSmem {
+    pcv::umma::Pipe pipe;
+    int err;
+};
+
+__global__ void __launch_bounds__(256, 1) k_umma_test(const __grid_constant__ CUtensorMap m0,
+                                                      const __grid_constant__ CUtensorMap m1,
+                                                      const __grid_constant__ CUtensorMap m2, int M, int K, float* C,
+                                                      int* err) {
+    using namespace pcv::umma;
+    extern __shared__ __align__(1024) unsigned char raw[];
+    uint8_t* base = (uint8_t*)(((uintptr_t)raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* stages = base;
+    UmmaTestSmem& sm = *reinterpret_cast<UmmaTestSmem*>(base + kStages * kStageBytes);
+    const int warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) {
+        pipe_init(sm.pipe);
+        sm.err = 0;
+        prefetch_map(&m0);
+        prefetch_map(&m1);
+        prefetch_map(&m2);
+    }
+    if (warp == 1) tmem_alloc(&sm.pipe.tmem_base, kTmemCols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    Phases ph;
+    auto epi = [&](int row0, int quad, uint32_t taddr) {
+        const int r = row0 - kTileM + quad * 32 + (threadIdx.x & 31);   // A rows start at plane row 128
+        for (int c0 = 0; c0 < kTileN; c0 += 32) {
+            float v[32];
+            tmem_ld32(taddr + c0, v);
+            if (r < M)
+                for (int j = 0; j < 32; ++j) C[(int64_t)r * kTileN + c0 + j] = v[j];
+        }
+    };
+    // two calls in a row to exercise the phase bookkeeping across block columns
+    for (int rep = 0; rep < 2; ++rep) {
+        const bool ok = block_column(sm.pipe, ph, stages, &m0, &m1, &m2, 0, kTileM, M, 0, K, epi);
+        if (!ok) atomicExch(&sm.err, 1);
+        __syncthreads();
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) tmem_dealloc(sm.pipe.tmem_base, kTmemCols);
+    if (threadIdx.x == 0) *err = sm.err;
+}
+
+bool make_map(CUtensorMap* map, void* base, uint64_t inner, uint64_t rows) {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        cudaDriverEntryPointQueryResult q;
+        void* fn = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn)
+            return false;
+        encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    }
+    cuuint64_t dims[2] = {inner, rows};
+    cuuint64_t strides[1] = {inner * 2};
+    cuuint32_t box[2] = {(cuuint32_t)pcv::umma::kChunkK, (cuuint32_t)pcv::umma::kTileM};
+    cuuint32_t estr[2] = {1, 1};
+    return encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+// C (M x 128, row-major) = A (M x K) * B (128 x K)^T through the split-BF16 tensor-core
+// pipeline; K a positive multiple of 32.  Host arrays.  Returns PCV_ERR_TIMEOUT if a
+// bounded wait ran out inside the kernel.
+PCV_API pcv_status pcv_selftest_umma(const float* A, int32_t M, const float* B, int32_t K, float* C) {
+    using namespace pcv::umma;
+    if (!A || !B || !C || M < 1 || K < kChunkK || K % kChunkK) return PCV_ERR_ARG;
+    const int Mp = (M + kTileM - 1) / kTileM * kTileM;
+    const int64_t rows = kTileM + Mp;
+    std::vector<float> X((size_t)rows * K, 0.0f);
+    for (int r = 0; r < kTileM; ++r)
+        for (int k = 0; k < K; ++k) X[(size_t)r * K + k] = B[(size_t)r * K + k];
+    for (int r = 0; r < M; ++r)
+        for (int k = 0; k < K; ++k) X[(size_t)(kTileM + r) * K + k] = A[(size_t)r * K + k];
+    float *dX = nullptr, *dC = nullptr;
+    __nv_bfloat16* dP = nullptr;
+    int* dErr = nullptr;
+    const int64_t n = rows * K;
+    pcv_status st = PCV_OK;
+    if (cudaMalloc(&dX, n * 4) || cudaMalloc(&dP, 3 * n * 2) || cudaMalloc(&dC, (size_t)M * kTileN * 4) ||
+        cudaMalloc(&dErr, 4)) {
+        st = PCV_ERR_OOM;
+    } else {
+        cudaMemcpy(dX, X.data(), n * 4, cudaMemcpyHostToDevice);
+        k_split<<<(unsigned)((n + 255) / 256), 256>>>(dX, n, dP, dP + n, dP + 2 * n);
+        CUtensorMap m[3];
+        bool ok = true;
+        for (int p = 0; p < 3; ++p) ok = ok && make_map(&m[p], dP + p * n, (uint64_t)K, (uint64_t)rows);
+        if (!ok) {
+            st = PCV_ERR_CUDA;
+        } else {
+            const int smem = kStages * kStageBytes + (int)sizeof(UmmaTestSmem) + 1024;
+            cudaFuncSetAttribute(k_umma_test, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            k_umma_test<<<1, 256, smem>>>(m[0], m[1], m[2], M, K, dC, dErr);
+            pcv::count_launch(2);
+            int herr = 0;
+            if (cudaMemcpy(&herr, dErr, 4, cudaMemcpyDeviceToHost) != cudaSuccess) st = PCV_ERR_CUDA;
+            else if (herr) st = PCV_ERR_TIMEOUT;
+            else if (cudaMemcpy(C, dC, (size_t)M * kTileN * 4, cudaMemcpyDeviceToHost) != cudaSuccess) st = PCV_ERR_CUDA;
+        }
+    }
+    cudaFree(dX);
+    cudaFree(dP);
+    cudaFree(dC);
+    cudaFree(dErr);
+    return st;
+}

@@ -1,0 +1,306 @@
+// umma.cuh -- Blackwell (sm_100a family) tensor-core building blocks in inline PTX:
+// TMEM allocation, tcgen05.mma (kind::f16, BF16 inputs, FP32 accumulators), TMA
+// tile loads, mbarriers with bounded waits, and the warp-specialised pipeline that
+// computes one block-column product
+//
+//     D[rows r0 .. r0+nr, 0 .. 128) = sum over K of A[r, K] * B[c, K]      (K-major)
+//
+// with A and B given as three BF16 planes each (x = hi + mid + lo, each term the
+// BF16 rounding of what the previous terms leave, see split3), so that the six products
+// hi*hi + hi*mid + mid*hi + hi*lo + lo*hi + mid*mid reproduce FP32-accurate
+// products while running on the BF16 tensor pipe.
+//
+// Roles (256 threads):  warp 0 lane 0 issues TMA loads into a 2-stage ring,
+// warp 1 lane 0 issues the MMAs, warps 4..7 (one per TMEM lane quadrant) drain the
+// accumulators through the caller's epilogue.  Two 128-row tiles form one pass;
+// the accumulators of consecutive passes alternate between two TMEM buffers so the
+// epilogue of one pass overlaps the MMAs of the next.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace pcv {
+namespace umma {
+
+constexpr int kTileM = 128;        // rows per tile (MMA M)
+constexpr int kTileN = 128;        // block-column width (MMA N)
+constexpr int kChunkK = 32;        // BF16 elements per TMA box row (64 bytes, 64B swizzle)
+constexpr int kPlanes = 3;
+constexpr int kTilesPerPass = 2;
+constexpr int kStages = 2;
+constexpr int kTileBytes = kTileM * kChunkK * 2;                    // 8 KB
+constexpr int kStageBytes = kPlanes * (kTilesPerPass + 1) * kTileBytes;   // 72 KB
+constexpr uint32_t kTmemCols = 512;
+constexpr uint64_t kWaitNs = 2000000000ull;  // bound of every mbarrier wait (2 s)
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// ---------------------------------------------------------------- mbarriers
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Wait for the phase with the given parity to complete; false once kWaitNs of wall
+// time have passed without it (the caller then reports an error instead of hanging).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    if (mbar_try(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (;;) {
+        for (int i = 0; i < 64; ++i)
+            if (mbar_try(bar, parity)) return true;
+        if (global_ns() - t0 > kWaitNs) return false;
+    }
+}
+
+// ---------------------------------------------------------------- TMA
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int c0, int c1, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_u32(dst)),
+        "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void prefetch_map(const CUtensorMap* map) {
+    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)map) : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// ---------------------------------------------------------------- TMEM and MMA
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst_smem, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst_smem)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand tile written by TMA with 64-byte
+// swizzle (rows of 64 bytes, 8-row groups 512 bytes apart).
+__device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t addr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3FFF);            // start address
+    d |= (uint64_t)1 << 16;                           // leading-dimension byte offset (unused here)
+    d |= (uint64_t)((512 >> 4) & 0x3FFF) << 32;       // stride-dimension byte offset: 8 rows x 64 B
+    d |= (uint64_t)1 << 46;                           // descriptor version
+    d |= (uint64_t)4 << 61;                           // 64-byte swizzle
+    return d;
+}
+
+// Instruction descriptor: kind::f16, A = B = BF16, D = FP32, both K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+// 32 lanes x 32 columns of FP32 from TMEM (one register per column).
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// ---------------------------------------------------------------- BF16 splitting
+
+// x = hi + mid + lo with each term the round-to-nearest BF16 of what is left; the
+// three terms carry 24 significant bits, the representation error is <= 2^-24 |x|.
+__device__ __forceinline__ void split3(float x, __nv_bfloat16& h, __nv_bfloat16& m, __nv_bfloat16& l) {
+    h = __float2bfloat16_rn(x);
+    const float r1 = x - __bfloat162float(h);
+    m = __float2bfloat16_rn(r1);
+    const float r2 = r1 - __bfloat162float(m);
+    l = __float2bfloat16_rn(r2);
+}
+
+// ---------------------------------------------------------------- pipeline state
+
+struct Pipe {
+    uint64_t full[kStages];
+    uint64_t empty[kStages];
+    uint64_t accf[2];
+    uint64_t acce[2];
+    uint32_t tmem_base;
+    uint32_t pad;
+};
+
+// Per-role phase counters; every role walks the same sequence of stages and passes.
+struct Phases {
+    uint32_t stage = 0;   // stage iterations done (ring position and parity)
+    uint32_t pass = 0;    // passes done (accumulator buffer and parity)
+};
+
+__device__ inline void pipe_init(Pipe& p) {
+    for (int s = 0; s < kStages; ++s) {
+        mbar_init(&p.full[s], 1);
+        mbar_init(&p.empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+        mbar_init(&p.accf[b], 1);
+        mbar_init(&p.acce[b], 4);   // one arrive per epilogue warp
+    }
+    fence_mbar_init();
+}
+
+// The six plane products (A plane, B plane): hi*hi, hi*mid, mid*hi, hi*lo, lo*hi, mid*mid.
+__host__ __device__ constexpr int prod_a(int q) { return q == 2 ? 1 : q == 4 ? 2 : q == 5 ? 1 : 0; }
+__host__ __device__ constexpr int prod_b(int q) { return q == 1 ? 1 : q == 3 ? 2 : q == 5 ? 1 : 0; }
+
+// One block-column product over all row tiles:
+//   rows [r0, r0 + nrows) of A against rows [b0, b0 + 128) of B over K in [0, K),
+//   K a multiple of kChunkK.  A and B rows live in the planes' tensor maps at row
+//   offset `row_base` (the task's slot).  For each finished 128-row tile the
+//   epilogue warps call epi(tile_row0, warp_quadrant, taddr_of_tile) and must read
+//   all 128 columns of their 32 lanes.  Returns false if a bounded wait ran out.
+template <class Epi>
+__device__ bool block_column(Pipe& P, Phases& ph, uint8_t* stages, const CUtensorMap* mapA0,
+                             const CUtensorMap* mapA1, const CUtensorMap* mapA2, int row_base, int r0,
+                             int nrows, int b0, int K, Epi&& epi) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ntiles = (nrows + kTileM - 1) / kTileM;
+    const int npass = (ntiles + kTilesPerPass - 1) / kTilesPerPass;
+    const int nk = K / kChunkK;
+    const CUtensorMap* maps[3] = {mapA0, mapA1, mapA2};
+    bool ok = true;
+    if (warp == 0 && lane == 0) {
+        // TMA producer
+        uint32_t it = ph.stage;
+        for (int p = 0; p < npass && ok; ++p) {
+            const int t0 = p * kTilesPerPass;
+            const int nt = min(kTilesPerPass, ntiles - t0);
+            for (int kc = 0; kc < nk; ++kc, ++it) {
+                const int s = it % kStages;
+                const uint32_t par = ((it / kStages) & 1) ^ 1;
+                if (!mbar_wait(&P.empty[s], par)) { ok = false; break; }
+                uint8_t* st = stages + s * kStageBytes;
+                mbar_expect_tx(&P.full[s], (uint32_t)(kPlanes * (nt + 1) * kTileBytes));
+                for (int pl = 0; pl < kPlanes; ++pl) {
+                    tma_load_2d(st + pl * kTileBytes, maps[pl], kc * kChunkK, row_base + b0, &P.full[s]);
+                    for (int t = 0; t < nt; ++t)
+                        tma_load_2d(st + (kPlanes + t * kPlanes + pl) * kTileBytes, maps[pl], kc * kChunkK,
+                                    row_base + r0 + (t0 + t) * kTileM, &P.full[s]);
+                }
+            }
+        }
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer
+        uint32_t it = ph.stage;
+        const uint32_t idesc = idesc_bf16(kTileM, kTileN);
+        for (int p = 0; p < npass && ok; ++p) {
+            const int t0 = p * kTilesPerPass;
+            const int nt = min(kTilesPerPass, ntiles - t0);
+            const uint32_t pp = ph.pass + p;
+            const int buf = pp & 1;
+            if (!mbar_wait(&P.acce[buf], ((pp >> 1) & 1) ^ 1)) { ok = false; break; }
+            tc_fence_after();
+            for (int kc = 0; kc < nk; ++kc, ++it) {
+                const int s = it % kStages;
+                if (!mbar_wait(&P.full[s], (it / kStages) & 1)) { ok = false; break; }
+                tc_fence_after();
+                const uint32_t st = smem_u32(stages + s * kStageBytes);
+                for (int t = 0; t < nt; ++t) {
+                    const uint32_t d = P.tmem_base + buf * (kTilesPerPass * kTileN) + t * kTileN;
+#pragma unroll
+                    for (int kk = 0; kk < kChunkK / 16; ++kk)
+#pragma unroll
+                        for (int q = 0; q < 6; ++q) {
+                            const uint32_t a = st + (kPlanes + t * kPlanes + prod_a(q)) * kTileBytes + kk * 32;
+                            const uint32_t b = st + prod_b(q) * kTileBytes + kk * 32;
+                            mma_bf16(d, smem_desc_sw64(a), smem_desc_sw64(b), idesc,
+                                     (kc > 0 || kk > 0 || q > 0) ? 1u : 0u);
+                        }
+                }
+                mma_commit(&P.empty[s]);
+            }
+            if (ok) mma_commit(&P.accf[buf]);
+        }
+    } else if (warp >= 4) {
+        // epilogue: one warp per TMEM lane quadrant
+        const int quad = warp & 3;
+        for (int p = 0; p < npass && ok; ++p) {
+            const int t0 = p * kTilesPerPass;
+            const int nt = min(kTilesPerPass, ntiles - t0);
+            const uint32_t pp = ph.pass + p;
+            const int buf = pp & 1;
+            if (!mbar_wait(&P.accf[buf], (pp >> 1) & 1)) { ok = false; break; }
+            tc_fence_after();
+            for (int t = 0; t < nt; ++t) {
+                const uint32_t taddr = P.tmem_base + ((uint32_t)(quad * 32) << 16) +
+                                       buf * (kTilesPerPass * kTileN) + t * kTileN;
+                epi(r0 + (t0 + t) * kTileM, quad, taddr);
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&P.acce[buf]);
+        }
+    }
+    // every role advances its counters identically (the producer and MMA counts
+    // follow from the shape alone)
+    ph.stage += (uint32_t)(npass > 0 ? npass * nk : 0);
+    ph.pass += (uint32_t)npass;
+    return ok;
+}
+
+}  // namespace umma
+}  // namespace pcv

@@ -72,6 +72,9 @@ _SIGS = {
                                                _vp, _vp, ctypes.c_int32, _vp, _vp, _vp, _vp]),
     "pcv_selftest_df": (ctypes.c_int, [ctypes.c_int32, _dp, _dp, ctypes.c_int64, _dp]),
     "pcv_selftest_df_device": (ctypes.c_int, [ctypes.c_int32, _vp, _vp, ctypes.c_int64, _vp, _vp]),
+    "pcv_selftest_umma": (ctypes.c_int, [ctypes.POINTER(ctypes.c_float), ctypes.c_int32,
+                                         ctypes.POINTER(ctypes.c_float), ctypes.c_int32,
+                                         ctypes.POINTER(ctypes.c_float)]),
     "pcv_destroy": (None, [_vp]),
     "pcv_status_str": (ctypes.c_char_p, [ctypes.c_int32]),
     "pcv_last_error": (ctypes.c_char_p, []),
@@ -310,6 +313,18 @@ def pcv_selftest_df_device(op: str, d_a, d_b, d_out, stream=None):
     _check(_lib.pcv_selftest_df_device(DF_OPS[op], d_a.data_ptr(), d_b.data_ptr() if d_b is not None else None,
                                        int(d_a.numel()), d_out.data_ptr(), _stream_ptr(stream)),
            "pcv_selftest_df_device")
+
+
+def pcv_selftest_umma(A, B):
+    """C = A @ B.T (B has 128 rows) through the split-BF16 tcgen05 pipeline; returns (status, C)."""
+    A = np.ascontiguousarray(A, dtype=np.float32)
+    B = np.ascontiguousarray(B, dtype=np.float32)
+    assert B.shape[0] == 128 and A.shape[1] == B.shape[1]
+    C = np.zeros((A.shape[0], 128), dtype=np.float32)
+    fp = ctypes.POINTER(ctypes.c_float)
+    st = _lib.pcv_selftest_umma(A.ctypes.data_as(fp), A.shape[0], B.ctypes.data_as(fp), A.shape[1],
+                                C.ctypes.data_as(fp))
+    return int(st), C
 
 
 def pcv_launch_count(reset: bool = False) -> int:

@@ -128,3 +128,34 @@ def test_sigma2_invariance_gpu(gpu_lib):
     with gpu_lib.Context(w.xy, w.v, w.role, w.layout) as ctx:
         s = ctx.cv_loss(P, precision="fp64")["sspe"]
     assert np.all(rel(s, s[0]) <= 1e-12)
+
+
+@pytest.fixture(scope="module")
+def paper5m():
+    return datagen.config_paper_5m()
+
+
+@pytest.mark.parametrize("prec,B", [("mixed", 8), ("fp64", 1)])
+def test_paper_scale_sampled(gpu_lib, paper5m, prec, B):
+    """The benchmark's own workload and launch configuration (4,999,696-node grid,
+    10% missing, 80/10/10 split, 40 x 40 cores, shell 0.001, batch of B
+    configurations): every configuration's total is checked for status and
+    finiteness; per-subset losses and predictions are compared with the oracle on
+    sampled subsets (a corner, an edge, the largest, random interior ones)."""
+    w = paper5m
+    P = w.params[np.arange(B) * 23 % len(w.params)]
+    with gpu_lib.Context(w.xy, w.v, w.role, w.layout) as ctx:
+        out = ctx.cv_loss(P, precision=prec, per_subset=True, predictions=True)
+        T_off, V_off = ctx.T_off.copy(), ctx.V_off.copy()
+    assert np.all(out["status"] == 0), out["status"]
+    assert np.all(np.isfinite(out["sspe"]))
+    k = np.diff(T_off)
+    nx = w.layout["nx"]
+    pick = sorted(set([0, nx - 1, nx * nx - 1, nx // 2, int(np.argmax(k))] +
+                      np.random.default_rng(5).choice(nx * nx, 3, replace=False).tolist()))
+    cores = oracle.layout_cores(w.layout)
+    members = {i: oracle.subset_members(w.xy, w.role, w.layout, i, cores) for i in pick}
+    for b in range(0, B, max(1, B // 2)):
+        ref = oracle.cv_loss(w.xy, w.v, w.role, w.layout, P[b:b + 1], members=members, subsets=pick)
+        sub = dict(z=out["z"][b:b + 1], yhat=out["yhat"][b:b + 1], sspe=out["sspe"][b:b + 1])
+        compare(sub, ref, V_off, pick, 1, prec, check_total=False)
