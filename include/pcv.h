@@ -103,6 +103,8 @@ typedef struct {
     double refine_tol;         /* mixed path: stop once a correction d satisfies
                                   ||d||_inf <= tol * ||x||_inf (default 1e-6); tasks that
                                   do not get there are recomputed in FP64 */
+    int32_t factor_engine;     /* mixed path factorisation: 0 = tensor cores (split-BF16
+                                  tcgen05 trailing updates, default), 1 = FP32 SIMT */
 } pcv_options;
 
 /* ---------------------------------------------------------------- host-only */

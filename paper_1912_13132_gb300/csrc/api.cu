@@ -60,6 +60,9 @@ struct DevBuf {
 
 struct Workspace {
     DevBuf<unsigned char> mem;
+    DevBuf<unsigned char> planes;          // mixed path, tensor engine: BF16 planes of the factors
+    int64_t plane_elems = 0;
+    alignas(64) unsigned char maps[3 * 128];   // CUtensorMap x 3 over the planes
     int grid = 0;
     int32_t ld = 0;
     int64_t slot_bytes = 0;
@@ -116,12 +119,14 @@ pcv_options default_options(const pcv_options* o) {
     d.workspace_fraction = 0.5;
     d.refine_max_iter = 6;
     d.refine_tol = 1e-6;
+    d.factor_engine = pcv::kMixedEngineTensor;
     if (o) {
         if (o->struct_size != 0 && o->struct_size != (int32_t)sizeof(pcv_options)) return d;
         if (o->max_slots > 0) d.max_slots = o->max_slots;
         if (o->workspace_fraction > 0 && o->workspace_fraction <= 0.95) d.workspace_fraction = o->workspace_fraction;
         if (o->refine_max_iter > 0) d.refine_max_iter = o->refine_max_iter;
         if (o->refine_tol > 0) d.refine_tol = o->refine_tol;
+        if (o->factor_engine == pcv::kMixedEngineSimt) d.factor_engine = pcv::kMixedEngineSimt;
     }
     return d;
 }
@@ -129,20 +134,32 @@ pcv_options default_options(const pcv_options* o) {
 int32_t round_up(int64_t v, int64_t m) { return (int32_t)(((std::max<int64_t>(v, 1) + m - 1) / m) * m); }
 
 // Allocate the per-CTA workspace slots of one precision (once per context).
-pcv_status ensure_workspace(pcv_ctx* c, int prec, int64_t ntask_hint) {
+pcv_status ensure_workspace(pcv_ctx* c, int prec) {
     Workspace& w = c->ws[prec];
     if (w.grid > 0) return PCV_OK;
     const int32_t ld = round_up(c->kmax, 128);
+    const bool tensor = prec == PCV_PREC_MIXED && c->opts.factor_engine == pcv::kMixedEngineTensor;
     const int64_t sb = prec == PCV_PREC_FP64 ? pcv::slot_bytes_fp64(ld, c->mmax) : pcv::slot_bytes_mixed(ld, c->mmax);
+    const int64_t pb = tensor ? 3 * (int64_t)ld * ld * 2 : 0;   // planes per slot
     size_t free_b = 0, total_b = 0;
     CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
     const double budget = c->opts.workspace_fraction * (double)free_b;
-    int64_t g = c->opts.max_slots > 0 ? c->opts.max_slots : c->sms;
-    g = std::min<int64_t>(g, (int64_t)(budget / (double)sb));
-    (void)ntask_hint;
+    // CTAs per SM: the tensor engine holds all of an SM's tensor memory, the SIMT
+    // engine runs two CTAs per SM, the FP64 kernel one
+    const int per_sm = (prec == PCV_PREC_MIXED && !tensor) ? 2 : 1;
+    int64_t g = c->opts.max_slots > 0 ? c->opts.max_slots : (int64_t)c->sms * per_sm;
+    if (tensor) g = std::min<int64_t>(g, c->sms);
+    g = std::min<int64_t>(g, (int64_t)(budget / (double)(sb + pb)));
     if (g < 1) return fail(PCV_ERR_OOM, "workspace for one task does not fit in device memory");
     cudaError_t e = w.mem.reserve((size_t)(g * sb));
     if (e != cudaSuccess) return cuda_fail(e, "workspace allocation");
+    if (tensor) {
+        w.plane_elems = g * (int64_t)ld * ld;
+        e = w.planes.reserve((size_t)(3 * w.plane_elems * 2));
+        if (e != cudaSuccess) return cuda_fail(e, "plane allocation");
+        if (!pcv::mixed_make_maps(w.planes.p, w.plane_elems, ld, (int)g, w.maps))
+            return fail(PCV_ERR_CUDA, "tensor map encoding failed");
+    }
     w.grid = (int)g;
     w.ld = ld;
     w.slot_bytes = sb;
@@ -303,12 +320,12 @@ static pcv_status run_tasks(pcv_ctx* c, const double* d_params, int32_t B, int32
     CUDA_TRY(cudaMemsetAsync(c->z.p, 0, (size_t)B * N * sizeof(double), s));
     CUDA_TRY(cudaMemsetAsync(c->tst.p, 0, (size_t)B * N * sizeof(int32_t), s));
     if ((int64_t)n_order * B == 0) return PCV_OK;
-    pcv_status st = ensure_workspace(c, prec, (int64_t)n_order * B);
+    pcv_status st = ensure_workspace(c, prec);
     if (st != PCV_OK) return st;
     if (prec == PCV_PREC_MIXED) {
         int e = pcv::mixed_prepare(c->device);
         if (e) return cuda_fail((cudaError_t)e, "mixed-path set-up");
-        st = ensure_workspace(c, PCV_PREC_FP64, 0);   // fallback tasks run in FP64
+        st = ensure_workspace(c, PCV_PREC_FP64);   // fallback tasks run in FP64
         if (st != PCV_OK) return st;
         CUDA_TRY(c->fb_list.reserve((size_t)n_order * B));
         CUDA_TRY(c->fb_count.reserve(2));
@@ -344,9 +361,12 @@ static pcv_status run_tasks(pcv_ctx* c, const double* d_params, int32_t B, int32
     a.coord_scale = c->coord_scale;
     a.fb_list = c->fb_list.p;
     a.fb_count = c->fb_count.p;
+    a.planes = w.planes.p;
+    a.plane_elems = w.plane_elems;
     const int grid = (int)std::min<int64_t>(w.grid, (int64_t)n_order * B);
     if (c->timing) CUDA_TRY(cudaEventRecord(c->ev[0], s));
-    int e = prec == PCV_PREC_FP64 ? pcv::launch_task_fp64(a, grid, stream) : pcv::launch_task_mixed(a, grid, stream);
+    int e = prec == PCV_PREC_FP64 ? pcv::launch_task_fp64(a, grid, stream)
+                                  : pcv::launch_task_mixed(a, w.maps, c->opts.factor_engine, grid, stream);
     if (e) return cuda_fail((cudaError_t)e, "task kernel launch");
     if (c->timing) {
         CUDA_TRY(cudaEventRecord(c->ev[1], s));

@@ -21,6 +21,7 @@
 
 #include "df.cuh"
 #include "pcv_internal.h"
+#include "umma.cuh"
 
 namespace pcv {
 namespace {
@@ -213,6 +214,150 @@ __device__ bool factor32(SmemM& sm, const SlotM& S, int k, int64_t ld) {
             for (int c = 0; c < NB; ++c)
                 if (c < jb) S.L[r + (int64_t)(j0 + c) * ld] = x[c];
         }
+        __syncthreads();
+    }
+    return true;
+}
+
+// ---------------------------------------------------------------- factorisation (tensor cores)
+
+constexpr int TB = umma::kTileN;          // 128-wide block columns
+constexpr int DP = TB + 1;                // row pitch of the diagonal block in shared memory
+
+struct TcShared {
+    umma::Pipe pipe;
+    int dead;   // a bounded wait ran out: this CTA stops using the tensor path
+};
+
+struct TcCtx {
+    TcShared* sh;
+    uint8_t* stages;                      // operand ring; between updates also the diagonal block
+    umma::Phases ph;
+    const CUtensorMap *m0, *m1, *m2;
+    __nv_bfloat16 *p0, *p1, *p2;          // this slot's planes (row-major, ld x ld)
+    int row_base;                         // this slot's first row in the tensor maps
+};
+
+// Left-looking blocked Cholesky with 128-wide block columns: the update of block
+// column J by all finished columns (the O(k^3) part) runs on the tensor cores from
+// the BF16 planes; the diagonal block and the panel solve run in FP32; the
+// finished block column is then split into the planes.  The FP32 factor stays in
+// S.L (column-major) for the triangular solves.  False if a pivot is not positive
+// or a bounded wait ran out.
+__device__ bool factor_tc(TcCtx& tc, const SlotM& S, int k, int64_t ld) {
+    const int tid = threadIdx.x;
+    float (*D)[DP] = reinterpret_cast<float (*)[DP]>(tc.stages);
+    float* rinv = reinterpret_cast<float*>(tc.stages + TB * DP * 4);
+    int* flag = reinterpret_cast<int*>(rinv + TB);
+    const int nb = (k + TB - 1) / TB;
+    for (int J = 0; J < nb; ++J) {
+        const int j0 = J * TB, jb = min(TB, k - j0);
+        if (j0 > 0) {
+            float* L = S.L;
+            auto epi = [&](int row0, int quad, uint32_t taddr) {
+                const int r = row0 + quad * 32 + (threadIdx.x & 31);
+#pragma unroll 1
+                for (int c0 = 0; c0 < TB; c0 += 32) {
+                    float v[32];
+                    umma::tmem_ld32(taddr + c0, v);
+                    if (r < k) {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j)
+                            if (c0 + j < jb) L[r + (int64_t)(j0 + c0 + j) * ld] -= v[j];
+                    }
+                }
+            };
+            const bool ok = tc.sh->dead == 0 &&
+                            umma::block_column(tc.sh->pipe, tc.ph, tc.stages, tc.m0, tc.m1, tc.m2, tc.row_base, j0,
+                                               k - j0, j0, j0, epi);
+            if (!ok) atomicExch(&tc.sh->dead, 1);
+            __syncthreads();
+            if (tc.sh->dead) return false;
+        }
+        // diagonal block: Cholesky-Crout in shared memory
+        for (int e = tid; e < TB * TB; e += NT) {
+            const int r = e & (TB - 1), c = e >> 7;
+            if (r < jb && c <= r) D[r][c] = S.L[(j0 + r) + (int64_t)(j0 + c) * ld];
+        }
+        if (tid == 0) *flag = 0;
+        __syncthreads();
+        for (int c = 0; c < jb; ++c) {
+            if (tid == 0) {
+                float s = D[c][c];
+                for (int p = 0; p < c; ++p) s = fmaf(-D[c][p], D[c][p], s);
+                if (!(s > 0.0f)) { *flag = 1; s = 1.0f; }
+                const float d = sqrtf(s);
+                D[c][c] = d;
+                rinv[c] = 1.0f / d;
+            }
+            __syncthreads();
+            const float rd = rinv[c];
+            for (int r = c + 1 + tid; r < jb; r += NT) {
+                float s = D[r][c];
+                for (int p = 0; p < c; ++p) s = fmaf(-D[r][p], D[c][p], s);
+                D[r][c] = s * rd;
+            }
+            __syncthreads();
+        }
+        if (*flag) return false;
+        for (int e = tid; e < TB * TB; e += NT) {
+            const int r = e & (TB - 1), c = e >> 7;
+            if (r < jb && c <= r) S.L[(j0 + r) + (int64_t)(j0 + c) * ld] = D[r][c];
+        }
+        // rows below the diagonal block: x L_JJ^T = row, in two halves of 64 columns
+        for (int r = j0 + jb + tid; r < k; r += NT) {
+            float x[64];
+#pragma unroll
+            for (int c = 0; c < 64; ++c) x[c] = c < jb ? S.L[r + (int64_t)(j0 + c) * ld] : 0.0f;
+#pragma unroll
+            for (int c = 0; c < 64; ++c) {
+                float s = x[c];
+#pragma unroll
+                for (int p = 0; p < c; ++p) s = fmaf(-x[p], D[c][p], s);
+                x[c] = c < jb ? s * rinv[c] : 0.0f;
+            }
+#pragma unroll
+            for (int c = 0; c < 64; ++c)
+                if (c < jb) S.L[r + (int64_t)(j0 + c) * ld] = x[c];
+            if (jb > 64) {
+                float y[64];
+#pragma unroll
+                for (int c = 0; c < 64; ++c) y[c] = 64 + c < jb ? S.L[r + (int64_t)(j0 + 64 + c) * ld] : 0.0f;
+#pragma unroll
+                for (int c = 0; c < 64; ++c) {
+                    float s = y[c];
+#pragma unroll
+                    for (int p = 0; p < 64; ++p) s = fmaf(-x[p], D[64 + c][p], s);
+#pragma unroll
+                    for (int p = 0; p < c; ++p) s = fmaf(-y[p], D[64 + c][64 + p], s);
+                    y[c] = 64 + c < jb ? s * rinv[64 + c] : 0.0f;
+                }
+#pragma unroll
+                for (int c = 0; c < 64; ++c)
+                    if (64 + c < jb) S.L[r + (int64_t)(j0 + 64 + c) * ld] = y[c];
+            }
+        }
+        __syncthreads();
+        // split the finished block column into the BF16 planes (rows j0.., 8 columns per item)
+        const int ng = (jb + 7) / 8;
+        for (int e = tid; e < (k - j0) * ng; e += NT) {
+            const int r = j0 + e % (k - j0), g = e / (k - j0);
+            __align__(16) __nv_bfloat16 h[8], m[8], l[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int c = g * 8 + q;
+                const float v = (c < jb && j0 + c <= r) ? S.L[r + (int64_t)(j0 + c) * ld] : 0.0f;
+                umma::split3(v, h[q], m[q], l[q]);
+            }
+            const int64_t off = (int64_t)r * ld + j0 + g * 8;
+            *reinterpret_cast<uint4*>(tc.p0 + off) = *reinterpret_cast<const uint4*>(h);
+            *reinterpret_cast<uint4*>(tc.p1 + off) = *reinterpret_cast<const uint4*>(m);
+            *reinterpret_cast<uint4*>(tc.p2 + off) = *reinterpret_cast<const uint4*>(l);
+        }
+        // the planes are read next by TMA (async proxy); the diagonal-block buffer is
+        // overwritten next by TMA
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+        umma::fence_proxy_async();
         __syncthreads();
     }
     return true;
@@ -415,7 +560,8 @@ __device__ void residual_df(SmemM& sm, const SlotM& S, int k, df inv_rho, double
 
 // ---------------------------------------------------------------- one task
 
-__device__ void run_task(SmemM& sm, const TaskArgs& a, int t, int i, int b) {
+template <bool TC>
+__device__ void run_task(SmemM& sm, TcCtx* tc, const TaskArgs& a, int t, int i, int b) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const double s2 = a.params[3 * b], rho = a.params[3 * b + 1], tau2 = a.params[3 * b + 2];
     const int64_t zoff = (int64_t)b * a.N + i;
@@ -473,7 +619,9 @@ __device__ void run_task(SmemM& sm, const TaskArgs& a, int t, int i, int b) {
             }
     __syncthreads();
 
-    bool ok = factor32(sm, S, k, ld);
+    bool ok;
+    if constexpr (TC) ok = factor_tc(*tc, S, k, ld);
+    else ok = factor32(sm, S, k, ld);
     __syncthreads();
     if (ok) {
         // iterative refinement: x += L^-T L^-1 r
@@ -571,8 +719,56 @@ __global__ void __launch_bounds__(NT, 2) k_cv_mixed(TaskArgs a) {
         const int t = sm.task;
         __syncthreads();
         if (t >= ntask) break;
-        run_task(sm, a, t, a.order[t / a.B], t % a.B);
+        run_task<false>(sm, nullptr, a, t, a.order[t / a.B], t % a.B);
     }
+}
+
+constexpr int kTcSmem = 1024 + umma::kStages * umma::kStageBytes + (int)sizeof(SmemM) + (int)sizeof(TcShared);
+
+// Tensor-core variant: one CTA per SM (it holds all 512 TMEM columns).
+__global__ void __launch_bounds__(NT, 1) k_cv_mixed_tc(TaskArgs a, const __grid_constant__ CUtensorMap m0,
+                                                       const __grid_constant__ CUtensorMap m1,
+                                                       const __grid_constant__ CUtensorMap m2) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    TcCtx tc;
+    tc.stages = base;
+    SmemM& sm = *reinterpret_cast<SmemM*>(base + umma::kStages * umma::kStageBytes);
+    tc.sh = reinterpret_cast<TcShared*>(base + umma::kStages * umma::kStageBytes + sizeof(SmemM));
+    tc.m0 = &m0;
+    tc.m1 = &m1;
+    tc.m2 = &m2;
+    const int64_t slot_elems = (int64_t)a.ld * a.ld;
+    __nv_bfloat16* P = reinterpret_cast<__nv_bfloat16*>(a.planes);
+    tc.p0 = P + blockIdx.x * slot_elems;
+    tc.p1 = P + a.plane_elems + blockIdx.x * slot_elems;
+    tc.p2 = P + 2 * a.plane_elems + blockIdx.x * slot_elems;
+    tc.row_base = blockIdx.x * a.ld;
+    const int warp = threadIdx.x >> 5;
+    for (int e = threadIdx.x; e < 2 * dfm::kExpTable; e += NT) sm.tbl[e] = c_exp.tbl[e];
+    if (threadIdx.x == 0) {
+        umma::pipe_init(tc.sh->pipe);
+        tc.sh->dead = 0;
+        umma::prefetch_map(&m0);
+        umma::prefetch_map(&m1);
+        umma::prefetch_map(&m2);
+    }
+    if (warp == 1) umma::tmem_alloc(&tc.sh->pipe.tmem_base, umma::kTmemCols);
+    umma::tc_fence_before();
+    __syncthreads();
+    umma::tc_fence_after();
+    const int ntask = a.n_order * a.B;
+    for (;;) {
+        if (threadIdx.x == 0) sm.task = (int)atomicAdd(a.counter, 1u);
+        __syncthreads();
+        const int t = sm.task;
+        __syncthreads();
+        if (t >= ntask) break;
+        run_task<true>(sm, &tc, a, t, a.order[t / a.B], t % a.B);
+    }
+    umma::tc_fence_before();
+    __syncthreads();
+    if (warp == 1) umma::tmem_dealloc(tc.sh->pipe.tmem_base, umma::kTmemCols);
 }
 
 std::mutex g_prep_mu;
@@ -595,14 +791,29 @@ int mixed_prepare(int device) {
     if (e != cudaSuccess) return (int)e;
     e = cudaFuncSetAttribute(k_cv_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SmemM));
     if (e != cudaSuccess) return (int)e;
+    e = cudaFuncSetAttribute(k_cv_mixed_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+    if (e != cudaSuccess) return (int)e;
     g_prepared[device] = true;
     return 0;
 }
 
-int launch_task_mixed(const TaskArgs& a, int grid, void* stream) {
-    k_cv_mixed<<<grid, NT, sizeof(SmemM), (cudaStream_t)stream>>>(a);
+int launch_task_mixed(const TaskArgs& a, const void* maps, int engine, int grid, void* stream) {
+    if (engine == kMixedEngineTensor) {
+        const CUtensorMap* m = reinterpret_cast<const CUtensorMap*>(maps);
+        k_cv_mixed_tc<<<grid, NT, kTcSmem, (cudaStream_t)stream>>>(a, m[0], m[1], m[2]);
+    } else {
+        k_cv_mixed<<<grid, NT, sizeof(SmemM), (cudaStream_t)stream>>>(a);
+    }
     count_launch();
     return (int)cudaGetLastError();
+}
+
+bool mixed_make_maps(void* planes, int64_t plane_elems, int32_t ld, int grid, void* maps_out) {
+    CUtensorMap* m = reinterpret_cast<CUtensorMap*>(maps_out);
+    __nv_bfloat16* P = reinterpret_cast<__nv_bfloat16*>(planes);
+    for (int p = 0; p < 3; ++p)
+        if (!umma::make_plane_map(&m[p], P + p * plane_elems, (uint64_t)ld, (uint64_t)grid * ld)) return false;
+    return true;
 }
 
 }  // namespace pcv

@@ -64,12 +64,20 @@ struct TaskArgs {
     const int32_t* task_list;
     const unsigned int* task_count;
     int32_t list_status;    // status written for a task finished in list mode
+    // mixed path, tensor-core factorisation: three BF16 planes of the factor, each
+    // plane_elems elements laid out as (slot * ld + row) * ld + column
+    void* planes;
+    int64_t plane_elems;
 };
 
 // Kernel launchers (one per precision); return the cudaError_t as int.
 int launch_task_fp64(const TaskArgs& a, int grid, void* stream);
 int64_t slot_bytes_fp64(int32_t ld, int64_t mmax);
-int launch_task_mixed(const TaskArgs& a, int grid, void* stream);
+// engine: 0 = tensor cores (split-BF16 tcgen05 trailing updates), 1 = FP32 SIMT.
+// maps: three CUtensorMap (128 bytes each) over the planes (engine 0 only).
+int launch_task_mixed(const TaskArgs& a, const void* maps, int engine, int grid, void* stream);
+bool mixed_make_maps(void* planes, int64_t plane_elems, int32_t ld, int grid, void* maps_out);
+constexpr int kMixedEngineTensor = 0, kMixedEngineSimt = 1;
 int64_t slot_bytes_mixed(int32_t ld, int64_t mmax);
 int mixed_prepare(int device);   // one-time per-device set-up of the mixed path
 

@@ -51,8 +51,6 @@ PCV_API pcv_status pcv_selftest_df_device(int32_t op, const double* d_a, const d
 }
 
 // ---------------------------------------------------------------- tensor-core pipeline self-test
-#include <cudaTypedefs.h>
-
 #include <vector>
 
 #include "umma.cuh"
@@ -112,26 +110,6 @@ __global__ void __launch_bounds__(256, 1) k_umma_test(const __grid_constant__ CU
     if (threadIdx.x == 0) *err = sm.err;
 }
 
-bool make_map(CUtensorMap* map, void* base, uint64_t inner, uint64_t rows) {
-    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
-    if (!encode) {
-        cudaDriverEntryPointQueryResult q;
-        void* fn = nullptr;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
-                cudaSuccess ||
-            q != cudaDriverEntryPointSuccess || !fn)
-            return false;
-        encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
-    }
-    cuuint64_t dims[2] = {inner, rows};
-    cuuint64_t strides[1] = {inner * 2};
-    cuuint32_t box[2] = {(cuuint32_t)pcv::umma::kChunkK, (cuuint32_t)pcv::umma::kTileM};
-    cuuint32_t estr[2] = {1, 1};
-    return encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-
 }  // namespace
 
 // C (M x 128, row-major) = A (M x K) * B (128 x K)^T through the split-BF16 tensor-core
@@ -160,7 +138,7 @@ PCV_API pcv_status pcv_selftest_umma(const float* A, int32_t M, const float* B, 
         k_split<<<(unsigned)((n + 255) / 256), 256>>>(dX, n, dP, dP + n, dP + 2 * n);
         CUtensorMap m[3];
         bool ok = true;
-        for (int p = 0; p < 3; ++p) ok = ok && make_map(&m[p], dP + p * n, (uint64_t)K, (uint64_t)rows);
+        for (int p = 0; p < 3; ++p) ok = ok && make_plane_map(&m[p], dP + p * n, (uint64_t)K, (uint64_t)rows);
         if (!ok) {
             st = PCV_ERR_CUDA;
         } else {

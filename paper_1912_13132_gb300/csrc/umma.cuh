@@ -18,6 +18,7 @@
 #pragma once
 
 #include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -300,6 +301,31 @@ __device__ bool block_column(Pipe& P, Phases& ph, uint8_t* stages, const CUtenso
     ph.stage += (uint32_t)(npass > 0 ? npass * nk : 0);
     ph.pass += (uint32_t)npass;
     return ok;
+}
+
+// ---------------------------------------------------------------- host: tensor maps
+
+// 2-D tensor map over a row-major BF16 matrix of `rows` rows of `inner` elements
+// (inner * 2 bytes a multiple of 16), boxes of kTileM rows x kChunkK elements,
+// 64-byte swizzle (the layout the shared-memory descriptors above expect).
+inline bool make_plane_map(CUtensorMap* map, void* base, uint64_t inner, uint64_t rows) {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        cudaDriverEntryPointQueryResult q;
+        void* fn = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn)
+            return false;
+        encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    }
+    cuuint64_t dims[2] = {inner, rows};
+    cuuint64_t strides[1] = {inner * 2};
+    cuuint32_t box[2] = {(cuuint32_t)kChunkK, (cuuint32_t)kTileM};
+    cuuint32_t estr[2] = {1, 1};
+    return encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 }  // namespace umma

@@ -35,7 +35,7 @@ class pcv_layout(ctypes.Structure):
 class pcv_options(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_int32), ("max_slots", ctypes.c_int32),
                 ("workspace_fraction", ctypes.c_double), ("refine_max_iter", ctypes.c_int32),
-                ("refine_tol", ctypes.c_double)]
+                ("refine_tol", ctypes.c_double), ("factor_engine", ctypes.c_int32)]
 
 
 class PcvError(RuntimeError):
@@ -184,13 +184,14 @@ class Context:
     """A device-resident dataset with its subset layout (pcv_create ... pcv_destroy)."""
 
     def __init__(self, xy, v, role, layout: dict, device: int = 0, max_slots: int = 0,
-                 workspace_fraction: float = 0.0, refine_max_iter: int = 0, refine_tol: float = 0.0):
+                 workspace_fraction: float = 0.0, refine_max_iter: int = 0, refine_tol: float = 0.0,
+                 factor_engine: str = "tensor"):
         xy = _f64(xy).reshape(-1, 2)
         v = _f64(v)
         role = np.ascontiguousarray(role, dtype=np.uint8)
         L, keep = make_layout(layout)
         o = pcv_options(ctypes.sizeof(pcv_options), max_slots, workspace_fraction, refine_max_iter,
-                        refine_tol)
+                        refine_tol, {"tensor": 0, "simt": 1}[factor_engine])
         h = _vp()
         _check(_lib.pcv_create(_ptr(xy, _dp), _ptr(v, _dp), _ptr(role, _u8p), len(v), ctypes.byref(L),
                                device, ctypes.byref(o), ctypes.byref(h)), "pcv_create")

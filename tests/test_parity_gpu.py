@@ -159,3 +159,19 @@ def test_paper_scale_sampled(gpu_lib, paper5m, prec, B):
         ref = oracle.cv_loss(w.xy, w.v, w.role, w.layout, P[b:b + 1], members=members, subsets=pick)
         sub = dict(z=out["z"][b:b + 1], yhat=out["yhat"][b:b + 1], sspe=out["sspe"][b:b + 1])
         compare(sub, ref, V_off, pick, 1, prec, check_total=False)
+
+
+@pytest.mark.parametrize("engine", ["tensor", "simt"])
+def test_mixed_engines(gpu_lib, engine):
+    """Both factorisation engines of the mixed path (split-BF16 tcgen05 trailing
+    updates, FP32 SIMT) meet the mixed tolerance on subsets spanning several
+    128-row tiles and a ragged tail (uniform 4096 workload, three configurations)."""
+    w = datagen.config_uniform_4096()
+    P = np.array([[1.0, 0.1, 0.05], [0.7, 0.03, 0.2], [2.0, 0.3, 0.001]])
+    with gpu_lib.Context(w.xy, w.v, w.role, w.layout, factor_engine=engine) as ctx:
+        out = ctx.cv_loss(P, precision="mixed", per_subset=True, predictions=True)
+        V_off = ctx.V_off.copy()
+    members = oracle.all_members(w.xy, w.role, w.layout)
+    ref = oracle.cv_loss(w.xy, w.v, w.role, w.layout, P, members=members)
+    assert np.all(out["status"] == 0), out["status"]
+    compare(out, ref, V_off, range(16), len(P), "mixed")
