@@ -55,6 +55,9 @@ def load_peaks() -> tuple[dict, str]:
 def make_workload(name: str):
     if name == "paper5m":
         return datagen.config_paper_5m()
+    if name == "paper-small":
+        # same subset sizes as paper5m (56-node cores, shell 0.001 scaled), 100 subsets: profiling case
+        return datagen.config_paper_5m(side=560, nx=10, delta=0.001 * 2236 / 560)
     if name == "cluster262k":
         return datagen.config_cluster_262k()
     if name == "uniform4096":
@@ -197,6 +200,9 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--max-slots", type=int, default=0, help="limit concurrent tasks (profiling runs)")
+    ap.add_argument("--engine", default="tensor", choices=["tensor", "simt"])
+    ap.add_argument("--tc-stages", type=int, default=0, help="TMA ring depth of the tensor engine (2 or 3)")
     args = ap.parse_args()
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
@@ -225,7 +231,8 @@ def main():
     w = make_workload(args.workload)
     t_gen = time.perf_counter() - t_setup
     t0 = time.perf_counter()
-    ctx = pcv.Context(w.xy, w.v, w.role, w.layout, device=local)
+    ctx = pcv.Context(w.xy, w.v, w.role, w.layout, device=local, max_slots=args.max_slots,
+                      factor_engine=args.engine, tc_stages=args.tc_stages)
     t_create = time.perf_counter() - t0
     k, m = task_sizes(ctx)
     B = args.batch
@@ -266,6 +273,7 @@ def main():
     launches = pcv.pcv_launch_count()
     barrier()
     clk = clocks.stop()
+    phases = ctx.phase_cycles() if args.precision == "mixed" else None
     total_s = sum(step_ms) / 1e3
     if dist is not None:
         t = torch.tensor([total_s], device="cuda")
@@ -283,12 +291,12 @@ def main():
         t0 = time.perf_counter()
         out = ctx.cv_loss(host_P[s], precision=args.precision, stream=stream)
         e2e_s.append(time.perf_counter() - t0)
-    e2e_total = sum(e2e_s)
+    e2e_total = sum(e2e_s) if e2e_s else 1.0
     if dist is not None:
         t = torch.tensor([e2e_total], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_total = float(t.item())
-    e2e_value = world * B * args.e2e_steps / e2e_total
+    e2e_value = world * B * args.e2e_steps / e2e_total if args.e2e_steps > 0 else None
 
     peaks, peak_src = load_peaks()
     flops = algorithmic_flops(k, m, B)
@@ -297,13 +305,14 @@ def main():
     if args.precision == "fp64":
         bound, peak, peak_note = "alu", FP64_NOMINAL_TFLOPS, "FP64 nominal (no measured FP64 peak)"
     else:
-        bound, peak, peak_note = "alu", None, None
-        info = pcv.mixed_info() if hasattr(pcv, "mixed_info") else None
-        if info and info.get("tensor"):
+        if args.engine == "tensor":
+            # six BF16 products per FP32-accurate product: the useful-flop ceiling of the
+            # split scheme is the measured sustained BF16 rate / 6
             bound = "tensor"
-            peak = peaks["bf16_tflops_sustained"] / info["products"]
-            peak_note = f"measured bf16 sustained / {info['products']} split products ({peak_src})"
+            peak = peaks["bf16_tflops_sustained"] / 6.0
+            peak_note = f"bf16 sustained ({peak_src}) / 6 split products"
         else:
+            bound = "alu"
             sm_max = (clk.get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0))
             peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12
             peak_note = "FP32 FMA: 152 SMs x 128 lanes x 2 flop x max SM clock"
@@ -313,16 +322,24 @@ def main():
 
     line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
                 ms_per_step=total_s * 1e3 / args.steps, higher_is_better=True, scaling="weak",
-                vs_baseline=None, dtype="f64" if args.precision == "fp64" else "mixed(bf16x6/f32/df64)",
+                vs_baseline=None,
+                dtype="f64" if args.precision == "fp64" else
+                ("bf16x6+f32+df32x2" if args.engine == "tensor" else "f32+df32x2"),
                 data="synthetic",
                 config=dict(workload=w.name, n_obs=int(len(w.v)), subsets=int(ctx.N), active_subsets=int(len(k)),
                             k_min=int(k.min()), k_max=int(k.max()), m_mean=float(m.mean()), batch=B,
-                            precision=args.precision, parallelism="replicas" if world > 1 else "single-gpu",
+                            precision=args.precision, engine=args.engine,
+                            parallelism="replicas" if world > 1 else "single-gpu",
                             l2="flushed between steps (512 MB write)"),
                 e2e=dict(value=e2e_value, unit=UNIT, h2d_bytes_per_step=24 * B, d2h_bytes_per_step=12 * B,
                          note="pcv_cv_loss host-pointer call; dataset resident since pcv_create"),
                 gpu_launches=int(launches), roofline=roof, clocks=clk,
                 setup=dict(datagen_s=t_gen, create_s=t_create))
+    if phases and phases.get("task"):
+        tot = phases["task"]
+        line["phase_share"] = {k2: round(v / tot, 4) for k2, v in phases.items()
+                               if v and k2 not in ("task", "residual_passes", "tasks")}
+        line["residual_passes_per_task"] = phases["residual_passes"] / max(phases["tasks"], 1)
     if rank == 0 and world == 1 and not args.no_cpu:
         active = np.nonzero(np.diff(ctx.V_off) > 0)[0]
         cb = cpu_baseline(w, P[0], args.cpu_budget, active)

@@ -100,11 +100,14 @@ typedef struct {
     int32_t max_slots;         /* concurrent tasks on the device (default: SM count) */
     double workspace_fraction; /* share of free device memory for workspaces (default 0.5) */
     int32_t refine_max_iter;   /* mixed path: maximum refinement corrections (default 6) */
-    double refine_tol;         /* mixed path: stop once a correction d satisfies
-                                  ||d||_inf <= tol * ||x||_inf (default 1e-6); tasks that
-                                  do not get there are recomputed in FP64 */
+    double refine_tol;         /* mixed path: stop once the error left after correction i,
+                                  estimated as ||d_i|| * ||d_i|| / ||d_i-1||, is at most
+                                  tol * ||x|| (max norms; default 1e-8); tasks whose
+                                  corrections stop shrinking are recomputed in FP64 */
     int32_t factor_engine;     /* mixed path factorisation: 0 = tensor cores (split-BF16
                                   tcgen05 trailing updates, default), 1 = FP32 SIMT */
+    int32_t tc_stages;         /* tensor engine: depth of the TMA operand ring, 2 or 3 (default 2);
+                                  fewer stages leave more on-chip memory to the L1 cache */
 } pcv_options;
 
 /* ---------------------------------------------------------------- host-only */
@@ -179,6 +182,17 @@ pcv_status pcv_predict(pcv_ctx* ctx, const double* params3, const double* xy_new
  * two durations in milliseconds.  PCV_ERR_ARG if timing is off or nothing ran. */
 pcv_status pcv_set_timing(pcv_ctx* ctx, int32_t enable);
 pcv_status pcv_kernel_time(pcv_ctx* ctx, double* task_ms, double* combine_ms);
+
+/* Per-phase SM cycles of the mixed task kernel, summed over its CTAs since timing
+ * was enabled (or since the last reset), 16 entries: 0 gather + FP32 assembly,
+ * 1 tensor-core trailing updates, 2 diagonal blocks, 3 panel solves, 4 BF16
+ * splitting, 5 SIMT factorisation (FP32 engine), 6 FP32 triangular solves,
+ * 7 double-float residuals, 8 prediction + loss, 9 whole tasks; entries 10 and 11
+ * count residual passes and finished tasks, 12..14 tasks handed to the FP64
+ * fallback because the factorisation broke down, a correction was not finite, or
+ * the corrections stopped shrinking (counts, not cycles); others unused.
+ * Synchronises the device. */
+pcv_status pcv_phase_cycles(pcv_ctx* ctx, uint64_t* out, int32_t reset);
 
 /* Destroy a context and free its device memory (synchronises the device). */
 void pcv_destroy(pcv_ctx* ctx);

@@ -95,7 +95,7 @@ struct pcv_ctx {
     DevBuf<double> z, params, sspe;
     DevBuf<int32_t> tst, status;
     DevBuf<unsigned int> counter;
-    Workspace ws[2];
+    Workspace ws[3];                        // FP64, mixed, FP64 fallback of the mixed path
     // prediction buffers
     DevBuf<double> Px, Py, Pyhat;
     DevBuf<int64_t> Poff;
@@ -104,6 +104,7 @@ struct pcv_ctx {
     bool timing = false;
     bool timed_task = false, timed_combine = false;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    DevBuf<unsigned long long> phase;       // per-phase cycle counters of the mixed kernel
     ~pcv_ctx() {
         for (auto& e : ev)
             if (e) cudaEventDestroy(e);
@@ -118,8 +119,9 @@ pcv_options default_options(const pcv_options* o) {
     d.max_slots = 0;
     d.workspace_fraction = 0.5;
     d.refine_max_iter = 6;
-    d.refine_tol = 1e-6;
+    d.refine_tol = 1e-8;
     d.factor_engine = pcv::kMixedEngineTensor;
+    d.tc_stages = 2;
     if (o) {
         if (o->struct_size != 0 && o->struct_size != (int32_t)sizeof(pcv_options)) return d;
         if (o->max_slots > 0) d.max_slots = o->max_slots;
@@ -127,6 +129,7 @@ pcv_options default_options(const pcv_options* o) {
         if (o->refine_max_iter > 0) d.refine_max_iter = o->refine_max_iter;
         if (o->refine_tol > 0) d.refine_tol = o->refine_tol;
         if (o->factor_engine == pcv::kMixedEngineSimt) d.factor_engine = pcv::kMixedEngineSimt;
+        if (o->tc_stages == 2 || o->tc_stages == 3) d.tc_stages = o->tc_stages;
     }
     return d;
 }
@@ -134,9 +137,14 @@ pcv_options default_options(const pcv_options* o) {
 int32_t round_up(int64_t v, int64_t m) { return (int32_t)(((std::max<int64_t>(v, 1) + m - 1) / m) * m); }
 
 // Allocate the per-CTA workspace slots of one precision (once per context).
+constexpr int kFallbackWs = 2;          // index of the fallback workspace
+constexpr int kFallbackSlots = 32;      // tasks needing the FP64 fallback are rare
+
 pcv_status ensure_workspace(pcv_ctx* c, int prec) {
     Workspace& w = c->ws[prec];
     if (w.grid > 0) return PCV_OK;
+    const bool fallback = prec == kFallbackWs;
+    if (fallback) prec = PCV_PREC_FP64;
     const int32_t ld = round_up(c->kmax, 128);
     const bool tensor = prec == PCV_PREC_MIXED && c->opts.factor_engine == pcv::kMixedEngineTensor;
     const int64_t sb = prec == PCV_PREC_FP64 ? pcv::slot_bytes_fp64(ld, c->mmax) : pcv::slot_bytes_mixed(ld, c->mmax);
@@ -144,11 +152,12 @@ pcv_status ensure_workspace(pcv_ctx* c, int prec) {
     size_t free_b = 0, total_b = 0;
     CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
     const double budget = c->opts.workspace_fraction * (double)free_b;
-    // CTAs per SM: the tensor engine holds all of an SM's tensor memory, the SIMT
-    // engine runs two CTAs per SM, the FP64 kernel one
-    const int per_sm = (prec == PCV_PREC_MIXED && !tensor) ? 2 : 1;
+    // CTAs per SM: two for both mixed engines (the tensor engine holds half of an
+    // SM's tensor memory per CTA), one for the FP64 kernel
+    const int per_sm = prec == PCV_PREC_MIXED ? 2 : 1;
     int64_t g = c->opts.max_slots > 0 ? c->opts.max_slots : (int64_t)c->sms * per_sm;
-    if (tensor) g = std::min<int64_t>(g, c->sms);
+    if (tensor) g = std::min<int64_t>(g, 2 * (int64_t)c->sms);
+    if (fallback) g = std::min<int64_t>(g, kFallbackSlots);
     g = std::min<int64_t>(g, (int64_t)(budget / (double)(sb + pb)));
     if (g < 1) return fail(PCV_ERR_OOM, "workspace for one task does not fit in device memory");
     cudaError_t e = w.mem.reserve((size_t)(g * sb));
@@ -325,7 +334,7 @@ static pcv_status run_tasks(pcv_ctx* c, const double* d_params, int32_t B, int32
     if (prec == PCV_PREC_MIXED) {
         int e = pcv::mixed_prepare(c->device);
         if (e) return cuda_fail((cudaError_t)e, "mixed-path set-up");
-        st = ensure_workspace(c, PCV_PREC_FP64);   // fallback tasks run in FP64
+        st = ensure_workspace(c, kFallbackWs);   // fallback tasks run in FP64
         if (st != PCV_OK) return st;
         CUDA_TRY(c->fb_list.reserve((size_t)n_order * B));
         CUDA_TRY(c->fb_count.reserve(2));
@@ -363,6 +372,8 @@ static pcv_status run_tasks(pcv_ctx* c, const double* d_params, int32_t B, int32
     a.fb_count = c->fb_count.p;
     a.planes = w.planes.p;
     a.plane_elems = w.plane_elems;
+    a.phase_cycles = c->timing ? c->phase.p : nullptr;
+    a.tc_stages = c->opts.tc_stages;
     const int grid = (int)std::min<int64_t>(w.grid, (int64_t)n_order * B);
     if (c->timing) CUDA_TRY(cudaEventRecord(c->ev[0], s));
     int e = prec == PCV_PREC_FP64 ? pcv::launch_task_fp64(a, grid, stream)
@@ -375,7 +386,7 @@ static pcv_status run_tasks(pcv_ctx* c, const double* d_params, int32_t B, int32
     if (prec == PCV_PREC_MIXED) {
         // tasks the mixed kernel could not finish run again in FP64 (the list and
         // its length stay on the device; CTAs beyond the list exit at once)
-        Workspace& w64 = c->ws[PCV_PREC_FP64];
+        Workspace& w64 = c->ws[kFallbackWs];
         pcv::TaskArgs f = a;
         f.work = reinterpret_cast<double*>(w64.mem.p);
         f.slot_bytes = w64.slot_bytes;
@@ -529,6 +540,8 @@ PCV_API pcv_status pcv_set_timing(pcv_ctx* c, int32_t enable) {
     CUDA_TRY(cudaSetDevice(c->device));
     for (auto& e : c->ev)
         if (!e) CUDA_TRY(cudaEventCreate(&e));
+    CUDA_TRY(c->phase.reserve(pcv::kPhaseCount));
+    CUDA_TRY(cudaMemset(c->phase.p, 0, pcv::kPhaseCount * sizeof(unsigned long long)));
     c->timing = enable != 0;
     c->timed_task = c->timed_combine = false;
     return PCV_OK;
@@ -549,6 +562,16 @@ PCV_API pcv_status pcv_kernel_time(pcv_ctx* c, double* task_ms, double* combine_
             *combine_ms = t;
         }
     }
+    return PCV_OK;
+}
+
+PCV_API pcv_status pcv_phase_cycles(pcv_ctx* c, uint64_t* out, int32_t reset) {
+    if (!c || !out) return fail(PCV_ERR_ARG, "NULL argument");
+    if (!c->phase.p) return fail(PCV_ERR_ARG, "timing was never enabled");
+    CUDA_TRY(cudaSetDevice(c->device));
+    CUDA_TRY(cudaDeviceSynchronize());
+    CUDA_TRY(cudaMemcpy(out, c->phase.p, pcv::kPhaseCount * sizeof(uint64_t), cudaMemcpyDeviceToHost));
+    if (reset) CUDA_TRY(cudaMemset(c->phase.p, 0, pcv::kPhaseCount * sizeof(unsigned long long)));
     return PCV_OK;
 }
 

@@ -35,6 +35,27 @@ constexpr double QSCALE = 1048576.0;  // 2^20: grid of the high parts of trainin
 
 __constant__ dfm::ExpConsts c_exp;
 
+// Per-phase cycle counters (thread 0 of each CTA adds its elapsed clock64 cycles).
+__device__ __forceinline__ long long now_cycles() {
+    long long t;
+    asm volatile("mov.u64 %0, %%clock64;" : "=l"(t));
+    return t;
+}
+
+struct PhaseTimer {
+    unsigned long long* out;
+    long long t;
+    __device__ explicit PhaseTimer(unsigned long long* o) : out(o), t(0) {
+        if (o) t = now_cycles();
+    }
+    __device__ void lap(int ph) {
+        if (!out) return;
+        const long long n = now_cycles();
+        if (threadIdx.x == 0) atomicAdd(out + ph, (unsigned long long)(n - t));
+        t = n;
+    }
+};
+
 struct SlotM {
     float* L;      // ld x ld, column-major, lower triangle
     double* yv;    // training values
@@ -71,17 +92,27 @@ __device__ __forceinline__ SlotM slot_of(const TaskArgs& a) {
     return s;
 }
 
-struct SmemM {
+// Shared memory used phase by phase (in the tensor-core kernel it lives in the
+// operand ring, which is idle outside the trailing updates).
+struct alignas(16) SmemM {
     float L[NB][NB + 1];           // diagonal block
-    float Ta[KC][NB + 4];          // trailing-update staging
-    float Tb[KC][NB + 4];
     float rinv[NB];                // reciprocals of the diagonal of L_JJ
-    float tbl[2 * dfm::kExpTable]; // exp table (copy of c_exp.tbl)
     float ph[16][NB], pl[16][NB];  // residual partial sums (double-float)
     float wj[NB];
     double dred[NT / 32];
     float fred[NT / 32];
     int flag;
+};
+
+// Trailing-update staging of the FP32 engine (read with float4 loads).
+struct alignas(16) SmemSimt {
+    float Ta[KC][NB + 4];
+    float Tb[KC][NB + 4];
+};
+
+// Shared memory kept for the whole kernel.
+struct SmemKeep {
+    float tbl[2 * dfm::kExpTable]; // exp table (copy of c_exp.tbl)
     int task;
 };
 
@@ -111,7 +142,7 @@ __device__ float block_max(SmemM& sm, float v) {
 // ---------------------------------------------------------------- factorisation (FP32)
 
 // C[r0:r0+rb, j0:j0+jb] -= L[r0:r0+rb, 0:j0] * L[j0:j0+jb, 0:j0]^T, register prefetch of the next chunk
-__device__ void update_tile32(SmemM& sm, float* A, int64_t ld, int r0, int rb, int j0, int jb) {
+__device__ void update_tile32(SmemSimt& sm, float* A, int64_t ld, int r0, int rb, int j0, int jb) {
     const int tid = threadIdx.x;
     const int ty = tid >> 4, tx = tid & 15;
     float acc[4][4];
@@ -160,13 +191,13 @@ __device__ void update_tile32(SmemM& sm, float* A, int64_t ld, int r0, int rb, i
 }
 
 // Left-looking blocked Cholesky of the FP32 matrix in S.L; false if a pivot is not positive.
-__device__ bool factor32(SmemM& sm, const SlotM& S, int k, int64_t ld) {
+__device__ bool factor32(SmemM& sm, SmemSimt& st, const SlotM& S, int k, int64_t ld) {
     const int tid = threadIdx.x;
     const int nb = (k + NB - 1) / NB;
     for (int J = 0; J < nb; ++J) {
         const int j0 = J * NB, jb = min(NB, k - j0);
         if (j0 > 0) {
-            for (int R = J; R < nb; ++R) update_tile32(sm, S.L, ld, R * NB, min(NB, k - R * NB), j0, jb);
+            for (int R = J; R < nb; ++R) update_tile32(st, S.L, ld, R * NB, min(NB, k - R * NB), j0, jb);
             __syncthreads();
         }
         for (int e = tid; e < NB * NB; e += NT) {
@@ -222,7 +253,10 @@ __device__ bool factor32(SmemM& sm, const SlotM& S, int k, int64_t ld) {
 // ---------------------------------------------------------------- factorisation (tensor cores)
 
 constexpr int TB = umma::kTileN;          // 128-wide block columns
-constexpr int DP = TB + 1;                // row pitch of the diagonal block in shared memory
+constexpr int kTcTilesPerPass = 1;        // one 128-row tile per pass: 256 TMEM columns per CTA
+constexpr int kTcStage = umma::stage_bytes(kTcTilesPerPass);   // 48 KB
+constexpr uint32_t kTcTmemCols = 2 * kTcTilesPerPass * umma::kTileN;
+constexpr int DP = TB + 4;                // row pitch of the diagonal block (rows 16-byte aligned)
 
 struct TcShared {
     umma::Pipe pipe;
@@ -244,11 +278,16 @@ struct TcCtx {
 // finished block column is then split into the planes.  The FP32 factor stays in
 // S.L (column-major) for the triangular solves.  False if a pivot is not positive
 // or a bounded wait ran out.
-__device__ bool factor_tc(TcCtx& tc, const SlotM& S, int k, int64_t ld) {
-    const int tid = threadIdx.x;
+__device__ bool factor_tc(TcCtx& tc, const SlotM& S, int k, int64_t ld, unsigned long long* clk) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    PhaseTimer tm(clk);
+    // the operand ring was written through the generic proxy since the last update
+    umma::fence_proxy_async();
+    __syncthreads();
     float (*D)[DP] = reinterpret_cast<float (*)[DP]>(tc.stages);
     float* rinv = reinterpret_cast<float*>(tc.stages + TB * DP * 4);
-    int* flag = reinterpret_cast<int*>(rinv + TB);
+    float* colc = rinv + TB;
+    int* flag = reinterpret_cast<int*>(colc + TB);
     const int nb = (k + TB - 1) / TB;
     for (int J = 0; J < nb; ++J) {
         const int j0 = J * TB, jb = min(TB, k - j0);
@@ -268,76 +307,129 @@ __device__ bool factor_tc(TcCtx& tc, const SlotM& S, int k, int64_t ld) {
                 }
             };
             const bool ok = tc.sh->dead == 0 &&
-                            umma::block_column(tc.sh->pipe, tc.ph, tc.stages, tc.m0, tc.m1, tc.m2, tc.row_base, j0,
-                                               k - j0, j0, j0, epi);
+                            umma::block_column<true, kTcTilesPerPass>(tc.sh->pipe, tc.ph, tc.stages, tc.m0, tc.m1, tc.m2,
+                                                     tc.row_base, j0, k - j0, j0, j0, epi, (int)(ld / 32));
             if (!ok) atomicExch(&tc.sh->dead, 1);
             __syncthreads();
             if (tc.sh->dead) return false;
+            tm.lap(kPhUpdate);
         }
-        // diagonal block: Cholesky-Crout in shared memory
-        for (int e = tid; e < TB * TB; e += NT) {
-            const int r = e & (TB - 1), c = e >> 7;
-            if (r < jb && c <= r) D[r][c] = S.L[(j0 + r) + (int64_t)(j0 + c) * ld];
+        // diagonal block: blocked right-looking Cholesky in shared memory, 32 columns per step
+        // whole 128 x 128 block, four rows per float4 (rows beyond k hold stale values
+        // that are never used); 16 independent loads per thread
+        {
+            float4 v[TB * TB / 4 / NT];
+#pragma unroll
+            for (int i = 0; i < TB * TB / 4 / NT; ++i) {
+                const int e = tid + i * NT, r4 = (e & (TB / 4 - 1)) * 4, c = e / (TB / 4);
+                v[i] = *reinterpret_cast<const float4*>(S.L + (j0 + r4) + (int64_t)(j0 + c) * ld);
+            }
+#pragma unroll
+            for (int i = 0; i < TB * TB / 4 / NT; ++i) {
+                const int e = tid + i * NT, r4 = (e & (TB / 4 - 1)) * 4, c = e / (TB / 4);
+                D[r4][c] = v[i].x;
+                D[r4 + 1][c] = v[i].y;
+                D[r4 + 2][c] = v[i].z;
+                D[r4 + 3][c] = v[i].w;
+            }
         }
         if (tid == 0) *flag = 0;
         __syncthreads();
+        // right-looking, all threads: scale column c into a contiguous copy, then the
+        // rank-1 update of the trailing lower triangle (warp per row, lanes along the row)
         for (int c = 0; c < jb; ++c) {
+            // every thread takes the pivot itself (no extra barrier)
+            float piv = D[c][c];
+            const bool badp = !(piv > 0.0f);
+            if (badp) piv = 1.0f;
+            const float d = sqrtf(piv), rd = 1.0f / d;
             if (tid == 0) {
-                float s = D[c][c];
-                for (int p = 0; p < c; ++p) s = fmaf(-D[c][p], D[c][p], s);
-                if (!(s > 0.0f)) { *flag = 1; s = 1.0f; }
-                const float d = sqrtf(s);
-                D[c][c] = d;
-                rinv[c] = 1.0f / d;
+                if (badp) *flag = 1;
+                rinv[c] = rd;
+            }
+            for (int r = c + 1 + tid; r < jb; r += NT) {
+                const float l = D[r][c] * rd;
+                D[r][c] = l;
+                colc[r] = l;
             }
             __syncthreads();
-            const float rd = rinv[c];
-            for (int r = c + 1 + tid; r < jb; r += NT) {
-                float s = D[r][c];
-                for (int p = 0; p < c; ++p) s = fmaf(-D[r][p], D[c][p], s);
-                D[r][c] = s * rd;
+            if (tid == 0) D[c][c] = d;
+            // rank-1 update, four rows per warp step (independent read-modify-writes)
+            for (int r0 = c + 1 + 4 * warp; r0 < jb; r0 += 4 * (NT / 32)) {
+                float lr[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) lr[u] = r0 + u < jb ? colc[r0 + u] : 0.0f;
+                const int qmax = min(r0 + 3, jb - 1);
+                for (int q = c + 1 + lane; q <= qmax; q += 32) {
+                    const float cq = colc[q];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int r = r0 + u;
+                        if (r < jb && q <= r) D[r][q] = fmaf(-lr[u], cq, D[r][q]);
+                    }
+                }
             }
             __syncthreads();
         }
         if (*flag) return false;
-        for (int e = tid; e < TB * TB; e += NT) {
-            const int r = e & (TB - 1), c = e >> 7;
-            if (r < jb && c <= r) S.L[(j0 + r) + (int64_t)(j0 + c) * ld] = D[r][c];
+#pragma unroll
+        for (int i = 0; i < TB * TB / 4 / NT; ++i) {   // write back (upper part: never read)
+            const int e = tid + i * NT, r4 = (e & (TB / 4 - 1)) * 4, c = e / (TB / 4);
+            *reinterpret_cast<float4*>(S.L + (j0 + r4) + (int64_t)(j0 + c) * ld) =
+                make_float4(D[r4][c], D[r4 + 1][c], D[r4 + 2][c], D[r4 + 3][c]);
         }
-        // rows below the diagonal block: x L_JJ^T = row, in two halves of 64 columns
+        tm.lap(kPhDiag);
+        // rows below the diagonal block: x L_JJ^T = row, 32 columns at a time (the solved
+        // columns are read back from the panel; 4 partial sums in the triangular part)
         for (int r = j0 + jb + tid; r < k; r += NT) {
-            float x[64];
+            float* Lr = S.L + r + (int64_t)j0 * ld;
+            for (int q0 = 0; q0 < jb; q0 += 32) {
+                float y[32];
 #pragma unroll
-            for (int c = 0; c < 64; ++c) x[c] = c < jb ? S.L[r + (int64_t)(j0 + c) * ld] : 0.0f;
+                for (int c = 0; c < 32; ++c) y[c] = q0 + c < jb ? Lr[(int64_t)(q0 + c) * ld] : 0.0f;
+                float n0 = 0.0f, n1 = 0.0f, n2 = 0.0f, n3 = 0.0f;
+                if (q0 > 0) {
+                    n0 = Lr[0];
+                    n1 = Lr[ld];
+                    n2 = Lr[2 * ld];
+                    n3 = Lr[3 * ld];
+                }
+                for (int p = 0; p < q0; p += 4) {
+                    const float x0 = n0, x1 = n1, x2 = n2, x3 = n3;
+                    if (p + 4 < q0) {   // next solved values in flight during this step
+                        n0 = Lr[(int64_t)(p + 4) * ld];
+                        n1 = Lr[(int64_t)(p + 5) * ld];
+                        n2 = Lr[(int64_t)(p + 6) * ld];
+                        n3 = Lr[(int64_t)(p + 7) * ld];
+                    }
 #pragma unroll
-            for (int c = 0; c < 64; ++c) {
-                float s = x[c];
-#pragma unroll
-                for (int p = 0; p < c; ++p) s = fmaf(-x[p], D[c][p], s);
-                x[c] = c < jb ? s * rinv[c] : 0.0f;
-            }
-#pragma unroll
-            for (int c = 0; c < 64; ++c)
-                if (c < jb) S.L[r + (int64_t)(j0 + c) * ld] = x[c];
-            if (jb > 64) {
-                float y[64];
-#pragma unroll
-                for (int c = 0; c < 64; ++c) y[c] = 64 + c < jb ? S.L[r + (int64_t)(j0 + 64 + c) * ld] : 0.0f;
-#pragma unroll
-                for (int c = 0; c < 64; ++c) {
-                    float s = y[c];
-#pragma unroll
-                    for (int p = 0; p < 64; ++p) s = fmaf(-x[p], D[64 + c][p], s);
-#pragma unroll
-                    for (int p = 0; p < c; ++p) s = fmaf(-y[p], D[64 + c][64 + p], s);
-                    y[c] = 64 + c < jb ? s * rinv[64 + c] : 0.0f;
+                    for (int c = 0; c < 32; ++c) {
+                        const float4 d = *reinterpret_cast<const float4*>(&D[q0 + c][p]);
+                        y[c] = fmaf(-x0, d.x, fmaf(-x1, d.y, fmaf(-x2, d.z, fmaf(-x3, d.w, y[c]))));
+                    }
                 }
 #pragma unroll
-                for (int c = 0; c < 64; ++c)
-                    if (64 + c < jb) S.L[r + (int64_t)(j0 + 64 + c) * ld] = y[c];
+                for (int c = 0; c < 32; ++c) {
+                    float a0 = y[c], a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
+#pragma unroll
+                    for (int p = 0; p + 3 < c; p += 4) {
+                        const float4 d = *reinterpret_cast<const float4*>(&D[q0 + c][q0 + p]);
+                        a0 = fmaf(-y[p], d.x, a0);
+                        a1 = fmaf(-y[p + 1], d.y, a1);
+                        a2 = fmaf(-y[p + 2], d.z, a2);
+                        a3 = fmaf(-y[p + 3], d.w, a3);
+                    }
+#pragma unroll
+                    for (int p = (c / 4) * 4; p < c; ++p) a0 = fmaf(-y[p], D[q0 + c][q0 + p], a0);
+                    y[c] = q0 + c < jb ? ((a0 + a1) + (a2 + a3)) * rinv[q0 + c] : 0.0f;
+                }
+#pragma unroll
+                for (int c = 0; c < 32; ++c)
+                    if (q0 + c < jb) Lr[(int64_t)(q0 + c) * ld] = y[c];
             }
         }
         __syncthreads();
+        tm.lap(kPhPanel);
         // split the finished block column into the BF16 planes (rows j0.., 8 columns per item)
         const int ng = (jb + 7) / 8;
         for (int e = tid; e < (k - j0) * ng; e += NT) {
@@ -349,7 +441,9 @@ __device__ bool factor_tc(TcCtx& tc, const SlotM& S, int k, int64_t ld) {
                 const float v = (c < jb && j0 + c <= r) ? S.L[r + (int64_t)(j0 + c) * ld] : 0.0f;
                 umma::split3(v, h[q], m[q], l[q]);
             }
-            const int64_t off = (int64_t)r * ld + j0 + g * 8;
+            // tiled plane layout: 128 x 32 tiles, tile (r / 128, c / 32), row-major inside
+            const int c = j0 + g * 8;
+            const int64_t off = ((int64_t)(r >> 7) * (ld >> 5) + (c >> 5)) * 4096 + (r & 127) * 32 + (c & 31);
             *reinterpret_cast<uint4*>(tc.p0 + off) = *reinterpret_cast<const uint4*>(h);
             *reinterpret_cast<uint4*>(tc.p1 + off) = *reinterpret_cast<const uint4*>(m);
             *reinterpret_cast<uint4*>(tc.p2 + off) = *reinterpret_cast<const uint4*>(l);
@@ -359,22 +453,41 @@ __device__ bool factor_tc(TcCtx& tc, const SlotM& S, int k, int64_t ld) {
         asm volatile("fence.proxy.async.global;" ::: "memory");
         umma::fence_proxy_async();
         __syncthreads();
+        tm.lap(kPhSplit);
     }
     return true;
 }
 
 // ---------------------------------------------------------------- FP32 triangular solves
 
-// w <- L^-1 w (column-oriented: diagonal block by one warp, rows below by all threads)
+// The 64 x 64 block of L at (j0, j0) into sm.L: four float4 loads per thread, all in
+// flight at once (rows beyond k and the upper part carry stale values that are never used).
+__device__ __forceinline__ void load_diag64(SmemM& sm, const float* L, int64_t ld, int j0) {
+    const int tid = threadIdx.x;
+    float4 v[NB * NB / 4 / NT];
+#pragma unroll
+    for (int i = 0; i < NB * NB / 4 / NT; ++i) {
+        const int e = tid + i * NT, r4 = (e & (NB / 4 - 1)) * 4, c = e / (NB / 4);
+        v[i] = *reinterpret_cast<const float4*>(L + (j0 + r4) + (int64_t)(j0 + c) * ld);
+    }
+#pragma unroll
+    for (int i = 0; i < NB * NB / 4 / NT; ++i) {
+        const int e = tid + i * NT, r4 = (e & (NB / 4 - 1)) * 4, c = e / (NB / 4);
+        sm.L[r4][c] = v[i].x;
+        sm.L[r4 + 1][c] = v[i].y;
+        sm.L[r4 + 2][c] = v[i].z;
+        sm.L[r4 + 3][c] = v[i].w;
+    }
+}
+
+// w <- L^-1 w (column-oriented: diagonal block by one warp, rows below by all threads,
+// one row per thread with 64 independent loads in flight)
 __device__ void forward32(SmemM& sm, const float* L, int64_t ld, float* w, int k) {
     const int tid = threadIdx.x, lane = tid & 31;
     const int nb = (k + NB - 1) / NB;
     for (int J = 0; J < nb; ++J) {
         const int j0 = J * NB, jb = min(NB, k - j0);
-        for (int e = tid; e < NB * NB; e += NT) {
-            const int r = e & (NB - 1), c = e >> 6;
-            if (r < jb && c <= r) sm.L[r][c] = L[(j0 + r) + (int64_t)(j0 + c) * ld];
-        }
+        load_diag64(sm, L, ld, j0);
         __syncthreads();
         if (tid < 32) {
             float v0 = lane < jb ? w[j0 + lane] : 0.0f;
@@ -390,32 +503,67 @@ __device__ void forward32(SmemM& sm, const float* L, int64_t ld, float* w, int k
             if (lane + 32 < jb) { w[j0 + lane + 32] = v1; sm.wj[lane + 32] = v1; }
         }
         __syncthreads();
-        for (int r = j0 + jb + tid; r < k; r += NT) {
-            float s = 0.0f;
-            for (int c = 0; c < jb; ++c) s = fmaf(L[r + (int64_t)(j0 + c) * ld], sm.wj[c], s);
-            w[r] -= s;
+        if (jb == NB) {
+            for (int r = j0 + NB + tid; r < k; r += NT) {
+                const float* Lr = L + r + (int64_t)j0 * ld;
+                float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
+#pragma unroll
+                for (int c = 0; c < NB; c += 4) {
+                    s0 = fmaf(Lr[(int64_t)c * ld], sm.wj[c], s0);
+                    s1 = fmaf(Lr[(int64_t)(c + 1) * ld], sm.wj[c + 1], s1);
+                    s2 = fmaf(Lr[(int64_t)(c + 2) * ld], sm.wj[c + 2], s2);
+                    s3 = fmaf(Lr[(int64_t)(c + 3) * ld], sm.wj[c + 3], s3);
+                }
+                w[r] -= (s0 + s1) + (s2 + s3);
+            }
         }
         __syncthreads();
     }
 }
 
-// w <- L^-T w
+// w <- L^-T w.  Dot products of the block's columns with the finished part of w:
+// warp wp takes columns 8wp .. 8wp+7, its lanes walk the rows (coalesced), eight
+// accumulators per thread, then a warp reduction.
 __device__ void backward32(SmemM& sm, const float* L, int64_t ld, float* w, int k) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nb = (k + NB - 1) / NB;
     for (int J = nb - 1; J >= 0; --J) {
         const int j0 = J * NB, jb = min(NB, k - j0);
-        for (int c = warp; c < jb; c += NT / 32) {
-            float s = 0.0f;
-            for (int p = j0 + jb + lane; p < k; p += 32) s = fmaf(L[p + (int64_t)(j0 + c) * ld], w[p], s);
+        {
+            float s[8];
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            if (lane == 0) sm.wj[c] = w[j0 + c] - s;
+            for (int q = 0; q < 8; ++q) s[q] = 0.0f;
+            const int c0 = warp * 8;
+            if (jb == NB) {
+                int p = j0 + jb + lane;
+                for (; p + 96 < k; p += 128) {   // four rows per lane in flight
+                    float wv[4], lv[4][8];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        wv[u] = w[p + 32 * u];
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) lv[u][q] = L[p + 32 * u + (int64_t)(j0 + c0 + q) * ld];
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) s[q] = fmaf(lv[u][q], wv[u], s[q]);
+                }
+                for (; p < k; p += 32) {
+                    const float wp = w[p];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) s[q] = fmaf(L[p + (int64_t)(j0 + c0 + q) * ld], wp, s[q]);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                float v = s[q];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (lane == 0 && c0 + q < jb) sm.wj[c0 + q] = w[j0 + c0 + q] - v;
+            }
         }
-        for (int e = tid; e < NB * NB; e += NT) {
-            const int r = e & (NB - 1), c = e >> 6;
-            if (r < jb && c <= r) sm.L[r][c] = L[(j0 + r) + (int64_t)(j0 + c) * ld];
-        }
+        load_diag64(sm, L, ld, j0);
         __syncthreads();
         if (tid < 32) {
             float v0 = lane < jb ? sm.wj[lane] : 0.0f;
@@ -465,13 +613,13 @@ __device__ __forceinline__ df t_any(const Pt& p, const Pt& q, df inv_rho) {
     return dfm::mul(dfm::sqrt_df(d2), inv_rho);
 }
 
-__device__ __forceinline__ df exp_neg_sm(const SmemM& sm, df t) {
-    return dfm::exp_neg(t, sm.tbl, c_exp.inv_c, c_exp.c1, c_exp.c2, c_exp.c3);
+__device__ __forceinline__ df exp_neg_sm(const float* tbl, df t) {
+    return dfm::exp_neg(t, tbl, c_exp.inv_c, c_exp.c1, c_exp.c2, c_exp.c3);
 }
 
 // r = y - A x with A = Sigma + lambda I: double-float entries, one pass over the
 // lower triangle in 64 x 64 tiles, each entry feeding its row and its column.
-__device__ void residual_df(SmemM& sm, const SlotM& S, int k, df inv_rho, double lam) {
+__device__ void residual_df(SmemM& sm, const float* tbl, const SlotM& S, int k, df inv_rho, double lam) {
     const int tid = threadIdx.x;
     const int rg = tid >> 4, cg = tid & 15;   // 16 x 16 threads, 4 x 4 entries each
     for (int a = tid; a < k; a += NT) { S.ah[a] = 0.0f; S.al[a] = 0.0f; }
@@ -505,7 +653,7 @@ __device__ void residual_df(SmemM& sm, const SlotM& S, int k, df inv_rho, double
                 for (int v = 0; v < 4; ++v) {
                     const int a = I * NB + rg * 4 + u, b = J * NB + cg * 4 + v;
                     if (a < k && b < k && (I != J || a > b)) {
-                        const df e = exp_neg_sm(sm, t_grid(pa[u], pb[v], inv_rho));
+                        const df e = exp_neg_sm(tbl, t_grid(pa[u], pb[v], inv_rho));
                         racc[u].add_prod(e, xb[v]);
                         cacc[v].add_prod(e, xa[u]);
                     }
@@ -561,7 +709,8 @@ __device__ void residual_df(SmemM& sm, const SlotM& S, int k, df inv_rho, double
 // ---------------------------------------------------------------- one task
 
 template <bool TC>
-__device__ void run_task(SmemM& sm, TcCtx* tc, const TaskArgs& a, int t, int i, int b) {
+__device__ void run_task(SmemM& sm, SmemKeep& keep, SmemSimt* simt, TcCtx* tc, const TaskArgs& a, int t, int i,
+                         int b) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const double s2 = a.params[3 * b], rho = a.params[3 * b + 1], tau2 = a.params[3 * b + 2];
     const int64_t zoff = (int64_t)b * a.N + i;
@@ -585,7 +734,10 @@ __device__ void run_task(SmemM& sm, TcCtx* tc, const TaskArgs& a, int t, int i, 
     const float inv_rho32 = (float)inv_rho_s;
     const double ox = k > 0 ? a.X[a.T_idx[t0]] : 0.0, oy = k > 0 ? a.Y[a.T_idx[t0]] : 0.0;
 
+    PhaseTimer tm(a.phase_cycles);
+    const long long t_task = a.phase_cycles ? now_cycles() : 0;
     // gather: scaled offsets, high parts on the 2^-20 grid
+#pragma unroll 4
     for (int q = tid; q < k; q += NT) {
         const int g = a.T_idx[t0 + q];
         const double dx = (a.X[g] - ox) * sc, dy = (a.Y[g] - oy) * sc;
@@ -600,57 +752,127 @@ __device__ void run_task(SmemM& sm, TcCtx* tc, const TaskArgs& a, int t, int i, 
     }
     __syncthreads();
 
-    // FP32 lower triangle of Sigma + lambda I
+    // FP32 lower triangle of Sigma + lambda I (the tensor-core kernel reads the
+    // coordinates from shared memory: the operand ring is idle before the factorisation)
+    const float *cxh = S.xh, *cxl = S.xl, *cyh = S.yh, *cyl = S.yl;
+    if constexpr (TC) {
+        if ((size_t)4 * ld * sizeof(float) <= (size_t)a.tc_stages * kTcStage) {
+            float* f = reinterpret_cast<float*>(tc->stages);
+            for (int q = tid; q < k; q += NT) {
+                f[q] = S.xh[q];
+                f[ld + q] = S.xl[q];
+                f[2 * ld + q] = S.yh[q];
+                f[3 * ld + q] = S.yl[q];
+            }
+            cxh = f;
+            cxl = f + ld;
+            cyh = f + 2 * ld;
+            cyl = f + 3 * ld;
+            __syncthreads();
+        }
+    }
     const float lam32 = (float)lam;
     const int nb = (k + NB - 1) / NB;
     for (int bj = 0; bj < nb; ++bj)
-        for (int bi = bj; bi < nb; ++bi)
-            for (int e = tid; e < NB * NB; e += NT) {
-                const int r = bi * NB + (e & (NB - 1)), c = bj * NB + (e >> 6);
-                if (r < k && c <= r) {
-                    float v = 1.0f + lam32;
-                    if (r != c) {
-                        const float dx = (S.xh[r] - S.xh[c]) + (S.xl[r] - S.xl[c]);
-                        const float dy = (S.yh[r] - S.yh[c]) + (S.yl[r] - S.yl[c]);
-                        v = __expf(-sqrtf(fmaf(dx, dx, dy * dy)) * inv_rho32);
-                    }
-                    S.L[r + (int64_t)c * ld] = v;
+        for (int bi = bj; bi < nb; ++bi) {
+            const int r = bi * NB + (tid & (NB - 1));     // fixed row per thread within a tile
+            if (r >= k) continue;
+            const float rxh = cxh[r], rxl = cxl[r], ryh = cyh[r], ryl = cyl[r];
+            for (int cc = tid >> 6; cc < NB; cc += NT / NB) {
+                const int c = bj * NB + cc;
+                if (c > r) break;
+                float v = 1.0f + lam32;
+                if (r != c) {
+                    const float dx = (rxh - cxh[c]) + (rxl - cxl[c]);
+                    const float dy = (ryh - cyh[c]) + (ryl - cyl[c]);
+                    v = expf(-sqrtf(fmaf(dx, dx, dy * dy)) * inv_rho32);
                 }
+                S.L[r + (int64_t)c * ld] = v;
             }
+        }
     __syncthreads();
 
+    tm.lap(kPhGather);
     bool ok;
-    if constexpr (TC) ok = factor_tc(*tc, S, k, ld);
-    else ok = factor32(sm, S, k, ld);
+    if constexpr (TC) ok = factor_tc(*tc, S, k, ld, a.phase_cycles);
+    else ok = factor32(sm, *simt, S, k, ld);
+    tm.t = a.phase_cycles ? now_cycles() : 0;
+    if constexpr (!TC) tm.lap(kPhFactorSimt);
+    // refinement and prediction work on per-task vectors; in the tensor-core kernel the
+    // operand ring is idle from here on, so they move to shared memory when they fit
+    if (!ok && a.phase_cycles && tid == 0) atomicAdd(a.phase_cycles + kPhFailFactor, 1ull);
+    SlotM R = S;
+    if constexpr (TC) {
+        // as many of the vectors as fit, most used first: coordinates and solution
+        // (residual and prediction), then the solve vector, then the accumulators
+        const size_t room = (size_t)a.tc_stages * kTcStage - sizeof(SmemM);
+        const size_t vec = (size_t)ld * sizeof(float);
+        if (ok && room >= 6 * vec) {
+            float* f = reinterpret_cast<float*>(tc->stages + sizeof(SmemM));
+            R.xh = f;
+            R.xl = f + ld;
+            R.yh = f + 2 * ld;
+            R.yl = f + 3 * ld;
+            R.qh = f + 4 * ld;
+            R.ql = f + 5 * ld;
+            if (room >= 7 * vec) R.w = f + 6 * ld;
+            if (room >= 9 * vec) {
+                R.ah = f + 7 * ld;
+                R.al = f + 8 * ld;
+            }
+            for (int q = tid; q < k; q += NT) {
+                R.xh[q] = S.xh[q];
+                R.xl[q] = S.xl[q];
+                R.yh[q] = S.yh[q];
+                R.yl[q] = S.yl[q];
+            }
+            __syncthreads();
+        }
+    }
     __syncthreads();
     if (ok) {
         // iterative refinement: x += L^-T L^-1 r
         ok = false;
+        float dprev = 0.0f;
         for (int it = 0; it <= a.refine_max_iter; ++it) {
-            for (int q = tid; q < k; q += NT) S.w[q] = (float)S.rr[q];
+            for (int q = tid; q < k; q += NT) R.w[q] = (float)R.rr[q];
             __syncthreads();
-            forward32(sm, S.L, ld, S.w, k);
-            backward32(sm, S.L, ld, S.w, k);
+            forward32(sm, R.L, ld, R.w, k);
+            backward32(sm, R.L, ld, R.w, k);
+            tm.lap(kPhSolve);
             float dmax = 0.0f, xmax = 0.0f;
             for (int q = tid; q < k; q += NT) {
-                const double xn = S.xs[q] + (double)S.w[q];
-                S.xs[q] = xn;
-                dmax = fmaxf(dmax, fabsf(S.w[q]));
+                const double xn = R.xs[q] + (double)R.w[q];
+                R.xs[q] = xn;
+                dmax = fmaxf(dmax, fabsf(R.w[q]));
                 xmax = fmaxf(xmax, fabsf((float)xn));
             }
             dmax = block_max(sm, dmax);
             xmax = block_max(sm, xmax);
-            if (!(dmax == dmax) || !(xmax == xmax)) break;            // NaN: give up
-            if (it >= 1 && dmax <= (float)a.refine_tol * xmax) { ok = true; break; }
-            if (it >= 1 && dmax > 0.5f * xmax) break;                  // not contracting
+            if (!(dmax == dmax) || !(xmax == xmax)) {                 // NaN: give up
+                if (a.phase_cycles && tid == 0) atomicAdd(a.phase_cycles + kPhFailNaN, 1ull);
+                break;
+            }
+            if (it >= 1) {
+                if (dmax > 0.5f * dprev) {                             // not contracting
+                    if (a.phase_cycles && tid == 0) atomicAdd(a.phase_cycles + kPhFailStall, 1ull);
+                    break;
+                }
+                // error left after this correction ~ |d_i| * (|d_i| / |d_i-1|)
+                const float est = dmax * (dmax / fmaxf(dprev, 1e-30f));
+                if (est <= (float)a.refine_tol * xmax) { ok = true; break; }
+            }
+            dprev = dmax;
             if (it == a.refine_max_iter) break;
             for (int q = tid; q < k; q += NT) {
-                const df v = dfm::from_double(S.xs[q]);
-                S.qh[q] = v.h;
-                S.ql[q] = v.l;
+                const df v = dfm::from_double(R.xs[q]);
+                R.qh[q] = v.h;
+                R.ql[q] = v.l;
             }
             __syncthreads();
-            residual_df(sm, S, k, inv_rho, lam);
+            residual_df(sm, keep.tbl, R, k, inv_rho, lam);
+            tm.lap(kPhResidual);
+            if (a.phase_cycles && tid == 0) atomicAdd(a.phase_cycles + kPhResidualPasses, 1ull);
         }
         if (k == 0) ok = true;
     }
@@ -667,33 +889,39 @@ __device__ void run_task(SmemM& sm, TcCtx* tc, const TaskArgs& a, int t, int i, 
 
     // predict (Eq. 3) in double-float, squared errors in FP64 (Eq. 4)
     for (int q = tid; q < k; q += NT) {
-        const df v = dfm::from_double(S.xs[q]);
-        S.qh[q] = v.h;
-        S.ql[q] = v.l;
+        const df v = dfm::from_double(R.xs[q]);
+        R.qh[q] = v.h;
+        R.ql[q] = v.l;
     }
     __syncthreads();
-    for (int j = warp; j < m; j += NT / 32) {
-        const df px = dfm::from_double((a.Px[p0 + j] - ox) * sc), py = dfm::from_double((a.Py[p0 + j] - oy) * sc);
-        const Pt P{px.h, px.l, py.h, py.l};
-        dfm::acc s;
+    for (int j0 = 2 * warp; j0 < m; j0 += 2 * (NT / 32)) {   // two prediction points per warp
+        const int j1 = min(j0 + 1, m - 1);
+        const df px0 = dfm::from_double((a.Px[p0 + j0] - ox) * sc), py0 = dfm::from_double((a.Py[p0 + j0] - oy) * sc);
+        const df px1 = dfm::from_double((a.Px[p0 + j1] - ox) * sc), py1 = dfm::from_double((a.Py[p0 + j1] - oy) * sc);
+        const Pt P0{px0.h, px0.l, py0.h, py0.l}, P1{px1.h, px1.l, py1.h, py1.l};
+        dfm::acc s0, s1;
         for (int q = lane; q < k; q += 32) {
-            const Pt Q{S.xh[q], S.xl[q], S.yh[q], S.yl[q]};
-            s.add_prod(exp_neg_sm(sm, t_any(P, Q, inv_rho)), df{S.qh[q], S.ql[q]});
+            const Pt Q{R.xh[q], R.xl[q], R.yh[q], R.yl[q]};
+            const df xq{R.qh[q], R.ql[q]};
+            s0.add_prod(exp_neg_sm(keep.tbl, t_any(P0, Q, inv_rho)), xq);
+            s1.add_prod(exp_neg_sm(keep.tbl, t_any(P1, Q, inv_rho)), xq);
         }
-        double v = (double)s.h + (double)s.l;
-        v = warp_sum_d(v);
-        if (lane == 0) {
+        const double v0 = warp_sum_d((double)s0.h + (double)s0.l);
+        const double v1 = warp_sum_d((double)s1.h + (double)s1.l);
+        if (lane < 2 && (lane == 0 || j1 != j0)) {
+            const int j = lane == 0 ? j0 : j1;
+            const double v = lane == 0 ? v0 : v1;
             if (a.yhat) a.yhat[(int64_t)b * a.yhat_stride + p0 + j] = v;
             if (a.Pv) {
                 const double e = v - a.Pv[p0 + j];
-                S.ep[j] = e * e;
+                R.ep[j] = e * e;
             }
         }
     }
     __syncthreads();
     if (a.Pv) {
         double s = 0.0;
-        for (int j = tid; j < m; j += NT) s += S.ep[j];
+        for (int j = tid; j < m; j += NT) s += R.ep[j];
         s = warp_sum_d(s);
         if (lane == 0) sm.dred[warp] = s;
         __syncthreads();
@@ -705,36 +933,62 @@ __device__ void run_task(SmemM& sm, TcCtx* tc, const TaskArgs& a, int t, int i, 
     }
     if (tid == 0) a.tstatus[zoff] = PCV_OK;
     __syncthreads();
+    tm.lap(kPhPredict);
+    if (a.phase_cycles && tid == 0) {
+        atomicAdd(a.phase_cycles + kPhTask, (unsigned long long)(now_cycles() - t_task));
+        atomicAdd(a.phase_cycles + kPhTasks, 1ull);
+    }
 }
 
 __global__ void __launch_bounds__(NT, 2) k_cv_mixed(TaskArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    // layout: SmemM, SmemSimt (both 16-byte aligned sizes), then SmemKeep
     SmemM& sm = *reinterpret_cast<SmemM*>(smem_raw);
-    for (int e = threadIdx.x; e < 2 * dfm::kExpTable; e += NT) sm.tbl[e] = c_exp.tbl[e];
+    SmemSimt& simt = *reinterpret_cast<SmemSimt*>(smem_raw + sizeof(SmemM));
+    SmemKeep& keep = *reinterpret_cast<SmemKeep*>(smem_raw + sizeof(SmemM) + sizeof(SmemSimt));
+    for (int e = threadIdx.x; e < 2 * dfm::kExpTable; e += NT) keep.tbl[e] = c_exp.tbl[e];
     __syncthreads();
     const int ntask = a.n_order * a.B;
     for (;;) {
-        if (threadIdx.x == 0) sm.task = (int)atomicAdd(a.counter, 1u);
+        if (threadIdx.x == 0) keep.task = (int)atomicAdd(a.counter, 1u);
         __syncthreads();
-        const int t = sm.task;
+        const int t = keep.task;
         __syncthreads();
         if (t >= ntask) break;
-        run_task<false>(sm, nullptr, a, t, a.order[t / a.B], t % a.B);
+        run_task<false>(sm, keep, &simt, nullptr, a, t, a.order[t / a.B], t % a.B);
     }
 }
 
-constexpr int kTcSmem = 1024 + umma::kStages * umma::kStageBytes + (int)sizeof(SmemM) + (int)sizeof(TcShared);
+constexpr int kSimtSmem = (int)(sizeof(SmemM) + sizeof(SmemKeep) + sizeof(SmemSimt));
+static_assert(sizeof(SmemM) % 16 == 0 && sizeof(SmemSimt) % 16 == 0 && alignof(SmemSimt) == 16,
+              "SmemSimt must start on a 16-byte boundary after SmemM");
+// tensor-core kernel layout (offsets from the 1024-aligned base): operand ring, then
+// the persistent struct, then the pipeline barriers (8-byte aligned mbarriers)
+// tensor-core kernel layout (offsets from the 1024-aligned base) for a ring of
+// `nst` stages: operand ring, then the persistent struct, then the pipeline barriers
+__host__ __device__ constexpr int tc_keep_off(int nst) { return nst * kTcStage; }
+__host__ __device__ constexpr int tc_sh_off(int nst) { return (tc_keep_off(nst) + (int)sizeof(SmemKeep) + 127) / 128 * 128; }
+__host__ __device__ constexpr int tc_smem(int nst) { return 1024 + tc_sh_off(nst) + (int)sizeof(TcShared); }
+constexpr int kTcSmem = tc_smem(umma::kStages);
+static_assert(tc_keep_off(2) % 16 == 0 && tc_sh_off(2) % 128 == 0, "shared-memory layout alignment");
+static_assert(kTcSmem <= 227 * 1024, "tensor-core kernel exceeds the shared memory of one CTA");
+static_assert(sizeof(SmemM) <= (size_t)2 * kTcStage && sizeof(SmemM) % 16 == 0,
+              "phase scratch must fit in a 2-stage ring, vectors after it 16-byte aligned");
+static_assert(TB * DP * 4 + 2 * TB * 4 + 16 <= 2 * kTcStage, "diagonal block must fit in a 2-stage ring");
+static_assert(2 * tc_smem(2) <= 228 * 1024, "two tensor-core CTAs must fit on one SM");
 
-// Tensor-core variant: one CTA per SM (it holds all 512 TMEM columns).
-__global__ void __launch_bounds__(NT, 1) k_cv_mixed_tc(TaskArgs a, const __grid_constant__ CUtensorMap m0,
+// Tensor-core variant: two CTAs per SM, 256 TMEM columns each.
+__global__ void __launch_bounds__(NT, 2) k_cv_mixed_tc(TaskArgs a, const __grid_constant__ CUtensorMap m0,
                                                        const __grid_constant__ CUtensorMap m1,
                                                        const __grid_constant__ CUtensorMap m2) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     TcCtx tc;
     tc.stages = base;
-    SmemM& sm = *reinterpret_cast<SmemM*>(base + umma::kStages * umma::kStageBytes);
-    tc.sh = reinterpret_cast<TcShared*>(base + umma::kStages * umma::kStageBytes + sizeof(SmemM));
+    SmemM& sm = *reinterpret_cast<SmemM*>(base);   // phase scratch shares the operand ring
+    const int nst = a.tc_stages;
+    SmemKeep& keep = *reinterpret_cast<SmemKeep*>(base + tc_keep_off(nst));
+    tc.sh = reinterpret_cast<TcShared*>(base + tc_sh_off(nst));
     tc.m0 = &m0;
     tc.m1 = &m1;
     tc.m2 = &m2;
@@ -745,30 +999,30 @@ __global__ void __launch_bounds__(NT, 1) k_cv_mixed_tc(TaskArgs a, const __grid_
     tc.p2 = P + 2 * a.plane_elems + blockIdx.x * slot_elems;
     tc.row_base = blockIdx.x * a.ld;
     const int warp = threadIdx.x >> 5;
-    for (int e = threadIdx.x; e < 2 * dfm::kExpTable; e += NT) sm.tbl[e] = c_exp.tbl[e];
+    for (int e = threadIdx.x; e < 2 * dfm::kExpTable; e += NT) keep.tbl[e] = c_exp.tbl[e];
     if (threadIdx.x == 0) {
-        umma::pipe_init(tc.sh->pipe);
+        umma::pipe_init(tc.sh->pipe, (uint32_t)nst);
         tc.sh->dead = 0;
         umma::prefetch_map(&m0);
         umma::prefetch_map(&m1);
         umma::prefetch_map(&m2);
     }
-    if (warp == 1) umma::tmem_alloc(&tc.sh->pipe.tmem_base, umma::kTmemCols);
+    if (warp == 1) umma::tmem_alloc(&tc.sh->pipe.tmem_base, kTcTmemCols);
     umma::tc_fence_before();
     __syncthreads();
     umma::tc_fence_after();
     const int ntask = a.n_order * a.B;
     for (;;) {
-        if (threadIdx.x == 0) sm.task = (int)atomicAdd(a.counter, 1u);
+        if (threadIdx.x == 0) keep.task = (int)atomicAdd(a.counter, 1u);
         __syncthreads();
-        const int t = sm.task;
+        const int t = keep.task;
         __syncthreads();
         if (t >= ntask) break;
-        run_task<true>(sm, &tc, a, t, a.order[t / a.B], t % a.B);
+        run_task<true>(sm, keep, nullptr, &tc, a, t, a.order[t / a.B], t % a.B);
     }
     umma::tc_fence_before();
     __syncthreads();
-    if (warp == 1) umma::tmem_dealloc(tc.sh->pipe.tmem_base, umma::kTmemCols);
+    if (warp == 1) umma::tmem_dealloc(tc.sh->pipe.tmem_base, kTcTmemCols);
 }
 
 std::mutex g_prep_mu;
@@ -789,7 +1043,7 @@ int mixed_prepare(int device) {
     dfm::exp_constants(k);
     cudaError_t e = cudaMemcpyToSymbol(c_exp, &k, sizeof(k));
     if (e != cudaSuccess) return (int)e;
-    e = cudaFuncSetAttribute(k_cv_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SmemM));
+    e = cudaFuncSetAttribute(k_cv_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, kSimtSmem);
     if (e != cudaSuccess) return (int)e;
     e = cudaFuncSetAttribute(k_cv_mixed_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
     if (e != cudaSuccess) return (int)e;
@@ -800,9 +1054,10 @@ int mixed_prepare(int device) {
 int launch_task_mixed(const TaskArgs& a, const void* maps, int engine, int grid, void* stream) {
     if (engine == kMixedEngineTensor) {
         const CUtensorMap* m = reinterpret_cast<const CUtensorMap*>(maps);
-        k_cv_mixed_tc<<<grid, NT, kTcSmem, (cudaStream_t)stream>>>(a, m[0], m[1], m[2]);
+        if (a.tc_stages < 2 || a.tc_stages > umma::kStages) return (int)cudaErrorInvalidValue;
+        k_cv_mixed_tc<<<grid, NT, tc_smem(a.tc_stages), (cudaStream_t)stream>>>(a, m[0], m[1], m[2]);
     } else {
-        k_cv_mixed<<<grid, NT, sizeof(SmemM), (cudaStream_t)stream>>>(a);
+        k_cv_mixed<<<grid, NT, kSimtSmem, (cudaStream_t)stream>>>(a);
     }
     count_launch();
     return (int)cudaGetLastError();
@@ -811,8 +1066,9 @@ int launch_task_mixed(const TaskArgs& a, const void* maps, int engine, int grid,
 bool mixed_make_maps(void* planes, int64_t plane_elems, int32_t ld, int grid, void* maps_out) {
     CUtensorMap* m = reinterpret_cast<CUtensorMap*>(maps_out);
     __nv_bfloat16* P = reinterpret_cast<__nv_bfloat16*>(planes);
+    const uint64_t tiles = (uint64_t)grid * (ld / umma::kTileM) * (ld / umma::kChunkK);
     for (int p = 0; p < 3; ++p)
-        if (!umma::make_plane_map(&m[p], P + p * plane_elems, (uint64_t)ld, (uint64_t)grid * ld)) return false;
+        if (!umma::make_tiled_map(&m[p], P + p * plane_elems, tiles)) return false;
     return true;
 }
 

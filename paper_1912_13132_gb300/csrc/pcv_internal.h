@@ -68,7 +68,15 @@ struct TaskArgs {
     // plane_elems elements laid out as (slot * ld + row) * ld + column
     void* planes;
     int64_t plane_elems;
+    // optional per-phase cycle counters (kPhaseCount entries, summed over CTAs), or NULL
+    unsigned long long* phase_cycles;
+    int32_t tc_stages;      // TMA ring depth of the tensor-core kernel (2 or 3)
 };
+
+// Phases timed by the mixed kernel when phase_cycles is set.
+enum Phase { kPhGather = 0, kPhUpdate, kPhDiag, kPhPanel, kPhSplit, kPhFactorSimt, kPhSolve, kPhResidual,
+             kPhPredict, kPhTask, kPhResidualPasses, kPhTasks, kPhFailFactor, kPhFailNaN, kPhFailStall,
+             kPhaseCount = 16 };
 
 // Kernel launchers (one per precision); return the cudaError_t as int.
 int launch_task_fp64(const TaskArgs& a, int grid, void* stream);

@@ -10,7 +10,7 @@
 // hi*hi + hi*mid + mid*hi + hi*lo + lo*hi + mid*mid reproduce FP32-accurate
 // products while running on the BF16 tensor pipe.
 //
-// Roles (256 threads):  warp 0 lane 0 issues TMA loads into a 2-stage ring,
+// Roles (256 threads):  warp 0 lane 0 issues TMA loads into a 3-stage ring,
 // warp 1 lane 0 issues the MMAs, warps 4..7 (one per TMEM lane quadrant) drain the
 // accumulators through the caller's epilogue.  Two 128-row tiles form one pass;
 // the accumulators of consecutive passes alternate between two TMEM buffers so the
@@ -31,10 +31,11 @@ constexpr int kTileM = 128;        // rows per tile (MMA M)
 constexpr int kTileN = 128;        // block-column width (MMA N)
 constexpr int kChunkK = 32;        // BF16 elements per TMA box row (64 bytes, 64B swizzle)
 constexpr int kPlanes = 3;
-constexpr int kTilesPerPass = 2;
-constexpr int kStages = 2;
+constexpr int kTilesPerPass = 2;   // default tiles per pass (template parameter TPP below)
+constexpr int kStages = 3;          // maximum ring depth (runtime depth in Pipe::nstages)
 constexpr int kTileBytes = kTileM * kChunkK * 2;                    // 8 KB
 constexpr int kStageBytes = kPlanes * (kTilesPerPass + 1) * kTileBytes;   // 72 KB
+__host__ __device__ constexpr int stage_bytes(int tpp) { return kPlanes * (tpp + 1) * kTileBytes; }
 constexpr uint32_t kTmemCols = 512;
 constexpr uint64_t kWaitNs = 2000000000ull;  // bound of every mbarrier wait (2 s)
 
@@ -90,6 +91,14 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
         "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
             smem_u32(dst)),
         "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int c0, int c1, int c2,
+                                            uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
+            smem_u32(dst)),
+        "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
         : "memory");
 }
 __device__ __forceinline__ void prefetch_map(const CUtensorMap* map) {
@@ -183,7 +192,7 @@ struct Pipe {
     uint64_t accf[2];
     uint64_t acce[2];
     uint32_t tmem_base;
-    uint32_t pad;
+    uint32_t nstages;     // ring depth in use (1 .. kStages)
 };
 
 // Per-role phase counters; every role walks the same sequence of stages and passes.
@@ -192,7 +201,8 @@ struct Phases {
     uint32_t pass = 0;    // passes done (accumulator buffer and parity)
 };
 
-__device__ inline void pipe_init(Pipe& p) {
+__device__ inline void pipe_init(Pipe& p, uint32_t nstages = kStages) {
+    p.nstages = nstages;
     for (int s = 0; s < kStages; ++s) {
         mbar_init(&p.full[s], 1);
         mbar_init(&p.empty[s], 1);
@@ -214,13 +224,23 @@ __host__ __device__ constexpr int prod_b(int q) { return q == 1 ? 1 : q == 3 ? 2
 //   offset `row_base` (the task's slot).  For each finished 128-row tile the
 //   epilogue warps call epi(tile_row0, warp_quadrant, taddr_of_tile) and must read
 //   all 128 columns of their 32 lanes.  Returns false if a bounded wait ran out.
-template <class Epi>
+// Operand layouts in global memory.  Row-major: a plane is a row-major matrix and a
+// box is 128 rows x 32 columns of it.  Tiled: a plane is stored as contiguous 8 KB
+// tiles of 128 rows x 32 columns (tile (R, kc) at index R * nkc + kc), so that every
+// box is one contiguous block of memory; `nkc` = columns / 32.
+template <bool TILED>
+__device__ __forceinline__ void load_box(void* dst, const CUtensorMap* map, int kc, int row, int nkc, uint64_t* bar) {
+    if constexpr (TILED) tma_load_3d(dst, map, 0, 0, (row / kTileM) * nkc + kc, bar);
+    else tma_load_2d(dst, map, kc * kChunkK, row, bar);
+}
+
+template <bool TILED = false, int TPP = kTilesPerPass, class Epi>
 __device__ bool block_column(Pipe& P, Phases& ph, uint8_t* stages, const CUtensorMap* mapA0,
                              const CUtensorMap* mapA1, const CUtensorMap* mapA2, int row_base, int r0,
-                             int nrows, int b0, int K, Epi&& epi) {
+                             int nrows, int b0, int K, Epi&& epi, int nkc = 0) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int ntiles = (nrows + kTileM - 1) / kTileM;
-    const int npass = (ntiles + kTilesPerPass - 1) / kTilesPerPass;
+    const int npass = (ntiles + TPP - 1) / TPP;
     const int nk = K / kChunkK;
     const CUtensorMap* maps[3] = {mapA0, mapA1, mapA2};
     bool ok = true;
@@ -228,19 +248,19 @@ __device__ bool block_column(Pipe& P, Phases& ph, uint8_t* stages, const CUtenso
         // TMA producer
         uint32_t it = ph.stage;
         for (int p = 0; p < npass && ok; ++p) {
-            const int t0 = p * kTilesPerPass;
-            const int nt = min(kTilesPerPass, ntiles - t0);
+            const int t0 = p * TPP;
+            const int nt = min(TPP, ntiles - t0);
             for (int kc = 0; kc < nk; ++kc, ++it) {
-                const int s = it % kStages;
-                const uint32_t par = ((it / kStages) & 1) ^ 1;
+                const int s = it % P.nstages;
+                const uint32_t par = ((it / P.nstages) & 1) ^ 1;
                 if (!mbar_wait(&P.empty[s], par)) { ok = false; break; }
-                uint8_t* st = stages + s * kStageBytes;
+                uint8_t* st = stages + s * stage_bytes(TPP);
                 mbar_expect_tx(&P.full[s], (uint32_t)(kPlanes * (nt + 1) * kTileBytes));
                 for (int pl = 0; pl < kPlanes; ++pl) {
-                    tma_load_2d(st + pl * kTileBytes, maps[pl], kc * kChunkK, row_base + b0, &P.full[s]);
+                    load_box<TILED>(st + pl * kTileBytes, maps[pl], kc, row_base + b0, nkc, &P.full[s]);
                     for (int t = 0; t < nt; ++t)
-                        tma_load_2d(st + (kPlanes + t * kPlanes + pl) * kTileBytes, maps[pl], kc * kChunkK,
-                                    row_base + r0 + (t0 + t) * kTileM, &P.full[s]);
+                        load_box<TILED>(st + (kPlanes + t * kPlanes + pl) * kTileBytes, maps[pl], kc,
+                                        row_base + r0 + (t0 + t) * kTileM, nkc, &P.full[s]);
                 }
             }
         }
@@ -249,19 +269,19 @@ __device__ bool block_column(Pipe& P, Phases& ph, uint8_t* stages, const CUtenso
         uint32_t it = ph.stage;
         const uint32_t idesc = idesc_bf16(kTileM, kTileN);
         for (int p = 0; p < npass && ok; ++p) {
-            const int t0 = p * kTilesPerPass;
-            const int nt = min(kTilesPerPass, ntiles - t0);
+            const int t0 = p * TPP;
+            const int nt = min(TPP, ntiles - t0);
             const uint32_t pp = ph.pass + p;
             const int buf = pp & 1;
             if (!mbar_wait(&P.acce[buf], ((pp >> 1) & 1) ^ 1)) { ok = false; break; }
             tc_fence_after();
             for (int kc = 0; kc < nk; ++kc, ++it) {
-                const int s = it % kStages;
-                if (!mbar_wait(&P.full[s], (it / kStages) & 1)) { ok = false; break; }
+                const int s = it % P.nstages;
+                if (!mbar_wait(&P.full[s], (it / P.nstages) & 1)) { ok = false; break; }
                 tc_fence_after();
-                const uint32_t st = smem_u32(stages + s * kStageBytes);
+                const uint32_t st = smem_u32(stages + s * stage_bytes(TPP));
                 for (int t = 0; t < nt; ++t) {
-                    const uint32_t d = P.tmem_base + buf * (kTilesPerPass * kTileN) + t * kTileN;
+                    const uint32_t d = P.tmem_base + buf * (TPP * kTileN) + t * kTileN;
 #pragma unroll
                     for (int kk = 0; kk < kChunkK / 16; ++kk)
 #pragma unroll
@@ -280,15 +300,15 @@ __device__ bool block_column(Pipe& P, Phases& ph, uint8_t* stages, const CUtenso
         // epilogue: one warp per TMEM lane quadrant
         const int quad = warp & 3;
         for (int p = 0; p < npass && ok; ++p) {
-            const int t0 = p * kTilesPerPass;
-            const int nt = min(kTilesPerPass, ntiles - t0);
+            const int t0 = p * TPP;
+            const int nt = min(TPP, ntiles - t0);
             const uint32_t pp = ph.pass + p;
             const int buf = pp & 1;
             if (!mbar_wait(&P.accf[buf], (pp >> 1) & 1)) { ok = false; break; }
             tc_fence_after();
             for (int t = 0; t < nt; ++t) {
                 const uint32_t taddr = P.tmem_base + ((uint32_t)(quad * 32) << 16) +
-                                       buf * (kTilesPerPass * kTileN) + t * kTileN;
+                                       buf * (TPP * kTileN) + t * kTileN;
                 epi(r0 + (t0 + t) * kTileM, quad, taddr);
             }
             tc_fence_before();
@@ -324,6 +344,28 @@ inline bool make_plane_map(CUtensorMap* map, void* base, uint64_t inner, uint64_
     cuuint32_t box[2] = {(cuuint32_t)kChunkK, (cuuint32_t)kTileM};
     cuuint32_t estr[2] = {1, 1};
     return encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// 3-D tensor map over a tiled BF16 plane (see load_box): dims (32, 128, tiles), box
+// (32, 128, 1), 64-byte swizzle.
+inline bool make_tiled_map(CUtensorMap* map, void* base, uint64_t tiles) {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        cudaDriverEntryPointQueryResult q;
+        void* fn = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn)
+            return false;
+        encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    }
+    cuuint64_t dims[3] = {(cuuint64_t)kChunkK, (cuuint64_t)kTileM, tiles};
+    cuuint64_t strides[2] = {(cuuint64_t)kChunkK * 2, (cuuint64_t)kChunkK * kTileM * 2};
+    cuuint32_t box[3] = {(cuuint32_t)kChunkK, (cuuint32_t)kTileM, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    return encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, estr,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }

@@ -35,7 +35,7 @@ class pcv_layout(ctypes.Structure):
 class pcv_options(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_int32), ("max_slots", ctypes.c_int32),
                 ("workspace_fraction", ctypes.c_double), ("refine_max_iter", ctypes.c_int32),
-                ("refine_tol", ctypes.c_double), ("factor_engine", ctypes.c_int32)]
+                ("refine_tol", ctypes.c_double), ("factor_engine", ctypes.c_int32), ("tc_stages", ctypes.c_int32)]
 
 
 class PcvError(RuntimeError):
@@ -68,6 +68,7 @@ _SIGS = {
     "pcv_predict": (ctypes.c_int, [_vp, _dp, _dp, ctypes.c_int64, ctypes.c_int32, _dp, _vp]),
     "pcv_set_timing": (ctypes.c_int, [_vp, ctypes.c_int32]),
     "pcv_kernel_time": (ctypes.c_int, [_vp, _dp, _dp]),
+    "pcv_phase_cycles": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_uint64), ctypes.c_int32]),
     "pcv_cv_loss_fp64_static": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int32, _i64p, _vp, _i64p, _vp, _vp,
                                                _vp, _vp, ctypes.c_int32, _vp, _vp, _vp, _vp]),
     "pcv_selftest_df": (ctypes.c_int, [ctypes.c_int32, _dp, _dp, ctypes.c_int64, _dp]),
@@ -185,13 +186,13 @@ class Context:
 
     def __init__(self, xy, v, role, layout: dict, device: int = 0, max_slots: int = 0,
                  workspace_fraction: float = 0.0, refine_max_iter: int = 0, refine_tol: float = 0.0,
-                 factor_engine: str = "tensor"):
+                 factor_engine: str = "tensor", tc_stages: int = 0):
         xy = _f64(xy).reshape(-1, 2)
         v = _f64(v)
         role = np.ascontiguousarray(role, dtype=np.uint8)
         L, keep = make_layout(layout)
         o = pcv_options(ctypes.sizeof(pcv_options), max_slots, workspace_fraction, refine_max_iter,
-                        refine_tol, {"tensor": 0, "simt": 1}[factor_engine])
+                        refine_tol, {"tensor": 0, "simt": 1}[factor_engine], tc_stages)
         h = _vp()
         _check(_lib.pcv_create(_ptr(xy, _dp), _ptr(v, _dp), _ptr(role, _u8p), len(v), ctypes.byref(L),
                                device, ctypes.byref(o), ctypes.byref(h)), "pcv_create")
@@ -252,6 +253,16 @@ class Context:
         t, c = ctypes.c_double(), ctypes.c_double()
         _check(_lib.pcv_kernel_time(self._h, ctypes.byref(t), ctypes.byref(c)), "pcv_kernel_time")
         return t.value, c.value
+
+    PHASES = ("gather_assemble", "tc_update", "diag", "panel_solve", "split", "factor_simt", "solves",
+              "residual", "predict_loss", "task", "residual_passes", "tasks", "fail_factor", "fail_nan",
+              "fail_stall")
+
+    def phase_cycles(self, reset: bool = False) -> dict:
+        """Per-phase SM cycles of the mixed kernel (see include/pcv.h)."""
+        out = (ctypes.c_uint64 * 16)()
+        _check(_lib.pcv_phase_cycles(self._h, out, 1 if reset else 0), "pcv_phase_cycles")
+        return {name: int(out[i]) for i, name in enumerate(self.PHASES)}
 
     def predict(self, params3, xy_new, precision="mixed", stream=None):
         p = _f64(params3).reshape(3)

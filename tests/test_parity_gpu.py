@@ -158,7 +158,8 @@ def test_paper_scale_sampled(gpu_lib, paper5m, prec, B):
     for b in range(0, B, max(1, B // 2)):
         ref = oracle.cv_loss(w.xy, w.v, w.role, w.layout, P[b:b + 1], members=members, subsets=pick)
         sub = dict(z=out["z"][b:b + 1], yhat=out["yhat"][b:b + 1], sspe=out["sspe"][b:b + 1])
-        compare(sub, ref, V_off, pick, 1, prec, check_total=False)
+        worst = compare(sub, ref, V_off, pick, 1, prec, check_total=False)
+        print("paper-scale", prec, b, worst)
 
 
 @pytest.mark.parametrize("engine", ["tensor", "simt"])
@@ -174,4 +175,5 @@ def test_mixed_engines(gpu_lib, engine):
     members = oracle.all_members(w.xy, w.role, w.layout)
     ref = oracle.cv_loss(w.xy, w.v, w.role, w.layout, P, members=members)
     assert np.all(out["status"] == 0), out["status"]
-    compare(out, ref, V_off, range(16), len(P), "mixed")
+    worst = compare(out, ref, V_off, range(16), len(P), "mixed")
+    print("mixed", engine, worst)
