@@ -117,6 +117,33 @@ class ClockSampler:
                     reasons=sorted(reasons), samples=len(sm))
 
 
+def kernel_code_hash(sources) -> str:
+    """sha256 of the kernel sources with // comments and blank lines removed (comment
+    edits do not change the compiled kernel, code edits do)."""
+    import hashlib
+    h = hashlib.sha256()
+    for src in sources:
+        for line in open(os.path.join(ROOT, src)).read().splitlines():
+            code = line.split("//", 1)[0].rstrip()
+            if code:
+                h.update(code.encode() + b"\n")
+    return h.hexdigest()
+
+
+def recorded_traffic(tasks_per_launch: int):
+    """DRAM bytes of one task-kernel launch from the committed ncu record
+    (profiles/task_kernel_traffic.txt), or None when the kernel sources changed since
+    the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "task_kernel_traffic.txt")
+    try:
+        rec = json.load(open(path))
+        if kernel_code_hash(rec["sources"]) != rec["source_sha256"]:
+            return None, "kernel changed since the ncu capture"
+        return rec["dram_bytes_per_task"] * tasks_per_launch, rec["note"]
+    except Exception as e:  # pragma: no cover
+        return None, f"no traffic record ({type(e).__name__})"
+
+
 def task_sizes(ctx):
     k = np.diff(ctx.T_off)
     m = np.diff(ctx.V_off)
@@ -203,6 +230,7 @@ def main():
     ap.add_argument("--max-slots", type=int, default=0, help="limit concurrent tasks (profiling runs)")
     ap.add_argument("--engine", default="tensor", choices=["tensor", "simt"])
     ap.add_argument("--tc-stages", type=int, default=0, help="TMA ring depth of the tensor engine (2 or 3)")
+    ap.add_argument("--refine-tol", type=float, default=0.0, help="refinement tolerance (0: library default)")
     args = ap.parse_args()
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
@@ -232,7 +260,7 @@ def main():
     t_gen = time.perf_counter() - t_setup
     t0 = time.perf_counter()
     ctx = pcv.Context(w.xy, w.v, w.role, w.layout, device=local, max_slots=args.max_slots,
-                      factor_engine=args.engine, tc_stages=args.tc_stages)
+                      factor_engine=args.engine, tc_stages=args.tc_stages, refine_tol=args.refine_tol)
     t_create = time.perf_counter() - t0
     k, m = task_sizes(ctx)
     B = args.batch
@@ -316,9 +344,11 @@ def main():
             sm_max = (clk.get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0))
             peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12
             peak_note = "FP32 FMA: 152 SMs x 128 lanes x 2 flop x max SM clock"
+    traffic, traffic_note = (recorded_traffic(len(k) * B) if (args.precision == "mixed" and args.engine == "tensor")
+                             else (None, "no ncu record for this kernel"))
     roof = dict(bound=bound, achieved=achieved, peak=peak, unit="TFLOP/s", frac=achieved / peak if peak else None,
-                traffic=None, peak_source=peak_note, kernel="task kernel (persistent)",
-                flops_per_launch=flops, launch_ms=t_task * 1e3)
+                traffic=traffic, traffic_note=traffic_note, peak_source=peak_note,
+                kernel="task kernel (persistent)", flops_per_launch=flops, launch_ms=t_task * 1e3)
 
     line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
                 ms_per_step=total_s * 1e3 / args.steps, higher_is_better=True, scaling="weak",

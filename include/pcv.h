@@ -102,7 +102,7 @@ typedef struct {
     int32_t refine_max_iter;   /* mixed path: maximum refinement corrections (default 6) */
     double refine_tol;         /* mixed path: stop once the error left after correction i,
                                   estimated as ||d_i|| * ||d_i|| / ||d_i-1||, is at most
-                                  tol * ||x|| (max norms; default 1e-8); tasks whose
+                                  tol * ||x|| (max norms; default 1e-7); tasks whose
                                   corrections stop shrinking are recomputed in FP64 */
     int32_t factor_engine;     /* mixed path factorisation: 0 = tensor cores (split-BF16
                                   tcgen05 trailing updates, default), 1 = FP32 SIMT */

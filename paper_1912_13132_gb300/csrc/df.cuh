@@ -67,12 +67,21 @@ PCV_HD df from_double(double v) {
 }
 PCV_HD double to_double(df a) { return (double)a.h + (double)a.l; }
 
-// sqrt of a non-negative double-float (one Newton correction on the FP32 root)
+// sqrt of a non-negative double-float: an approximate FP32 root s = a.h / sqrt(a.h)
+// from the reciprocal square root, then one correction with the exact residual
+// a - s^2 (FMA): s + (a - s^2) / (2 s).  The correction's own relative error (that of
+// the approximate reciprocal, ~2^-22) multiplies a term of size ~2^-22 s, so the
+// result carries ~44 correct bits.
 PCV_HD df sqrt_df(df a) {
     if (!(a.h > 0.0f)) return {0.0f, 0.0f};
-    const float s = sqrtf(a.h);
+#if defined(__CUDA_ARCH__)
+    const float r = rsqrtf(a.h);
+#else
+    const float r = 1.0f / std::sqrt(a.h);
+#endif
+    const float s = a.h * r;
     const float e = fmaf(-s, s, a.h) + a.l;
-    return fast_two_sum(s, e * (0.5f / s));
+    return fast_two_sum(s, e * (0.5f * r));
 }
 
 // Accumulator for sums of double-float products (Ogita-Rump-Oishi style: the

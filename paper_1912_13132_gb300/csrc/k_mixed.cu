@@ -2,14 +2,16 @@
 //
 // Same task decomposition as the FP64 path (Algorithm 1's parallel loop over
 // subsets, extended over the batch of configurations), different arithmetic:
-//   gather     training coordinates as scaled offsets from the subset's first
-//              training point, split in double-float (high parts on a 2^-20 grid
-//              so that differences of high parts are exact)
+//   gather     training coordinates as offsets from the subset's first training
+//              point in units of rho, split in double-float (high parts on a
+//              power-of-two grid so that differences of high parts are exact)
 //   assemble   A32 = Sigma(rho) + lambda I in FP32                  (Eq. 3, Sec. 3)
-//   factor     A32 ~ L L^T in FP32, left-looking, 64-wide block columns
+//   factor     A32 ~ L L^T, left-looking: tensor engine (k_cv_mixed_tc) with
+//              128-wide block columns whose trailing updates run on tcgen05 from
+//              split-BF16 planes; FP32 engine (k_cv_mixed) with 64-wide blocks
 //   refine     x <- x + L^-T L^-1 r,  r = y - A x with A's entries and the sums
-//              in double-float (exp by Tang's method, see df.cuh), until the last
-//              correction is below refine_tol of the solution
+//              in double-float (exp by Tang's method, see df.cuh), until the error
+//              left, estimated as |d_i|^2 / |d_i-1|, is below refine_tol |x|
 //   predict    yhat_j = sum_a exp(-||p_j - s_a|| / rho) x_a in double-float (Eq. 3)
 //   loss       z = sum_j (yhat_j - y_V,j)^2 in FP64                  (Eq. 4)
 // A task whose FP32 factorisation breaks down or whose refinement does not
@@ -31,7 +33,6 @@ using dfm::df;
 constexpr int NB = 64;   // block-column width of the factorisation and of the residual tiles
 constexpr int NT = 256;  // threads per CTA
 constexpr int KC = 16;   // K chunk of the trailing update
-constexpr double QSCALE = 1048576.0;  // 2^20: grid of the high parts of training coordinates
 
 __constant__ dfm::ExpConsts c_exp;
 
@@ -588,20 +589,21 @@ struct Pt {
     float xh, xl, yh, yl;
 };
 
-// t = ||p - q|| / rho in double-float; the high parts of both points lie on the
-// 2^-20 grid (|x| < 1), so their differences are exact
-__device__ __forceinline__ df t_grid(const Pt& p, const Pt& q, df inv_rho) {
+// t = ||p - q|| for coordinates already in units of rho (so t = distance / rho), in
+// double-float; the high parts of both points lie on a common power-of-two grid
+// chosen so that their differences are exact
+__device__ __forceinline__ df t_grid(const Pt& p, const Pt& q) {
     const df dx = dfm::fast_two_sum(p.xh - q.xh, p.xl - q.xl);
     const df dy = dfm::fast_two_sum(p.yh - q.yh, p.yl - q.yl);
     const df sx = dfm::two_prod(dx.h, dx.h), sy = dfm::two_prod(dy.h, dy.h);
     df d2 = dfm::two_sum(sx.h, sy.h);
     d2.l += sx.l + sy.l + 2.0f * (dx.h * dx.l + dy.h * dy.l);
     d2 = dfm::fast_two_sum(d2.h, d2.l);
-    return dfm::mul(dfm::sqrt_df(d2), inv_rho);
+    return dfm::sqrt_df(d2);
 }
 
 // same for arbitrary double-float points (prediction locations)
-__device__ __forceinline__ df t_any(const Pt& p, const Pt& q, df inv_rho) {
+__device__ __forceinline__ df t_any(const Pt& p, const Pt& q) {
     df dx = dfm::two_sum(p.xh, -q.xh);
     dx = dfm::fast_two_sum(dx.h, dx.l + (p.xl - q.xl));
     df dy = dfm::two_sum(p.yh, -q.yh);
@@ -610,7 +612,7 @@ __device__ __forceinline__ df t_any(const Pt& p, const Pt& q, df inv_rho) {
     df d2 = dfm::two_sum(sx.h, sy.h);
     d2.l += sx.l + sy.l + 2.0f * (dx.h * dx.l + dy.h * dy.l);
     d2 = dfm::fast_two_sum(d2.h, d2.l);
-    return dfm::mul(dfm::sqrt_df(d2), inv_rho);
+    return dfm::sqrt_df(d2);
 }
 
 __device__ __forceinline__ df exp_neg_sm(const float* tbl, df t) {
@@ -619,7 +621,7 @@ __device__ __forceinline__ df exp_neg_sm(const float* tbl, df t) {
 
 // r = y - A x with A = Sigma + lambda I: double-float entries, one pass over the
 // lower triangle in 64 x 64 tiles, each entry feeding its row and its column.
-__device__ void residual_df(SmemM& sm, const float* tbl, const SlotM& S, int k, df inv_rho, double lam) {
+__device__ void residual_df(SmemM& sm, const float* tbl, const SlotM& S, int k, double lam) {
     const int tid = threadIdx.x;
     const int rg = tid >> 4, cg = tid & 15;   // 16 x 16 threads, 4 x 4 entries each
     for (int a = tid; a < k; a += NT) { S.ah[a] = 0.0f; S.al[a] = 0.0f; }
@@ -653,7 +655,7 @@ __device__ void residual_df(SmemM& sm, const float* tbl, const SlotM& S, int k, 
                 for (int v = 0; v < 4; ++v) {
                     const int a = I * NB + rg * 4 + u, b = J * NB + cg * 4 + v;
                     if (a < k && b < k && (I != J || a > b)) {
-                        const df e = exp_neg_sm(tbl, t_grid(pa[u], pb[v], inv_rho));
+                        const df e = exp_neg_sm(tbl, t_grid(pa[u], pb[v]));
                         racc[u].add_prod(e, xb[v]);
                         cacc[v].add_prod(e, xa[u]);
                     }
@@ -728,20 +730,29 @@ __device__ void run_task(SmemM& sm, SmemKeep& keep, SmemSimt* simt, TcCtx* tc, c
     const int k = (int)(a.T_off[i + 1] - t0);
     const int64_t ld = a.ld;
     const SlotM S = slot_of(a);
-    const double sc = a.coord_scale;
-    const double inv_rho_s = 1.0 / (rho * sc);      // distances are measured in scaled units
-    const df inv_rho = dfm::from_double(inv_rho_s);
-    const float inv_rho32 = (float)inv_rho_s;
-    const double ox = k > 0 ? a.X[a.T_idx[t0]] : 0.0, oy = k > 0 ? a.Y[a.T_idx[t0]] : 0.0;
-
     PhaseTimer tm(a.phase_cycles);
     const long long t_task = a.phase_cycles ? now_cycles() : 0;
-    // gather: scaled offsets, high parts on the 2^-20 grid
+    // coordinates become offsets from the subset's first training point in units of
+    // rho (so covariance arguments are plain distances); their high parts lie on a
+    // power-of-two grid fine enough that differences of high parts are exact floats
+    const double sc = 1.0 / rho;
+    const double ox = k > 0 ? a.X[a.T_idx[t0]] : 0.0, oy = k > 0 ? a.Y[a.T_idx[t0]] : 0.0;
+    float omax = 0.0f;
+    for (int q = tid; q < k; q += NT) {
+        const int g = a.T_idx[t0 + q];
+        omax = fmaxf(omax, (float)fmax(fabs(a.X[g] - ox), fabs(a.Y[g] - oy)));
+    }
+    omax = block_max(sm, omax) * (float)sc * 1.0001f;
+    // |offset| < 2^eb, grid 2^-(21 - eb): high parts and their differences need <= 23 bits
+    const int eb = max(0, ilogbf(fmaxf(omax, 1.0f)) + 1);
+    const double qscale = exp2((double)(21 - eb));
+
+    // gather
 #pragma unroll 4
     for (int q = tid; q < k; q += NT) {
         const int g = a.T_idx[t0 + q];
         const double dx = (a.X[g] - ox) * sc, dy = (a.Y[g] - oy) * sc;
-        const double hx = rint(dx * QSCALE) / QSCALE, hy = rint(dy * QSCALE) / QSCALE;
+        const double hx = rint(dx * qscale) / qscale, hy = rint(dy * qscale) / qscale;
         S.xh[q] = (float)hx;
         S.xl[q] = (float)(dx - hx);
         S.yh[q] = (float)hy;
@@ -785,7 +796,7 @@ __device__ void run_task(SmemM& sm, SmemKeep& keep, SmemSimt* simt, TcCtx* tc, c
                 if (r != c) {
                     const float dx = (rxh - cxh[c]) + (rxl - cxl[c]);
                     const float dy = (ryh - cyh[c]) + (ryl - cyl[c]);
-                    v = expf(-sqrtf(fmaf(dx, dx, dy * dy)) * inv_rho32);
+                    v = expf(-sqrtf(fmaf(dx, dx, dy * dy)));
                 }
                 S.L[r + (int64_t)c * ld] = v;
             }
@@ -870,7 +881,7 @@ __device__ void run_task(SmemM& sm, SmemKeep& keep, SmemSimt* simt, TcCtx* tc, c
                 R.ql[q] = v.l;
             }
             __syncthreads();
-            residual_df(sm, keep.tbl, R, k, inv_rho, lam);
+            residual_df(sm, keep.tbl, R, k, lam);
             tm.lap(kPhResidual);
             if (a.phase_cycles && tid == 0) atomicAdd(a.phase_cycles + kPhResidualPasses, 1ull);
         }
@@ -903,8 +914,8 @@ __device__ void run_task(SmemM& sm, SmemKeep& keep, SmemSimt* simt, TcCtx* tc, c
         for (int q = lane; q < k; q += 32) {
             const Pt Q{R.xh[q], R.xl[q], R.yh[q], R.yl[q]};
             const df xq{R.qh[q], R.ql[q]};
-            s0.add_prod(exp_neg_sm(keep.tbl, t_any(P0, Q, inv_rho)), xq);
-            s1.add_prod(exp_neg_sm(keep.tbl, t_any(P1, Q, inv_rho)), xq);
+            s0.add_prod(exp_neg_sm(keep.tbl, t_any(P0, Q)), xq);
+            s1.add_prod(exp_neg_sm(keep.tbl, t_any(P1, Q)), xq);
         }
         const double v0 = warp_sum_d((double)s0.h + (double)s0.l);
         const double v1 = warp_sum_d((double)s1.h + (double)s1.l);

@@ -10,11 +10,11 @@
 // hi*hi + hi*mid + mid*hi + hi*lo + lo*hi + mid*mid reproduce FP32-accurate
 // products while running on the BF16 tensor pipe.
 //
-// Roles (256 threads):  warp 0 lane 0 issues TMA loads into a 3-stage ring,
-// warp 1 lane 0 issues the MMAs, warps 4..7 (one per TMEM lane quadrant) drain the
-// accumulators through the caller's epilogue.  Two 128-row tiles form one pass;
-// the accumulators of consecutive passes alternate between two TMEM buffers so the
-// epilogue of one pass overlaps the MMAs of the next.
+// Roles (256 threads):  warp 0 lane 0 issues TMA loads into a ring of Pipe::nstages
+// stages, warp 1 lane 0 issues the MMAs, warps 4..7 (one per TMEM lane quadrant)
+// drain the accumulators through the caller's epilogue.  TPP 128-row tiles (template
+// parameter) form one pass; the accumulators of consecutive passes alternate between
+// two TMEM buffers so the epilogue of one pass overlaps the MMAs of the next.
 #pragma once
 
 #include <cuda.h>

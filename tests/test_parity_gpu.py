@@ -177,3 +177,26 @@ def test_mixed_engines(gpu_lib, engine):
     assert np.all(out["status"] == 0), out["status"]
     worst = compare(out, ref, V_off, range(16), len(P), "mixed")
     print("mixed", engine, worst)
+
+
+@pytest.mark.parametrize("rho,tau2", [(0.02, 0.001), (0.02, 0.1), (0.2, 0.001), (0.2, 0.01), (0.2, 0.1)])
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_grid_precision_stress(gpu_lib, prec, rho, tau2):
+    """Gridded 1024^2 training set (fine 2048^2 grid, 131 072 validation nodes), 32-cell
+    cores with 8-cell shells (k = 1600 / 1920 / 2304): the conditioning sweep of the
+    precision-stress workload (rho in {0.02, 0.2}, tau2 in {0.001, 0.01, 0.1}, the
+    largest condition numbers near 1e6).  The field's own parameters are evaluated;
+    sampled subsets (corner, edge, interior) are compared with the oracle."""
+    w = datagen.config_grid_1m(rho=rho, tau2=tau2)
+    P = w.params
+    nx = w.layout["nx"]
+    pick = [0, nx // 2, nx * (nx // 2) + nx // 2]
+    with gpu_lib.Context(w.xy, w.v, w.role, w.layout) as ctx:
+        out = ctx.cv_loss(P, precision=prec, per_subset=True, predictions=True)
+        V_off = ctx.V_off.copy()
+    assert out["status"][0] in (0, 7), out["status"]       # 7: some tasks recomputed in FP64
+    cores = oracle.layout_cores(w.layout)
+    members = {i: oracle.subset_members(w.xy, w.role, w.layout, i, cores) for i in pick}
+    ref = oracle.cv_loss(w.xy, w.v, w.role, w.layout, P, members=members, subsets=pick)
+    worst = compare(out, ref, V_off, pick, 1, prec, check_total=False)
+    print("grid stress", prec, rho, tau2, out["status"].tolist(), worst)
