@@ -8,14 +8,18 @@ split, 40 x 40 cores, shell 0.001, about 1600 subsets of 2250-2630 training
 points), seeded and synthetic.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64]
-                    [--workload paper5m|cluster262k|uniform4096] [--batch B]
-                    [--impl ours|reference]
+                    [--workload paper5m|cluster262k|uniform4096|serving] [--batch B]
+                    [--impl ours|reference] [--serve-seconds S] [--hbm-budget-gb G]
 
 Prints one JSON line (rank 0).  `value` is device-timed (CUDA events around each
 step on the launching stream, L2 flushed between steps); `e2e` is the same metric
 through the host-pointer C-ABI call (parameter upload and result download inside
 the timed region); `roofline` uses the task kernel's own event-timed duration;
 `cpu_baseline` times the FP64 oracle on a bounded sample of the same workload.
+`serving` (rank 0, one GPU) runs the request loop over eight gridded datasets
+(65,536 to 1,048,576 training points): Nelder-Mead clients submit CV evaluations
+and prediction requests; capacity from a burst of the request mix first, then Poisson arrivals at
+50/80/100% of it, with p50/p99 latency per load level.
 """
 from __future__ import annotations
 
@@ -187,6 +191,206 @@ def cpu_baseline(w, params, budget_s: float, active, seed: int = 0):
                 t_full=t_full)
 
 
+def nelder_mead(x0, step: float):
+    """Ask/tell Nelder-Mead (a generator: yields a point, receives its loss) with the
+    usual coefficients (reflection 1, expansion 2, contraction 1/2, shrink 1/2)."""
+    n = len(x0)
+    simplex = [np.asarray(x0, dtype=np.float64)] + [np.asarray(x0, dtype=np.float64) + step * e
+                                                    for e in np.eye(n)]
+    f = []
+    for x in simplex:
+        f.append((yield x))
+    while True:
+        order = np.argsort(f)
+        simplex = [simplex[i] for i in order]
+        f = [f[i] for i in order]
+        c = np.mean(simplex[:-1], axis=0)
+        xr = c + (c - simplex[-1])
+        fr = yield xr
+        if f[0] <= fr < f[-2]:
+            simplex[-1], f[-1] = xr, fr
+            continue
+        if fr < f[0]:
+            xe = c + 2.0 * (c - simplex[-1])
+            fe = yield xe
+            simplex[-1], f[-1] = (xe, fe) if fe < fr else (xr, fr)
+            continue
+        xc = c + 0.5 * (xr - c) if fr < f[-1] else c + 0.5 * (simplex[-1] - c)
+        fc = yield xc
+        if fc < min(fr, f[-1]):
+            simplex[-1], f[-1] = xc, fc
+            continue
+        for i in range(1, n + 1):
+            simplex[i] = simplex[0] + 0.5 * (simplex[i] - simplex[0])
+            f[i] = yield simplex[i]
+
+
+# projection of Nelder-Mead proposals, log(sigma2, rho, tau2)
+LOG_LO = np.log([0.05, 0.005, 1e-3])
+LOG_HI = np.log([20.0, 0.5, 1.0])
+
+
+class ServingClient:
+    """Serving workload over several datasets.  Each request goes to a dataset drawn
+    uniformly at random; 80% are CV evaluations, 20% predictions of 10^3-10^5 uniform
+    new locations at the dataset's best parameters so far.  A CV request evaluates the
+    next point of an idle Nelder-Mead run (over log(sigma2, rho, tau2)) on that
+    dataset; if all of the dataset's runs are waiting for a result it evaluates a probe
+    near the best point found (log-normal perturbation, sd 0.1).  Requests go through
+    pcv_server_*; each finished request reports its submit-to-completion latency."""
+
+    def __init__(self, pcv, srv, workloads, n_runs: int, seed: int):
+        from concurrent.futures import ThreadPoolExecutor
+        self.srv = srv
+        self.rng = np.random.default_rng(seed)
+        self.ws = workloads
+        self.lock = threading.Lock()
+        self.cond = threading.Condition(self.lock)
+        self.pool = ThreadPoolExecutor(64)
+        self.runs = []
+        for r in range(n_runs):
+            d = r % len(workloads)
+            s2, rho, tau2 = workloads[d].params[0]
+            x0 = np.log([1.0, rho, tau2]) + self.rng.uniform(-1.0, 1.0, 3) * np.array([0.5, 1.0, 1.0])
+            g = nelder_mead(np.clip(x0, LOG_LO, LOG_HI), 0.3)
+            self.runs.append(dict(gen=g, dataset=d, x=next(g), busy=False))
+        self.best = [(np.inf, np.log(w.params[0])) for w in workloads]
+        self.records = []          # (phase, kind, latency_ms, status)
+        self.outstanding = 0
+        self.counts = dict(nm=0, probe=0, predict=0)
+        self.phase = None
+
+    @staticmethod
+    def _params(x):
+        return np.exp(np.clip(x, LOG_LO, LOG_HI))
+
+    def _submit_one(self):
+        """One request of the mix (called with the lock held)."""
+        d = int(self.rng.integers(len(self.ws)))
+        if self.rng.random() < 0.8:
+            idle = [r for r, run in enumerate(self.runs) if run["dataset"] == d and not run["busy"]]
+            if idle:
+                r = idle[0]
+                self.runs[r]["busy"] = True
+                x = self.runs[r]["x"]
+                self.counts["nm"] += 1
+            else:
+                r = -1
+                x = self.best[d][1] + self.rng.normal(0.0, 0.1, 3)
+                self.counts["probe"] += 1
+            rid = self.srv.submit_cv(d, self._params(x))
+            self.outstanding += 1
+            self.pool.submit(self._wait_cv, r, d, x, rid, self.phase)
+        else:
+            m = int(round(np.exp(self.rng.uniform(np.log(1e3), np.log(1e5)))))
+            rid = self.srv.submit_predict(d, self._params(self.best[d][1]), self.rng.random((m, 2)))
+            self.outstanding += 1
+            self.counts["predict"] += 1
+            self.pool.submit(self._wait_pred, rid, self.phase)
+
+    def _wait_cv(self, r, d, x, rid, phase):
+        res = self.srv.wait(rid, timeout_s=600.0)
+        with self.lock:
+            loss = res["sspe"] if (res["status"] in (0, 7) and np.isfinite(res["sspe"])) else np.inf
+            if loss < self.best[d][0]:
+                self.best[d] = (loss, np.array(x, dtype=np.float64))
+            if r >= 0:
+                run = self.runs[r]
+                run["x"] = run["gen"].send(loss)
+                run["busy"] = False
+            self.records.append((phase, "cv", res["latency_ms"], res["status"]))
+            self.outstanding -= 1
+            self.cond.notify_all()
+
+    def _wait_pred(self, rid, phase):
+        res = self.srv.wait(rid, timeout_s=600.0)
+        with self.lock:
+            self.records.append((phase, "predict", res["latency_ms"], res["status"]))
+            self.outstanding -= 1
+            self.cond.notify_all()
+
+    def drain(self):
+        with self.lock:
+            self.cond.wait_for(lambda: self.outstanding == 0, timeout=900.0)
+
+    def burst(self, n: int) -> float:
+        """n requests of the mix submitted at once; returns requests/s to complete them
+        (the capacity the open-loop loads are scaled to)."""
+        t0 = time.perf_counter()
+        with self.lock:
+            self.phase = "burst"
+            for _ in range(n):
+                self._submit_one()
+        self.drain()
+        return n / (time.perf_counter() - t0)
+
+    def open(self, rate: float, seconds: float, label: str) -> dict:
+        """Poisson arrivals of the mix at `rate` requests/s for `seconds`, then drain."""
+        with self.lock:
+            self.phase = label
+            before = dict(self.counts)
+        t0 = time.perf_counter()
+        t_next = t0 + self.rng.exponential(1.0 / rate)
+        while t_next < t0 + seconds:
+            dt = t_next - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            with self.lock:
+                self._submit_one()
+            t_next += self.rng.exponential(1.0 / rate)
+        self.drain()
+        elapsed = time.perf_counter() - t0
+        n = {k: self.counts[k] - before[k] for k in self.counts}
+        rec = [r for r in self.records if r[0] == label]
+        lat = [r[2] for r in rec]
+        lat_cv = [r[2] for r in rec if r[1] == "cv"]
+        lat_pr = [r[2] for r in rec if r[1] == "predict"]
+
+        def pct(v, q):
+            return float(np.percentile(v, q)) if v else None
+        return dict(rate_req_s=rate, seconds=seconds, cv_nelder_mead=n["nm"], cv_probe=n["probe"],
+                    predict=n["predict"], failed=sum(1 for r in rec if r[3] not in (0, 7)),
+                    cv_evals_per_s=(n["nm"] + n["probe"]) / elapsed, drain_s=elapsed - seconds,
+                    p50_ms=pct(lat, 50), p99_ms=pct(lat, 99), cv_p50_ms=pct(lat_cv, 50),
+                    cv_p99_ms=pct(lat_cv, 99), predict_p50_ms=pct(lat_pr, 50), predict_p99_ms=pct(lat_pr, 99))
+
+
+def run_serving(pcv, device: int, seconds: float, hbm_budget_gb: float, max_batch: int, n_runs: int = 32,
+                seed: int = 0, max_slots: int = 152) -> dict:
+    """Serving measurement on the eight gridded datasets: capacity from a burst of the
+    request mix, then Poisson arrivals at 50/80/100% of it."""
+    t0 = time.perf_counter()
+    ws = datagen.config_serving()
+    t_gen = time.perf_counter() - t0
+    # at most half of the GPU's task slots per dataset, so that two datasets' launches
+    # run side by side
+    ctxs = [pcv.Context(w.xy, w.v, w.role, w.layout, device=device, max_slots=max_slots) for w in ws]
+    # first call per dataset: work memory, tensor maps, one-time set-up
+    for c, w in zip(ctxs, ws):
+        c.cv_loss(w.params[:1])
+    t_setup = time.perf_counter() - t0
+    out = dict(workload="serving-8-grids-256..1024sq-32x32cores-8buf",
+               datasets=[dict(name=w.name, n_obs=int(len(w.v)), subsets=int(c.N)) for w, c in zip(ws, ctxs)],
+               nelder_mead_runs=n_runs, max_batch=max_batch, hbm_budget_gb=hbm_budget_gb or None,
+               slots_per_dataset=max_slots,
+               setup_s=round(t_setup, 2), datagen_s=round(t_gen, 2))
+    with pcv.Server(ctxs, max_batch=max_batch, precision="mixed",
+                    hbm_budget_bytes=hbm_budget_gb * 1e9) as srv:
+        cl = ServingClient(pcv, srv, ws, n_runs, seed)
+        cap = cl.burst(20 * len(ws))
+        out["capacity_req_s"] = cap
+        out["loads"] = []
+        for frac in (0.5, 0.8, 1.0):
+            out["loads"].append(dict(load=frac, **cl.open(frac * cap, seconds, f"load{frac}")))
+        st = srv.stats()
+        out["server"] = dict(p50_ms=st["p50_ms"], p99_ms=st["p99_ms"], completed=st["completed"],
+                             batches=st["batches"], evictions=st["evictions"])
+        cl.pool.shutdown()
+    for c in ctxs:
+        c.close()
+    return out
+
+
 def run_reference(args, rank: int, world: int):
     """The oracle as it stands on the host cores, a bounded sample per step."""
     if rank != 0:
@@ -231,6 +435,11 @@ def main():
     ap.add_argument("--engine", default="tensor", choices=["tensor", "simt"])
     ap.add_argument("--tc-stages", type=int, default=0, help="TMA ring depth of the tensor engine (2 or 3)")
     ap.add_argument("--refine-tol", type=float, default=0.0, help="refinement tolerance (0: library default)")
+    ap.add_argument("--serve-seconds", type=float, default=10.0,
+                    help="seconds per serving load level (0: no serving measurement)")
+    ap.add_argument("--serve-batch", type=int, default=16, help="CV requests per serving batch")
+    ap.add_argument("--hbm-budget-gb", type=float, default=0.0, help="serving work-memory budget (0: unlimited)")
+    ap.add_argument("--serve-slots", type=int, default=152, help="task slots per serving dataset")
     args = ap.parse_args()
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
@@ -254,6 +463,18 @@ def main():
     def barrier():
         if dist is not None:
             dist.barrier()
+
+    if args.workload == "serving":
+        if rank == 0:
+            sv = run_serving(pcv, local, args.serve_seconds or 10.0, args.hbm_budget_gb, args.serve_batch,
+                             max_slots=args.serve_slots)
+            full = sv["loads"][-1]
+            print(json.dumps(dict(metric=METRIC, value=full["cv_evals_per_s"], unit=UNIT, n_gpus=1, steps=0,
+                                  warmup=0, higher_is_better=True, scaling="weak", vs_baseline=None,
+                                  dtype="bf16x6+f32+df32x2", data="synthetic",
+                                  config=dict(workload=sv["workload"], precision="mixed"),
+                                  serving=sv)), flush=True)
+        return
 
     t_setup = time.perf_counter()
     w = make_workload(args.workload)
@@ -377,9 +598,12 @@ def main():
                                     sample=f"{cb['n_done']} of {cb['n_total']} subsets with validation data, one "
                                            f"configuration ({cb['elapsed']:.1f} s), extrapolated by subset count "
                                            f"to {cb['t_full']:.0f} s per configuration")
+    ctx.close()
+    if rank == 0 and world == 1 and args.serve_seconds > 0:
+        line["serving"] = run_serving(pcv, local, args.serve_seconds, args.hbm_budget_gb, args.serve_batch,
+                                      max_slots=args.serve_slots)
     if rank == 0:
         print(json.dumps(line), flush=True)
-    ctx.close()
     if dist is not None:
         dist.destroy_process_group()
 

@@ -197,6 +197,56 @@ pcv_status pcv_phase_cycles(pcv_ctx* ctx, uint64_t* out, int32_t reset);
 /* Destroy a context and free its device memory (synchronises the device). */
 void pcv_destroy(pcv_ctx* ctx);
 
+/* ------------------------------------------------------------------ serving
+ *
+ * A request loop over several device-resident datasets (contexts) for outer
+ * optimisers that submit CV-loss evaluations one configuration at a time (the
+ * paper evaluates its grid of configurations sequentially, Sec. 4.4) and for
+ * prediction requests.  Continuous batching: each dataset has a worker thread and
+ * stream; a worker takes all CV requests queued for its dataset (up to max_batch)
+ * as one pcv_cv_loss batch, so requests arriving meanwhile join the next batch;
+ * workers of different datasets run concurrently and their kernels overlap on the
+ * device.  Admission by device memory: a batch starts only when its dataset's
+ * work memory fits hbm_budget_bytes; idle datasets' work memory is released
+ * (least recently used first) to make room.  Streams get priorities by work per
+ * configuration (sum of k^3 over subsets), the smallest dataset highest, so that
+ * waiting launches of short jobs are scheduled first.  Results do not depend on
+ * batching (every subset task is computed on its own; the sums have a fixed order).
+ *
+ * The server takes the contexts over: while it exists, no other thread may use
+ * them.  Contexts should be created with max_slots set so that their work memory
+ * is predictable.  Thread-safe: any thread may submit and wait. */
+typedef struct pcv_server pcv_server;
+
+typedef struct {
+    int32_t struct_size;      /* sizeof(pcv_server_options) */
+    int32_t max_batch;        /* CV requests per batch (default 16) */
+    int32_t precision;        /* PCV_PREC_MIXED (default) or PCV_PREC_FP64 */
+    double hbm_budget_bytes;  /* work-memory budget over all datasets; 0 = unlimited */
+} pcv_server_options;
+
+pcv_status pcv_server_create(pcv_ctx* const* ctxs, int32_t n_ctx, const pcv_server_options* opts,
+                             pcv_server** out);
+/* Queue a CV-loss evaluation of one configuration (sigma2, rho, tau2) on dataset
+ * `dataset` (index into ctxs); *request_id identifies it. */
+pcv_status pcv_server_submit_cv(pcv_server* s, int32_t dataset, const double* params3, int64_t* request_id);
+/* Queue a prediction at m locations (m x 2, copied). */
+pcv_status pcv_server_submit_predict(pcv_server* s, int32_t dataset, const double* params3,
+                                     const double* xy_new, int64_t m, int64_t* request_id);
+/* Wait up to timeout_s (<= 0: no limit) for a request and take its results: the
+ * CV loss and per-configuration status (CV), or m predictions into yhat (caller's
+ * array, may be NULL), and the latency from submission to completion in ms.  The
+ * request is forgotten afterwards.  PCV_ERR_TIMEOUT if not done in time. */
+pcv_status pcv_server_wait(pcv_server* s, int64_t request_id, double timeout_s, double* sspe,
+                           int32_t* status, double* yhat, double* latency_ms);
+/* Latency percentiles over all completed requests, CV evaluations per second from
+ * the first submission to the last completion, counts of completed requests, batches and evictions. */
+pcv_status pcv_server_stats(pcv_server* s, double* p50_ms, double* p99_ms, double* cv_evals_per_s,
+                            int64_t* completed, int64_t* batches, int64_t* evictions);
+/* Stop the workers (requests still queued are dropped) and free the server; the
+ * contexts remain the caller's. */
+void pcv_server_destroy(pcv_server* s);
+
 /* ------------------------------------------------- allocation-free variant
  *
  * The paper has no counterpart to this entry point; it exists for callers that

@@ -140,24 +140,33 @@ int32_t round_up(int64_t v, int64_t m) { return (int32_t)(((std::max<int64_t>(v,
 constexpr int kFallbackWs = 2;          // index of the fallback workspace
 constexpr int kFallbackSlots = 32;      // tasks needing the FP64 fallback are rare
 
-pcv_status ensure_workspace(pcv_ctx* c, int prec) {
-    Workspace& w = c->ws[prec];
-    if (w.grid > 0) return PCV_OK;
-    const bool fallback = prec == kFallbackWs;
-    if (fallback) prec = PCV_PREC_FP64;
-    const int32_t ld = round_up(c->kmax, 128);
+// Slot count (before the free-memory clamp) and bytes per slot of workspace `wi`
+// (PCV_PREC_FP64, PCV_PREC_MIXED or kFallbackWs).
+void workspace_shape(const pcv_ctx* c, int wi, int64_t& g, int64_t& sb, int64_t& pb, int32_t& ld) {
+    const bool fallback = wi == kFallbackWs;
+    const int prec = fallback ? PCV_PREC_FP64 : wi;
+    ld = round_up(c->kmax, 128);
     const bool tensor = prec == PCV_PREC_MIXED && c->opts.factor_engine == pcv::kMixedEngineTensor;
-    const int64_t sb = prec == PCV_PREC_FP64 ? pcv::slot_bytes_fp64(ld, c->mmax) : pcv::slot_bytes_mixed(ld, c->mmax);
-    const int64_t pb = tensor ? 3 * (int64_t)ld * ld * 2 : 0;   // planes per slot
-    size_t free_b = 0, total_b = 0;
-    CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
-    const double budget = c->opts.workspace_fraction * (double)free_b;
+    sb = prec == PCV_PREC_FP64 ? pcv::slot_bytes_fp64(ld, c->mmax) : pcv::slot_bytes_mixed(ld, c->mmax);
+    pb = tensor ? 3 * (int64_t)ld * ld * 2 : 0;   // planes per slot
     // CTAs per SM: two for both mixed engines (the tensor engine holds half of an
     // SM's tensor memory per CTA), one for the FP64 kernel
     const int per_sm = prec == PCV_PREC_MIXED ? 2 : 1;
-    int64_t g = c->opts.max_slots > 0 ? c->opts.max_slots : (int64_t)c->sms * per_sm;
+    g = c->opts.max_slots > 0 ? c->opts.max_slots : (int64_t)c->sms * per_sm;
     if (tensor) g = std::min<int64_t>(g, 2 * (int64_t)c->sms);
     if (fallback) g = std::min<int64_t>(g, kFallbackSlots);
+}
+
+pcv_status ensure_workspace(pcv_ctx* c, int wi) {
+    Workspace& w = c->ws[wi];
+    if (w.grid > 0) return PCV_OK;
+    int64_t g, sb, pb;
+    int32_t ld;
+    workspace_shape(c, wi, g, sb, pb, ld);
+    const bool tensor = pb > 0;
+    size_t free_b = 0, total_b = 0;
+    CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+    const double budget = c->opts.workspace_fraction * (double)free_b;
     g = std::min<int64_t>(g, (int64_t)(budget / (double)(sb + pb)));
     if (g < 1) return fail(PCV_ERR_OOM, "workspace for one task does not fit in device memory");
     cudaError_t e = w.mem.reserve((size_t)(g * sb));
@@ -178,6 +187,54 @@ pcv_status ensure_workspace(pcv_ctx* c, int prec) {
 bool bad_precision(int32_t p) { return p != PCV_PREC_FP64 && p != PCV_PREC_MIXED; }
 
 }  // namespace
+
+// ----------------------------------------------------------------- helpers for the server
+
+namespace pcv {
+
+int64_t ctx_workspace_estimate(pcv_ctx* c, int32_t prec) {
+    int64_t total = 0;
+    const int list[2] = {prec, prec == PCV_PREC_MIXED ? kFallbackWs : -1};
+    for (int wi : list) {
+        if (wi < 0 || c->ws[wi].grid > 0) continue;
+        int64_t g, sb, pb;
+        int32_t ld;
+        workspace_shape(c, wi, g, sb, pb, ld);
+        total += g * (sb + pb);
+    }
+    return total;
+}
+
+int64_t ctx_workspace_resident(pcv_ctx* c) {
+    int64_t t = 0;
+    for (const auto& w : c->ws) t += (int64_t)(w.mem.n * sizeof(unsigned char) + w.planes.n);
+    return t;
+}
+
+void ctx_release_workspace(pcv_ctx* c) {
+    cudaSetDevice(c->device);
+    for (auto& w : c->ws) {
+        w.mem.release();
+        w.planes.release();
+        w.grid = 0;
+        w.plane_elems = 0;
+    }
+}
+
+int ctx_device(const pcv_ctx* c) { return c->device; }
+
+double ctx_work_estimate(const pcv_ctx* c) {
+    const Plan& P = c->plan;
+    double w = 0.0;
+    for (int32_t i = 0; i < P.N; ++i) {
+        if (P.V_off[i + 1] == P.V_off[i]) continue;
+        const double k = (double)(P.T_off[i + 1] - P.T_off[i]);
+        w += k * k * k;
+    }
+    return w;
+}
+
+}  // namespace pcv
 
 // ----------------------------------------------------------------- plans
 

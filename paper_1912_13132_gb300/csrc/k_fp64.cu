@@ -16,6 +16,8 @@
 
 #include <cmath>
 
+#include <mutex>
+
 #include "pcv_internal.h"
 
 namespace pcv {
@@ -291,12 +293,21 @@ int64_t slot_bytes_fp64(int32_t ld, int64_t mmax) {
 }
 
 int launch_task_fp64(const TaskArgs& a, int grid, void* stream) {
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_cv_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)sizeof(Smem64));
-        if (e != cudaSuccess) return (int)e;
-        attr_set = true;
+    // the shared-memory opt-in is a per-device function attribute; contexts on
+    // several devices and the serving workers may get here concurrently
+    static std::mutex mu;
+    static bool attr_set[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return (int)e;
+    if (dev < 0 || dev >= 64) return (int)cudaErrorInvalidDevice;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (!attr_set[dev]) {
+            e = cudaFuncSetAttribute(k_cv_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem64));
+            if (e != cudaSuccess) return (int)e;
+            attr_set[dev] = true;
+        }
     }
     k_cv_fp64<<<grid, NT, sizeof(Smem64), (cudaStream_t)stream>>>(a);
     count_launch();

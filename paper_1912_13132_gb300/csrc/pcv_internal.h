@@ -95,4 +95,11 @@ int launch_combine(const double* z, const int32_t* tstatus, const double* params
 
 void count_launch(int n = 1);
 
+// Workspace bookkeeping used by the serving loop (server.cpp).
+int64_t ctx_workspace_estimate(pcv_ctx* c, int32_t prec);   // bytes still to allocate for `prec`
+int64_t ctx_workspace_resident(pcv_ctx* c);                  // bytes held now
+void ctx_release_workspace(pcv_ctx* c);                      // free all (context must be idle)
+int ctx_device(const pcv_ctx* c);
+double ctx_work_estimate(const pcv_ctx* c);                  // sum of k^3 over subsets with validation data
+
 }  // namespace pcv

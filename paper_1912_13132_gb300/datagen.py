@@ -239,3 +239,24 @@ def config_paper_5m(side=2236, nx=40, delta=0.001, seed=BASE_SEED + 5, missing=0
     return Workload(f"paper-5m-{side}sq-{nx}x{nx}", xy, v, role,
                     dict(kind="grid", nx=nx, ny=nx, delta=delta, domain=(0.0, 1.0, 0.0, 1.0)),
                     params, dict(seed=seed, side=side))
+
+
+SERVING_SIDES = (256, 320, 384, 512, 640, 768, 896, 1024)
+
+
+def config_serving(sides=SERVING_SIDES, seed=BASE_SEED + 4) -> list:
+    """Serving workload: one gridded dataset per side (65,536 to 1,048,576 TRAIN), each
+    built like the precision-stress set (fine grid of twice the side, TRAIN on the even
+    sub-grid, VALID = TRAIN/8 other fine nodes, 32-cell cores with 8-cell shells), with
+    its own rho log-uniform in [0.02, 0.2] and tau2 log-uniform in [0.01, 0.1].
+    """
+    rng = np.random.default_rng(seed)
+    out = []
+    for i, side in enumerate(sides):
+        rho = float(np.exp(rng.uniform(np.log(0.02), np.log(0.2))))
+        tau2 = float(np.exp(rng.uniform(np.log(0.01), np.log(0.1))))
+        w = config_grid_1m(rho=rho, tau2=tau2, seed=seed + 17 * (i + 1), fine=2 * side, cells=32, buf=8,
+                           n_valid=side * side // 8)
+        w.name = f"serve-grid-{side}sq-rho{rho:.3g}-tau{tau2:.3g}"
+        out.append(w)
+    return out

@@ -38,6 +38,11 @@ class pcv_options(ctypes.Structure):
                 ("refine_tol", ctypes.c_double), ("factor_engine", ctypes.c_int32), ("tc_stages", ctypes.c_int32)]
 
 
+class pcv_server_options(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_int32), ("max_batch", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("hbm_budget_bytes", ctypes.c_double)]
+
+
 class PcvError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{msg} (status {status})")
@@ -76,6 +81,13 @@ _SIGS = {
     "pcv_selftest_umma": (ctypes.c_int, [ctypes.POINTER(ctypes.c_float), ctypes.c_int32,
                                          ctypes.POINTER(ctypes.c_float), ctypes.c_int32,
                                          ctypes.POINTER(ctypes.c_float)]),
+    "pcv_server_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int32, ctypes.POINTER(pcv_server_options),
+                                         ctypes.POINTER(_vp)]),
+    "pcv_server_submit_cv": (ctypes.c_int, [_vp, ctypes.c_int32, _dp, _i64p]),
+    "pcv_server_submit_predict": (ctypes.c_int, [_vp, ctypes.c_int32, _dp, _dp, ctypes.c_int64, _i64p]),
+    "pcv_server_wait": (ctypes.c_int, [_vp, ctypes.c_int64, ctypes.c_double, _dp, _i32p, _dp, _dp]),
+    "pcv_server_stats": (ctypes.c_int, [_vp, _dp, _dp, _dp, _i64p, _i64p, _i64p]),
+    "pcv_server_destroy": (None, [_vp]),
     "pcv_destroy": (None, [_vp]),
     "pcv_status_str": (ctypes.c_char_p, [ctypes.c_int32]),
     "pcv_last_error": (ctypes.c_char_p, []),
@@ -271,6 +283,69 @@ class Context:
         _check(_lib.pcv_predict(self._h, _ptr(p, _dp), _ptr(q, _dp), len(q), PRECISIONS[precision],
                                 _ptr(out, _dp), _stream_ptr(stream)), "pcv_predict")
         return out
+
+
+class Server:
+    """Continuous-batching request loop over device-resident datasets (pcv_server_*)."""
+
+    def __init__(self, contexts, max_batch: int = 16, precision: str = "mixed", hbm_budget_bytes: float = 0.0):
+        self.contexts = list(contexts)
+        arr = (_vp * len(self.contexts))(*[c._h for c in self.contexts])
+        o = pcv_server_options(ctypes.sizeof(pcv_server_options), max_batch, PRECISIONS[precision],
+                               float(hbm_budget_bytes))
+        h = _vp()
+        _check(_lib.pcv_server_create(arr, len(self.contexts), ctypes.byref(o), ctypes.byref(h)), "pcv_server_create")
+        self._h = h
+        self._m = {}
+
+    def submit_cv(self, dataset: int, params3) -> int:
+        p = _f64(params3).reshape(3)
+        rid = ctypes.c_int64()
+        _check(_lib.pcv_server_submit_cv(self._h, dataset, _ptr(p, _dp), ctypes.byref(rid)), "pcv_server_submit_cv")
+        return rid.value
+
+    def submit_predict(self, dataset: int, params3, xy_new) -> int:
+        p = _f64(params3).reshape(3)
+        q = _f64(xy_new).reshape(-1, 2)
+        rid = ctypes.c_int64()
+        _check(_lib.pcv_server_submit_predict(self._h, dataset, _ptr(p, _dp), _ptr(q, _dp), len(q),
+                                              ctypes.byref(rid)), "pcv_server_submit_predict")
+        self._m[rid.value] = len(q)
+        return rid.value
+
+    def wait(self, rid: int, timeout_s: float = 0.0) -> dict:
+        m = self._m.pop(rid, 0)
+        y = np.empty(m) if m else None
+        sspe, st, lat = ctypes.c_double(), ctypes.c_int32(), ctypes.c_double()
+        _check(_lib.pcv_server_wait(self._h, rid, timeout_s, ctypes.byref(sspe), ctypes.byref(st),
+                                    _ptr(y, _dp) if y is not None else None, ctypes.byref(lat)), "pcv_server_wait")
+        out = dict(status=st.value, latency_ms=lat.value)
+        if y is not None:
+            out["yhat"] = y
+        else:
+            out["sspe"] = sspe.value
+        return out
+
+    def stats(self) -> dict:
+        p50, p99, eps = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        done, batches, ev = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(_lib.pcv_server_stats(self._h, ctypes.byref(p50), ctypes.byref(p99), ctypes.byref(eps),
+                                     ctypes.byref(done), ctypes.byref(batches), ctypes.byref(ev)), "pcv_server_stats")
+        return dict(p50_ms=p50.value, p99_ms=p99.value, cv_evals_per_s=eps.value, completed=done.value,
+                    batches=batches.value, evictions=ev.value)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.pcv_server_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 def pcv_create(xy, v, role, layout: dict, device: int = 0, **opts) -> Context:
