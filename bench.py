@@ -44,6 +44,8 @@ METRIC = "param-config CV evals/sec @5M obs: mixed vs FP64 at <=1e-6 rel err; p5
 UNIT = "evals/s"
 PEAKS_FALLBACK = dict(hbm_gbs=6800.0, bf16_tflops=1900.0, bf16_tflops_sustained=1700.0)
 FP64_NOMINAL_TFLOPS = 1.25      # GB300 FP64 (SIMT and tensor), nominal
+# tensor engines: (operand terms x products, products per FP32-accurate product)
+SCHEMES = {"tensor": ("f16x3", 3), "tensor-bf16": ("bf16x6", 6)}
 
 
 def load_peaks() -> tuple[dict, str]:
@@ -134,13 +136,16 @@ def kernel_code_hash(sources) -> str:
     return h.hexdigest()
 
 
-def recorded_traffic(tasks_per_launch: int):
-    """DRAM bytes of one task-kernel launch from the committed ncu record
-    (profiles/task_kernel_traffic.txt), or None when the kernel sources changed since
-    the counters were taken."""
+def recorded_traffic(tasks_per_launch: int, engine: str = "tensor"):
+    """DRAM bytes of one task-kernel launch from the committed ncu record of the engine
+    (profiles/task_kernel_traffic.txt, a JSON object per engine), or None when there is
+    none or the kernel sources changed since the counters were taken."""
     path = os.path.join(ROOT, "profiles", "task_kernel_traffic.txt")
     try:
         rec = json.load(open(path))
+        if engine not in rec:
+            return None, "no ncu record for this engine"
+        rec = rec[engine]
         if kernel_code_hash(rec["sources"]) != rec["source_sha256"]:
             return None, "kernel changed since the ncu capture"
         return rec["dram_bytes_per_task"] * tasks_per_launch, rec["note"]
@@ -356,7 +361,7 @@ class ServingClient:
 
 
 def run_serving(pcv, device: int, seconds: float, hbm_budget_gb: float, max_batch: int, n_runs: int = 32,
-                seed: int = 0, max_slots: int = 152) -> dict:
+                seed: int = 0, max_slots: int = 152, engine: str = "tensor") -> dict:
     """Serving measurement on the eight gridded datasets: capacity from a burst of the
     request mix, then Poisson arrivals at 50/80/100% of it."""
     t0 = time.perf_counter()
@@ -364,7 +369,8 @@ def run_serving(pcv, device: int, seconds: float, hbm_budget_gb: float, max_batc
     t_gen = time.perf_counter() - t0
     # at most half of the GPU's task slots per dataset, so that two datasets' launches
     # run side by side
-    ctxs = [pcv.Context(w.xy, w.v, w.role, w.layout, device=device, max_slots=max_slots) for w in ws]
+    ctxs = [pcv.Context(w.xy, w.v, w.role, w.layout, device=device, max_slots=max_slots, factor_engine=engine)
+            for w in ws]
     # first call per dataset: work memory, tensor maps, one-time set-up
     for c, w in zip(ctxs, ws):
         c.cv_loss(w.params[:1])
@@ -372,7 +378,7 @@ def run_serving(pcv, device: int, seconds: float, hbm_budget_gb: float, max_batc
     out = dict(workload="serving-8-grids-256..1024sq-32x32cores-8buf",
                datasets=[dict(name=w.name, n_obs=int(len(w.v)), subsets=int(c.N)) for w, c in zip(ws, ctxs)],
                nelder_mead_runs=n_runs, max_batch=max_batch, hbm_budget_gb=hbm_budget_gb or None,
-               slots_per_dataset=max_slots,
+               slots_per_dataset=max_slots, engine=engine,
                setup_s=round(t_setup, 2), datagen_s=round(t_gen, 2))
     with pcv.Server(ctxs, max_batch=max_batch, precision="mixed",
                     hbm_budget_bytes=hbm_budget_gb * 1e9) as srv:
@@ -432,7 +438,7 @@ def main():
     ap.add_argument("--ref-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--max-slots", type=int, default=0, help="limit concurrent tasks (profiling runs)")
-    ap.add_argument("--engine", default="tensor", choices=["tensor", "simt"])
+    ap.add_argument("--engine", default="tensor", choices=["tensor", "simt", "tensor-bf16"])
     ap.add_argument("--tc-stages", type=int, default=0, help="TMA ring depth of the tensor engine (2 or 3)")
     ap.add_argument("--refine-tol", type=float, default=0.0, help="refinement tolerance (0: library default)")
     ap.add_argument("--serve-seconds", type=float, default=10.0,
@@ -467,11 +473,13 @@ def main():
     if args.workload == "serving":
         if rank == 0:
             sv = run_serving(pcv, local, args.serve_seconds or 10.0, args.hbm_budget_gb, args.serve_batch,
-                             max_slots=args.serve_slots)
+                             max_slots=args.serve_slots, engine=args.engine)
             full = sv["loads"][-1]
             print(json.dumps(dict(metric=METRIC, value=full["cv_evals_per_s"], unit=UNIT, n_gpus=1, steps=0,
                                   warmup=0, higher_is_better=True, scaling="weak", vs_baseline=None,
-                                  dtype="bf16x6+f32+df32x2", data="synthetic",
+                                  dtype=(SCHEMES[args.engine][0] + "+f32+df32x2" if args.engine in SCHEMES
+                                         else "f32+df32x2"),
+                                  data="synthetic",
                                   config=dict(workload=sv["workload"], precision="mixed"),
                                   serving=sv)), flush=True)
         return
@@ -554,18 +562,20 @@ def main():
     if args.precision == "fp64":
         bound, peak, peak_note = "alu", FP64_NOMINAL_TFLOPS, "FP64 nominal (no measured FP64 peak)"
     else:
-        if args.engine == "tensor":
-            # six BF16 products per FP32-accurate product: the useful-flop ceiling of the
-            # split scheme is the measured sustained BF16 rate / 6
+        if args.engine in SCHEMES:
+            # n 16-bit products per FP32-accurate product: the useful-flop ceiling of the
+            # split scheme is the measured sustained BF16 rate / n (FP16 runs at the BF16
+            # rate: nominal ratio 1)
             bound = "tensor"
-            peak = peaks["bf16_tflops_sustained"] / 6.0
-            peak_note = f"bf16 sustained ({peak_src}) / 6 split products"
+            nprod = SCHEMES[args.engine][1]
+            peak = peaks["bf16_tflops_sustained"] / nprod
+            peak_note = f"bf16 sustained ({peak_src}) / {nprod} split products"
         else:
             bound = "alu"
             sm_max = (clk.get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0))
             peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12
             peak_note = "FP32 FMA: 152 SMs x 128 lanes x 2 flop x max SM clock"
-    traffic, traffic_note = (recorded_traffic(len(k) * B) if (args.precision == "mixed" and args.engine == "tensor")
+    traffic, traffic_note = (recorded_traffic(len(k) * B, args.engine) if args.precision == "mixed"
                              else (None, "no ncu record for this kernel"))
     roof = dict(bound=bound, achieved=achieved, peak=peak, unit="TFLOP/s", frac=achieved / peak if peak else None,
                 traffic=traffic, traffic_note=traffic_note, peak_source=peak_note,
@@ -575,7 +585,7 @@ def main():
                 ms_per_step=total_s * 1e3 / args.steps, higher_is_better=True, scaling="weak",
                 vs_baseline=None,
                 dtype="f64" if args.precision == "fp64" else
-                ("bf16x6+f32+df32x2" if args.engine == "tensor" else "f32+df32x2"),
+                (SCHEMES[args.engine][0] + "+f32+df32x2" if args.engine in SCHEMES else "f32+df32x2"),
                 data="synthetic",
                 config=dict(workload=w.name, n_obs=int(len(w.v)), subsets=int(ctx.N), active_subsets=int(len(k)),
                             k_min=int(k.min()), k_max=int(k.max()), m_mean=float(m.mean()), batch=B,
@@ -588,9 +598,10 @@ def main():
                 setup=dict(datagen_s=t_gen, create_s=t_create))
     if phases and phases.get("task"):
         tot = phases["task"]
-        line["phase_share"] = {k2: round(v / tot, 4) for k2, v in phases.items()
-                               if v and k2 not in ("task", "residual_passes", "tasks")}
+        counts = ("task", "residual_passes", "tasks", "fail_factor", "fail_nan", "fail_stall")
+        line["phase_share"] = {k2: round(v / tot, 4) for k2, v in phases.items() if v and k2 not in counts}
         line["residual_passes_per_task"] = phases["residual_passes"] / max(phases["tasks"], 1)
+        line["fp64_fallback_tasks"] = {k2: phases[k2] for k2 in ("fail_factor", "fail_nan", "fail_stall")}
     if rank == 0 and world == 1 and not args.no_cpu:
         active = np.nonzero(np.diff(ctx.V_off) > 0)[0]
         cb = cpu_baseline(w, P[0], args.cpu_budget, active)
@@ -601,7 +612,7 @@ def main():
     ctx.close()
     if rank == 0 and world == 1 and args.serve_seconds > 0:
         line["serving"] = run_serving(pcv, local, args.serve_seconds, args.hbm_budget_gb, args.serve_batch,
-                                      max_slots=args.serve_slots)
+                                      max_slots=args.serve_slots, engine=args.engine)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:

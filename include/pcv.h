@@ -104,10 +104,15 @@ typedef struct {
                                   estimated as ||d_i|| * ||d_i|| / ||d_i-1||, is at most
                                   tol * ||x|| (max norms; default 1e-7); tasks whose
                                   corrections stop shrinking are recomputed in FP64 */
-    int32_t factor_engine;     /* mixed path factorisation: 0 = tensor cores (split-BF16
-                                  tcgen05 trailing updates, default), 1 = FP32 SIMT */
-    int32_t tc_stages;         /* tensor engine: depth of the TMA operand ring, 2 or 3 (default 2);
-                                  fewer stages leave more on-chip memory to the L1 cache */
+    int32_t factor_engine;     /* mixed path factorisation: 0 = tensor cores with FP32 values
+                                  split in two FP16 terms, three products (default; a task
+                                  whose values leave FP16 range, which needs tau2 / sigma2
+                                  above ~6e4, is recomputed in FP64); 1 = FP32 SIMT;
+                                  2 = tensor cores with three BF16 terms, six products
+                                  (FP32 range, half again the operand bytes, twice the MMAs) */
+    int32_t tc_stages;         /* tensor engines: depth of the TMA operand ring, 2 to 4 (0 =
+                                  default: 3 for engine 0, 2 for engine 2); rings above
+                                  96 KB leave one CTA per SM */
 } pcv_options;
 
 /* ---------------------------------------------------------------- host-only */
@@ -185,8 +190,10 @@ pcv_status pcv_kernel_time(pcv_ctx* ctx, double* task_ms, double* combine_ms);
 
 /* Per-phase SM cycles of the mixed task kernel, summed over its CTAs since timing
  * was enabled (or since the last reset), 16 entries: 0 gather + FP32 assembly,
- * 1 tensor-core trailing updates, 2 diagonal blocks, 3 panel solves, 4 BF16
- * splitting, 5 SIMT factorisation (FP32 engine), 6 FP32 triangular solves,
+ * 1 tensor-core trailing updates, 2 diagonal-block factorisations and inverses,
+ * 3 panel solves (tensor cores, against the diagonal block's inverse), 4 loads and
+ * stores of the diagonal blocks and their BF16 planes,
+ * 5 SIMT factorisation (FP32 engine), 6 FP32 triangular solves,
  * 7 double-float residuals, 8 prediction + loss, 9 whole tasks; entries 10 and 11
  * count residual passes and finished tasks, 12..14 tasks handed to the FP64
  * fallback because the factorisation broke down, a correction was not finite, or

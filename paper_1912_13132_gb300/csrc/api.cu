@@ -121,16 +121,18 @@ pcv_options default_options(const pcv_options* o) {
     d.refine_max_iter = 6;
     d.refine_tol = 1e-7;
     d.factor_engine = pcv::kMixedEngineTensor;
-    d.tc_stages = 2;
+    d.tc_stages = 0;
     if (o) {
         if (o->struct_size != 0 && o->struct_size != (int32_t)sizeof(pcv_options)) return d;
         if (o->max_slots > 0) d.max_slots = o->max_slots;
         if (o->workspace_fraction > 0 && o->workspace_fraction <= 0.95) d.workspace_fraction = o->workspace_fraction;
         if (o->refine_max_iter > 0) d.refine_max_iter = o->refine_max_iter;
         if (o->refine_tol > 0) d.refine_tol = o->refine_tol;
-        if (o->factor_engine == pcv::kMixedEngineSimt) d.factor_engine = pcv::kMixedEngineSimt;
-        if (o->tc_stages == 2 || o->tc_stages == 3) d.tc_stages = o->tc_stages;
+        if (o->factor_engine == pcv::kMixedEngineSimt || o->factor_engine == pcv::kMixedEngineTensorBF16)
+            d.factor_engine = o->factor_engine;
+        if (o->tc_stages >= 2 && o->tc_stages <= 4) d.tc_stages = o->tc_stages;
     }
+    if (d.tc_stages == 0) d.tc_stages = pcv::mixed_default_stages(d.factor_engine);
     return d;
 }
 
@@ -146,9 +148,10 @@ void workspace_shape(const pcv_ctx* c, int wi, int64_t& g, int64_t& sb, int64_t&
     const bool fallback = wi == kFallbackWs;
     const int prec = fallback ? PCV_PREC_FP64 : wi;
     ld = round_up(c->kmax, 128);
-    const bool tensor = prec == PCV_PREC_MIXED && c->opts.factor_engine == pcv::kMixedEngineTensor;
+    const int planes = prec == PCV_PREC_MIXED ? pcv::mixed_planes(c->opts.factor_engine) : 0;
+    const bool tensor = planes > 0;
     sb = prec == PCV_PREC_FP64 ? pcv::slot_bytes_fp64(ld, c->mmax) : pcv::slot_bytes_mixed(ld, c->mmax);
-    pb = tensor ? 3 * (int64_t)ld * ld * 2 : 0;   // planes per slot
+    pb = (int64_t)planes * ld * ld * 2;   // 16-bit planes per slot
     // CTAs per SM: two for both mixed engines (the tensor engine holds half of an
     // SM's tensor memory per CTA), one for the FP64 kernel
     const int per_sm = prec == PCV_PREC_MIXED ? 2 : 1;
@@ -172,10 +175,11 @@ pcv_status ensure_workspace(pcv_ctx* c, int wi) {
     cudaError_t e = w.mem.reserve((size_t)(g * sb));
     if (e != cudaSuccess) return cuda_fail(e, "workspace allocation");
     if (tensor) {
+        const int np = pcv::mixed_planes(c->opts.factor_engine);
         w.plane_elems = g * (int64_t)ld * ld;
-        e = w.planes.reserve((size_t)(3 * w.plane_elems * 2));
+        e = w.planes.reserve((size_t)(np * w.plane_elems * 2));
         if (e != cudaSuccess) return cuda_fail(e, "plane allocation");
-        if (!pcv::mixed_make_maps(w.planes.p, w.plane_elems, ld, (int)g, w.maps))
+        if (!pcv::mixed_make_maps(w.planes.p, w.plane_elems, ld, (int)g, np, w.maps))
             return fail(PCV_ERR_CUDA, "tensor map encoding failed");
     }
     w.grid = (int)g;

@@ -112,13 +112,14 @@ PCV_HD float pow2_neg(int n) {
 }
 
 // Constants of the exponential, filled on the host (see exp_constants below).
-struct ExpConsts {
+struct alignas(8) ExpConsts {
     float tbl[2 * kExpTable];  // 2^(-i/256) = tbl[2i] + tbl[2i+1]
     float inv_c;               // 256 / ln2 (rounded)
     float c1, c2, c3;          // ln2/256 = c1 + c2 + c3, c1 with 9 significant bits
 };
 
 // exp(-t) for a double-float t >= 0; 0 beyond t = 87 (below FLT_MIN territory).
+// `tbl` must be 8-byte aligned on the device.
 PCV_HD df exp_neg(df t, const float* tbl, float inv_c, float c1, float c2, float c3) {
     if (!(t.h < 87.0f)) return {0.0f, 0.0f};
     const float jf = rintf(t.h * inv_c);
@@ -138,7 +139,12 @@ PCV_HD df exp_neg(df t, const float* tbl, float inv_c, float c1, float c2, float
     // table value times (1 + q)
     const int i = j & (kExpTable - 1);
     const int n = j >> 8;
+#if defined(__CUDA_ARCH__)
+    const float2 t2 = reinterpret_cast<const float2*>(tbl)[i];   // one 8-byte load
+    const df T = {t2.x, t2.y};
+#else
     const df T = {tbl[2 * i], tbl[2 * i + 1]};
+#endif
     const df Tq = mul(T, q);
     df res = two_sum(T.h, Tq.h);
     res = fast_two_sum(res.h, res.l + T.l + Tq.l);

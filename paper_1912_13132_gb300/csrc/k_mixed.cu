@@ -18,6 +18,7 @@
 // converge is appended to a fallback list that the FP64 kernel then runs.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <mutex>
 
@@ -99,7 +100,7 @@ struct alignas(16) SmemM {
     float L[NB][NB + 1];           // diagonal block
     float rinv[NB];                // reciprocals of the diagonal of L_JJ
     float ph[16][NB], pl[16][NB];  // residual partial sums (double-float)
-    float wj[NB];
+    float wj[2 * NB];              // solve block (128 entries in the tensor-core kernel)
     double dred[NT / 32];
     float fred[NT / 32];
     int flag;
@@ -112,7 +113,7 @@ struct alignas(16) SmemSimt {
 };
 
 // Shared memory kept for the whole kernel.
-struct SmemKeep {
+struct alignas(8) SmemKeep {
     float tbl[2 * dfm::kExpTable]; // exp table (copy of c_exp.tbl)
     int task;
 };
@@ -255,9 +256,15 @@ __device__ bool factor32(SmemM& sm, SmemSimt& st, const SlotM& S, int k, int64_t
 
 constexpr int TB = umma::kTileN;          // 128-wide block columns
 constexpr int kTcTilesPerPass = 1;        // one 128-row tile per pass: 256 TMEM columns per CTA
-constexpr int kTcStage = umma::stage_bytes(kTcTilesPerPass);   // 48 KB
 constexpr uint32_t kTcTmemCols = 2 * kTcTilesPerPass * umma::kTileN;
+// The operand ring (stages x stage bytes of the scheme) doubles as the shared memory of
+// the phases between trailing updates, which need kTcRingMin bytes: 2 stages of the
+// three-plane scheme, 3 of the two-plane one.
+constexpr int kTcRingMin = 96 * 1024;
+template <class Sch>
+__host__ __device__ constexpr int tc_ring_bytes(int nst) { return nst * umma::stage_bytes<Sch>(kTcTilesPerPass); }
 constexpr int DP = TB + 4;                // row pitch of the diagonal block (rows 16-byte aligned)
+static_assert(TB == 2 * NB, "the tensor-core solves use 2 * NB-wide blocks");
 
 struct TcShared {
     umma::Pipe pipe;
@@ -269,16 +276,235 @@ struct TcCtx {
     uint8_t* stages;                      // operand ring; between updates also the diagonal block
     umma::Phases ph;
     const CUtensorMap *m0, *m1, *m2;
-    __nv_bfloat16 *p0, *p1, *p2;          // this slot's planes (row-major, ld x ld)
+    uint16_t* p[3];                       // this slot's planes (16-bit terms, tiled, ld x ld)
     int row_base;                         // this slot's first row in the tensor maps
 };
 
-// Left-looking blocked Cholesky with 128-wide block columns: the update of block
-// column J by all finished columns (the O(k^3) part) runs on the tensor cores from
-// the BF16 planes; the diagonal block and the panel solve run in FP32; the
-// finished block column is then split into the planes.  The FP32 factor stays in
-// S.L (column-major) for the triangular solves.  False if a pivot is not positive
+// Element (r, c) of a slot's planes: 128 x 32 tiles, tile (r / 128, c / 32),
+// row-major inside a tile (the layout the 3-D tensor maps address).
+__device__ __forceinline__ int64_t plane_off(int r, int c, int64_t ld) {
+    return ((int64_t)(r >> 7) * (ld >> 5) + (c >> 5)) * 4096 + (r & 127) * 32 + (c & 31);
+}
+
+// Eight consecutive FP32 values (c multiple of 8) split into the scheme's planes.
+template <class Sch>
+__device__ __forceinline__ void store_planes8(const TcCtx& tc, int64_t off, const float* x) {
+    __align__(16) uint16_t t[Sch::kPlanes][8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        uint16_t u[Sch::kPlanes];
+        umma::split_terms(Sch{}, x[q], u);
+#pragma unroll
+        for (int pl = 0; pl < Sch::kPlanes; ++pl) t[pl][q] = u[pl];
+    }
+#pragma unroll
+    for (int pl = 0; pl < Sch::kPlanes; ++pl)
+        *reinterpret_cast<uint4*>(tc.p[pl] + off) = *reinterpret_cast<const uint4*>(t[pl]);
+}
+
+// Cholesky of the nb x nb (nb <= 32) sub-block of D at (c0, c0) by one warp: lane i
+// holds row i in registers; column c is scaled by its pivot, then the later columns
+// take the rank-1 update with the scaled entries of the rows they belong to, fetched
+// by shuffles.  Every lane runs every update (no divergent branches): entries above a
+// lane's diagonal then hold meaningless values, which are never read -- the sub-block's
+// upper triangle in D is scratch.  Writes 1 / L[c][c] to rinv; false (the same in all
+// lanes) if a pivot is not positive.
+__device__ __forceinline__ bool chol32_warp(float (*D)[DP], float* rinv, int c0, int nb, int lane) {
+    float a[32];
+    const bool live = lane < nb;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) a[j] = live ? D[c0 + lane][c0 + j] : 0.0f;
+    bool ok = true;
+#pragma unroll
+    for (int c = 0; c < 32; ++c) {
+        if (c < nb) {
+            float piv = __shfl_sync(0xffffffffu, a[c], c);
+            if (!(piv > 0.0f)) {
+                ok = false;
+                piv = 1.0f;
+            }
+            const float d = sqrtf(piv), rd = 1.0f / d;
+            a[c] = lane == c ? d : a[c] * rd;
+            rinv[c0 + c] = rd;
+#pragma unroll
+            for (int j = c + 1; j < 32; ++j) a[j] = fmaf(-a[c], __shfl_sync(0xffffffffu, a[c], j), a[j]);
+        }
+    }
+    if (live) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) D[c0 + lane][c0 + j] = a[j];
+    }
+    return ok;
+}
+
+// Rows t0..jb-1 of D, columns c0..c0+31: x L11^T = row with L11 the factored 32 x 32
+// sub-block at (c0, c0); one row per thread, four partial sums.
+__device__ __forceinline__ void trsm32_rows(float (*D)[DP], const float* rinv, int c0, int t0, int jb) {
+    for (int r = t0 + (int)threadIdx.x; r < jb; r += NT) {
+        float y[32];
+#pragma unroll
+        for (int p = 0; p < 32; p += 4) {
+            const float4 v = *reinterpret_cast<const float4*>(&D[r][c0 + p]);
+            y[p] = v.x;
+            y[p + 1] = v.y;
+            y[p + 2] = v.z;
+            y[p + 3] = v.w;
+        }
+#pragma unroll
+        for (int c = 0; c < 32; ++c) {
+            float a0 = y[c], a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
+#pragma unroll
+            for (int p = 0; p + 3 < c; p += 4) {
+                const float4 d = *reinterpret_cast<const float4*>(&D[c0 + c][c0 + p]);
+                a0 = fmaf(-y[p], d.x, a0);
+                a1 = fmaf(-y[p + 1], d.y, a1);
+                a2 = fmaf(-y[p + 2], d.z, a2);
+                a3 = fmaf(-y[p + 3], d.w, a3);
+            }
+#pragma unroll
+            for (int p = (c / 4) * 4; p < c; ++p) a0 = fmaf(-y[p], D[c0 + c][c0 + p], a0);
+            y[c] = ((a0 + a1) + (a2 + a3)) * rinv[c0 + c];
+        }
+#pragma unroll
+        for (int p = 0; p < 32; p += 4)
+            *reinterpret_cast<float4*>(&D[r][c0 + p]) = make_float4(y[p], y[p + 1], y[p + 2], y[p + 3]);
+    }
+}
+
+// Trailing update D[r][q] -= sum_c D[r][c0 + c] D[q][c0 + c] for t0 <= q <= r < jb, in 4 x 4
+// tiles of (r, q), one tile per thread; rows past jb are read clamped and not written.
+__device__ __forceinline__ void syrk32_trailing(float (*D)[DP], int c0, int t0, int jb) {
+    const int nt4 = (jb - t0 + 3) / 4;
+    const int ntiles = nt4 * (nt4 + 1) / 2;
+    for (int e = threadIdx.x; e < ntiles; e += NT) {
+        // e -> (bi, bj) with bj <= bi, row-major over the lower triangle of tiles
+        int bi = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+        while (bi * (bi + 1) / 2 > e) --bi;
+        while ((bi + 1) * (bi + 2) / 2 <= e) ++bi;
+        const int bj = e - bi * (bi + 1) / 2;
+        const int r0 = t0 + 4 * bi, q0 = t0 + 4 * bj;
+        float acc[4][4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] = 0.0f;
+#pragma unroll
+        for (int p = 0; p < 32; p += 4) {
+            float4 ar[4], br[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                ar[u] = *reinterpret_cast<const float4*>(&D[min(r0 + u, TB - 1)][c0 + p]);
+                br[u] = *reinterpret_cast<const float4*>(&D[min(q0 + u, TB - 1)][c0 + p]);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v)
+                    acc[u][v] = fmaf(ar[u].x, br[v].x, fmaf(ar[u].y, br[v].y,
+                                fmaf(ar[u].z, br[v].z, fmaf(ar[u].w, br[v].w, acc[u][v]))));
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const int r = r0 + u, q = q0 + v;
+                if (r < jb && q <= r) D[r][q] -= acc[u][v];
+            }
+    }
+}
+
+// Column j (= lane) of the inverse of the 32 x 32 lower-triangular block of D at
+// (c0, c0), by forward substitution in registers (x_i = 0 above the diagonal), written
+// back in place, zeros above the diagonal.  rinv holds the reciprocal diagonal.
+__device__ __forceinline__ void inv32_warp(float (*D)[DP], const float* rinv, int c0, int lane) {
+    float x[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+        float s = 0.0f;
+#pragma unroll
+        for (int p = 0; p < i; ++p) s = fmaf(D[c0 + i][c0 + p], x[p], s);
+        const float ri = rinv[c0 + i];
+        x[i] = i == lane ? ri : (i > lane ? -s * ri : 0.0f);
+    }
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < 32; ++i) D[c0 + i][c0 + lane] = x[i];
+}
+
+// In-place inverse of the 128 x 128 lower-triangular factor in D, in 32 x 32 blocks:
+// the four diagonal blocks first (one warp each), then the column blocks J = 2, 1, 0
+// from the identity Linv L = I:
+//   Linv[I][J] = -( sum_{K=J+1..I} Linv[I][K] L[K][J] ) Linv[J][J],   I > J,
+// whose right-hand side only reads finished inverse blocks and column block J of L,
+// which is overwritten last.  Y is 3 x 32 x 32 floats of scratch.
+__device__ void trinv128(float (*D)[DP], const float* rinv, float* Y) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (warp < 4) inv32_warp(D, rinv, 32 * warp, lane);
+    __syncthreads();
+    for (int J = 2; J >= 0; --J) {
+        const int nI = 3 - J;
+        for (int e = tid; e < nI * 256; e += NT) {
+            const int b = e >> 8, r0 = ((e >> 5) & 7) * 4, c = e & 31, I = J + 1 + b;
+            float y[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+            for (int K = J + 1; K <= I; ++K) {
+#pragma unroll
+                for (int p = 0; p < 32; p += 4) {
+                    float col[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) col[q] = D[32 * K + p + q][32 * J + c];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const float4 a = *reinterpret_cast<const float4*>(&D[32 * I + r0 + u][32 * K + p]);
+                        y[u] = fmaf(a.x, col[0], fmaf(a.y, col[1], fmaf(a.z, col[2], fmaf(a.w, col[3], y[u]))));
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) Y[(b * 32 + r0 + u) * 32 + c] = y[u];
+        }
+        __syncthreads();
+        for (int e = tid; e < nI * 256; e += NT) {
+            const int b = e >> 8, r0 = ((e >> 5) & 7) * 4, c = e & 31, I = J + 1 + b;
+            float z[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+            for (int p = 0; p < 32; p += 4) {
+                float col[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) col[q] = D[32 * J + p + q][32 * J + c];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const float4 a = *reinterpret_cast<const float4*>(&Y[(b * 32 + r0 + u) * 32 + p]);
+                    z[u] = fmaf(a.x, col[0], fmaf(a.y, col[1], fmaf(a.z, col[2], fmaf(a.w, col[3], z[u]))));
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) D[32 * I + r0 + u][32 * J + c] = -z[u];
+        }
+        __syncthreads();
+    }
+}
+
+// Shared-memory use of the factorisation between trailing updates (inside the
+// operand ring): diagonal block, reciprocal diagonal, flag, inverse scratch.
+constexpr int kDiagRinvOff = TB * DP * 4;
+constexpr int kDiagFlagOff = kDiagRinvOff + TB * 4;
+constexpr int kDiagYOff = kDiagFlagOff + 16;
+constexpr int kDiagRedOff = kDiagYOff + 3 * 32 * 32 * 4;   // per-warp maxima
+constexpr int kDiagBytes = kDiagRedOff + (NT / 32) * 4;
+
+// Left-looking blocked Cholesky with 128-wide block columns, all O(k^3) work on the
+// tensor cores from split-BF16 planes.  For block column J:
+//   update   C = A[j0:, J] - L[j0:, :j0] L[J, :j0]^T   (tensor cores; the diagonal
+//            block's rows stay FP32, the rows below go to the planes only)
+//   diagonal L_JJ L_JJ^T = C_JJ in FP32 (blocked, shared memory), then L_JJ^-1
+//   panel    L[below, J] = C[below, J] L_JJ^-T          (tensor cores, the inverse's
+//            planes in the diagonal block's place, which no later update reads)
+// The panel's epilogue writes the FP32 factor (kept in S.L, column-major, for the
+// triangular solves) and its planes for the updates of later block columns.  S.L
+// keeps L_JJ^-1 (zeros above its diagonal) in place of each diagonal block: the
+// solves multiply by it instead of substituting.  False if a pivot is not positive
 // or a bounded wait ran out.
+template <class Sch>
 __device__ bool factor_tc(TcCtx& tc, const SlotM& S, int k, int64_t ld, unsigned long long* clk) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     PhaseTimer tm(clk);
@@ -286,44 +512,64 @@ __device__ bool factor_tc(TcCtx& tc, const SlotM& S, int k, int64_t ld, unsigned
     umma::fence_proxy_async();
     __syncthreads();
     float (*D)[DP] = reinterpret_cast<float (*)[DP]>(tc.stages);
-    float* rinv = reinterpret_cast<float*>(tc.stages + TB * DP * 4);
-    float* colc = rinv + TB;
-    int* flag = reinterpret_cast<int*>(colc + TB);
+    float* rinv = reinterpret_cast<float*>(tc.stages + kDiagRinvOff);
+    int* flag = reinterpret_cast<int*>(tc.stages + kDiagFlagOff);
+    float* Y = reinterpret_cast<float*>(tc.stages + kDiagYOff);
+    float* L = S.L;
     const int nb = (k + TB - 1) / TB;
     for (int J = 0; J < nb; ++J) {
         const int j0 = J * TB, jb = min(TB, k - j0);
+        const bool below = j0 + TB < k;   // rows below the diagonal block (then jb == TB)
         if (j0 > 0) {
-            float* L = S.L;
             auto epi = [&](int row0, int quad, uint32_t taddr) {
                 const int r = row0 + quad * 32 + (threadIdx.x & 31);
+                const bool diag_rows = row0 < j0 + TB;
 #pragma unroll 1
                 for (int c0 = 0; c0 < TB; c0 += 32) {
                     float v[32];
                     umma::tmem_ld32(taddr + c0, v);
                     if (r < k) {
+                        float* Lr = L + r + (int64_t)(j0 + c0) * ld;
+                        if (diag_rows) {
 #pragma unroll
-                        for (int j = 0; j < 32; ++j)
-                            if (c0 + j < jb) L[r + (int64_t)(j0 + c0 + j) * ld] -= v[j];
+                            for (int j = 0; j < 32; ++j)
+                                if (c0 + j < jb) Lr[(int64_t)j * ld] -= v[j];
+                        } else {
+#pragma unroll
+                            for (int j = 0; j < 32; ++j) v[j] = Lr[(int64_t)j * ld] - v[j];
+                            const int64_t off = plane_off(r, j0 + c0, ld);
+#pragma unroll
+                            for (int g = 0; g < 4; ++g) store_planes8<Sch>(tc, off + 8 * g, v + 8 * g);
+                        }
                     }
                 }
             };
             const bool ok = tc.sh->dead == 0 &&
-                            umma::block_column<true, kTcTilesPerPass>(tc.sh->pipe, tc.ph, tc.stages, tc.m0, tc.m1, tc.m2,
+                            umma::block_column<true, kTcTilesPerPass, Sch>(tc.sh->pipe, tc.ph, tc.stages, tc.m0, tc.m1, tc.m2,
                                                      tc.row_base, j0, k - j0, j0, j0, epi, (int)(ld / 32));
             if (!ok) atomicExch(&tc.sh->dead, 1);
             __syncthreads();
             if (tc.sh->dead) return false;
             tm.lap(kPhUpdate);
+        } else if (below) {
+            // first block column: the assembled rows below the diagonal block into the planes
+            for (int e = tid; e < (k - TB) * (TB / 8); e += NT) {
+                const int r = TB + e % (k - TB), g = e / (k - TB);
+                float x[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) x[q] = L[r + (int64_t)(g * 8 + q) * ld];
+                store_planes8<Sch>(tc, plane_off(r, g * 8, ld), x);
+            }
+            tm.lap(kPhDiagIO);
         }
-        // diagonal block: blocked right-looking Cholesky in shared memory, 32 columns per step
-        // whole 128 x 128 block, four rows per float4 (rows beyond k hold stale values
-        // that are never used); 16 independent loads per thread
+        // diagonal block in shared memory: whole 128 x 128 block, four rows per float4
+        // (rows beyond k hold stale values that are never used); 16 independent loads per thread
         {
             float4 v[TB * TB / 4 / NT];
 #pragma unroll
             for (int i = 0; i < TB * TB / 4 / NT; ++i) {
                 const int e = tid + i * NT, r4 = (e & (TB / 4 - 1)) * 4, c = e / (TB / 4);
-                v[i] = *reinterpret_cast<const float4*>(S.L + (j0 + r4) + (int64_t)(j0 + c) * ld);
+                v[i] = *reinterpret_cast<const float4*>(L + (j0 + r4) + (int64_t)(j0 + c) * ld);
             }
 #pragma unroll
             for (int i = 0; i < TB * TB / 4 / NT; ++i) {
@@ -334,127 +580,112 @@ __device__ bool factor_tc(TcCtx& tc, const SlotM& S, int k, int64_t ld, unsigned
                 D[r4 + 3][c] = v[i].w;
             }
         }
+        if (jb < TB) {
+            // last, partial block: identity beyond jb, so the factor and its inverse are
+            // block diagonal with an identity pad (rows and columns past k never mix in)
+            for (int e = tid; e < TB * TB; e += NT) {
+                const int r = e / TB, c = e % TB;
+                if (r >= jb || c >= jb) D[r][c] = r == c ? 1.0f : 0.0f;
+            }
+        }
         if (tid == 0) *flag = 0;
         __syncthreads();
-        // right-looking, all threads: scale column c into a contiguous copy, then the
-        // rank-1 update of the trailing lower triangle (warp per row, lanes along the row)
-        for (int c = 0; c < jb; ++c) {
-            // every thread takes the pivot itself (no extra barrier)
-            float piv = D[c][c];
-            const bool badp = !(piv > 0.0f);
-            if (badp) piv = 1.0f;
-            const float d = sqrtf(piv), rd = 1.0f / d;
-            if (tid == 0) {
-                if (badp) *flag = 1;
-                rinv[c] = rd;
-            }
-            for (int r = c + 1 + tid; r < jb; r += NT) {
-                const float l = D[r][c] * rd;
-                D[r][c] = l;
-                colc[r] = l;
-            }
+        tm.lap(kPhDiagIO);
+        // blocked right-looking Cholesky, 32 columns per step: the 32 x 32 diagonal
+        // sub-block by one warp in registers, the rows below it against that factor, then
+        // the symmetric update of the trailing part (three barriers per step)
+        for (int c0 = 0; c0 < TB; c0 += 32) {
+            if (warp == 0 && !chol32_warp(D, rinv, c0, 32, lane) && lane == 0) *flag = 1;
             __syncthreads();
-            if (tid == 0) D[c][c] = d;
-            // rank-1 update, four rows per warp step (independent read-modify-writes)
-            for (int r0 = c + 1 + 4 * warp; r0 < jb; r0 += 4 * (NT / 32)) {
-                float lr[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) lr[u] = r0 + u < jb ? colc[r0 + u] : 0.0f;
-                const int qmax = min(r0 + 3, jb - 1);
-                for (int q = c + 1 + lane; q <= qmax; q += 32) {
-                    const float cq = colc[q];
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const int r = r0 + u;
-                        if (r < jb && q <= r) D[r][q] = fmaf(-lr[u], cq, D[r][q]);
-                    }
-                }
+            const int t0 = c0 + 32;
+            if (t0 < TB) {
+                trsm32_rows(D, rinv, c0, t0, TB);
+                __syncthreads();
+                syrk32_trailing(D, c0, t0, TB);
+                __syncthreads();
             }
-            __syncthreads();
         }
         if (*flag) return false;
-#pragma unroll
-        for (int i = 0; i < TB * TB / 4 / NT; ++i) {   // write back (upper part: never read)
-            const int e = tid + i * NT, r4 = (e & (TB / 4 - 1)) * 4, c = e / (TB / 4);
-            *reinterpret_cast<float4*>(S.L + (j0 + r4) + (int64_t)(j0 + c) * ld) =
-                make_float4(D[r4][c], D[r4 + 1][c], D[r4 + 2][c], D[r4 + 3][c]);
-        }
+        // L_JJ^-1 in place; the FP32 factor keeps the inverse in the diagonal block's
+        // place (the triangular solves multiply by it), zeros above its diagonal
+        trinv128(D, rinv, Y);
         tm.lap(kPhDiag);
-        // rows below the diagonal block: x L_JJ^T = row, 32 columns at a time (the solved
-        // columns are read back from the panel; 4 partial sums in the triangular part)
-        for (int r = j0 + jb + tid; r < k; r += NT) {
-            float* Lr = S.L + r + (int64_t)j0 * ld;
-            for (int q0 = 0; q0 < jb; q0 += 32) {
-                float y[32];
 #pragma unroll
-                for (int c = 0; c < 32; ++c) y[c] = q0 + c < jb ? Lr[(int64_t)(q0 + c) * ld] : 0.0f;
-                float n0 = 0.0f, n1 = 0.0f, n2 = 0.0f, n3 = 0.0f;
-                if (q0 > 0) {
-                    n0 = Lr[0];
-                    n1 = Lr[ld];
-                    n2 = Lr[2 * ld];
-                    n3 = Lr[3 * ld];
-                }
-                for (int p = 0; p < q0; p += 4) {
-                    const float x0 = n0, x1 = n1, x2 = n2, x3 = n3;
-                    if (p + 4 < q0) {   // next solved values in flight during this step
-                        n0 = Lr[(int64_t)(p + 4) * ld];
-                        n1 = Lr[(int64_t)(p + 5) * ld];
-                        n2 = Lr[(int64_t)(p + 6) * ld];
-                        n3 = Lr[(int64_t)(p + 7) * ld];
-                    }
-#pragma unroll
-                    for (int c = 0; c < 32; ++c) {
-                        const float4 d = *reinterpret_cast<const float4*>(&D[q0 + c][p]);
-                        y[c] = fmaf(-x0, d.x, fmaf(-x1, d.y, fmaf(-x2, d.z, fmaf(-x3, d.w, y[c]))));
-                    }
-                }
-#pragma unroll
-                for (int c = 0; c < 32; ++c) {
-                    float a0 = y[c], a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
-#pragma unroll
-                    for (int p = 0; p + 3 < c; p += 4) {
-                        const float4 d = *reinterpret_cast<const float4*>(&D[q0 + c][q0 + p]);
-                        a0 = fmaf(-y[p], d.x, a0);
-                        a1 = fmaf(-y[p + 1], d.y, a1);
-                        a2 = fmaf(-y[p + 2], d.z, a2);
-                        a3 = fmaf(-y[p + 3], d.w, a3);
-                    }
-#pragma unroll
-                    for (int p = (c / 4) * 4; p < c; ++p) a0 = fmaf(-y[p], D[q0 + c][q0 + p], a0);
-                    y[c] = q0 + c < jb ? ((a0 + a1) + (a2 + a3)) * rinv[q0 + c] : 0.0f;
-                }
-#pragma unroll
-                for (int c = 0; c < 32; ++c)
-                    if (q0 + c < jb) Lr[(int64_t)(q0 + c) * ld] = y[c];
-            }
+        for (int i = 0; i < TB * TB / 4 / NT; ++i) {
+            const int e = tid + i * NT, r4 = (e & (TB / 4 - 1)) * 4, c = e / (TB / 4);
+            *reinterpret_cast<float4*>(L + (j0 + r4) + (int64_t)(j0 + c) * ld) =
+                make_float4(c <= r4 ? D[r4][c] : 0.0f, c <= r4 + 1 ? D[r4 + 1][c] : 0.0f,
+                            c <= r4 + 2 ? D[r4 + 2][c] : 0.0f, c <= r4 + 3 ? D[r4 + 3][c] : 0.0f);
         }
+        if (!below) {   // last block column
+            __syncthreads();
+            tm.lap(kPhDiagIO);
+            break;
+        }
+        // the inverse's planes in the diagonal block's place: the panel's B operand,
+        // B[n][q] = 2^-e L_JJ^-1[n][q], with the power of two 2^e >= max |L_JJ^-1| keeping
+        // the terms in range of a 16-bit format (the panel's epilogue scales back)
+        float amax = 0.0f;
+        for (int e = tid; e < TB * TB; e += NT) {
+            const int r = e / TB, c = e % TB;
+            if (c <= r) amax = fmaxf(amax, fabsf(D[r][c]));
+        }
+        amax = warp_max(amax);
+        float* red = reinterpret_cast<float*>(tc.stages + kDiagRedOff);
+        if (lane == 0) red[warp] = amax;
         __syncthreads();
-        tm.lap(kPhPanel);
-        // split the finished block column into the BF16 planes (rows j0.., 8 columns per item)
-        const int ng = (jb + 7) / 8;
-        for (int e = tid; e < (k - j0) * ng; e += NT) {
-            const int r = j0 + e % (k - j0), g = e / (k - j0);
-            __align__(16) __nv_bfloat16 h[8], m[8], l[8];
+        amax = red[0];
+#pragma unroll
+        for (int w = 1; w < NT / 32; ++w) amax = fmaxf(amax, red[w]);
+        const int ex = amax > 1.0f ? ilogbf(amax) + 1 : 0;   // amax < 2^ex
+        const float down = scalbnf(1.0f, -ex), up = scalbnf(1.0f, ex);
+        for (int e = tid; e < TB * (TB / 8); e += NT) {
+            const int r = e / (TB / 8), g = e % (TB / 8);
+            float x[8];
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
                 const int c = g * 8 + q;
-                const float v = (c < jb && j0 + c <= r) ? S.L[r + (int64_t)(j0 + c) * ld] : 0.0f;
-                umma::split3(v, h[q], m[q], l[q]);
+                x[q] = c <= r ? D[r][c] * down : 0.0f;
             }
-            // tiled plane layout: 128 x 32 tiles, tile (r / 128, c / 32), row-major inside
-            const int c = j0 + g * 8;
-            const int64_t off = ((int64_t)(r >> 7) * (ld >> 5) + (c >> 5)) * 4096 + (r & 127) * 32 + (c & 31);
-            *reinterpret_cast<uint4*>(tc.p0 + off) = *reinterpret_cast<const uint4*>(h);
-            *reinterpret_cast<uint4*>(tc.p1 + off) = *reinterpret_cast<const uint4*>(m);
-            *reinterpret_cast<uint4*>(tc.p2 + off) = *reinterpret_cast<const uint4*>(l);
+            store_planes8<Sch>(tc, plane_off(j0 + r, j0 + g * 8, ld), x);
         }
-        // the planes are read next by TMA (async proxy); the diagonal-block buffer is
-        // overwritten next by TMA
+        // the planes are read next by TMA (async proxy), which also overwrites the
+        // diagonal-block buffer
         asm volatile("fence.proxy.async.global;" ::: "memory");
         umma::fence_proxy_async();
         __syncthreads();
-        tm.lap(kPhSplit);
+        tm.lap(kPhDiagIO);
+        {
+            auto epi = [&](int row0, int quad, uint32_t taddr) {
+                const int r = row0 + quad * 32 + (threadIdx.x & 31);
+#pragma unroll 1
+                for (int c0 = 0; c0 < TB; c0 += 32) {
+                    float v[32];
+                    umma::tmem_ld32(taddr + c0, v);
+                    if (r < k) {
+                        float* Lr = L + r + (int64_t)(j0 + c0) * ld;
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) {
+                            v[j] *= up;
+                            Lr[(int64_t)j * ld] = v[j];
+                        }
+                        const int64_t off = plane_off(r, j0 + c0, ld);
+#pragma unroll
+                        for (int g = 0; g < 4; ++g) store_planes8<Sch>(tc, off + 8 * g, v + 8 * g);
+                    }
+                }
+            };
+            const bool ok = tc.sh->dead == 0 &&
+                            umma::block_column<true, kTcTilesPerPass, Sch>(tc.sh->pipe, tc.ph, tc.stages, tc.m0, tc.m1, tc.m2,
+                                                     tc.row_base, j0 + TB, k - j0 - TB, j0, TB, epi,
+                                                     (int)(ld / 32), j0 / 32);
+            if (!ok) atomicExch(&tc.sh->dead, 1);
+            // the panel's planes are read by the next update's TMA loads
+            asm volatile("fence.proxy.async.global;" ::: "memory");
+            __syncthreads();
+            if (tc.sh->dead) return false;
+            tm.lap(kPhPanel);
+        }
     }
     return true;
 }
@@ -578,6 +809,115 @@ __device__ void backward32(SmemM& sm, const float* L, int64_t ld, float* w, int 
             }
             if (lane < jb) w[j0 + lane] = v0;
             if (lane + 32 < jb) w[j0 + lane + 32] = v1;
+        }
+        __syncthreads();
+    }
+}
+
+// Triangular solves of the tensor-core kernel, whose FP32 factor holds the inverse
+// of every 128 x 128 diagonal block (see factor_tc).  w <- L^-1 w, block by block:
+// w_J <- L_JJ^-1 w_J (a product: two threads per row, 64 columns each), then the
+// rows below take w[r] -= L[r, J] w_J.
+__device__ void forward_inv(SmemM& sm, const float* L, int64_t ld, float* w, int k) {
+    constexpr int TBs = 2 * NB;
+    const int tid = threadIdx.x;
+    float* part = &sm.ph[0][0];
+    const int nb = (k + TBs - 1) / TBs;
+    for (int J = 0; J < nb; ++J) {
+        const int j0 = J * TBs, jb = min(TBs, k - j0);
+        if (tid < TBs) sm.wj[tid] = tid < jb ? w[j0 + tid] : 0.0f;
+        __syncthreads();
+        {
+            const int r = tid & (TBs - 1), h = tid >> 7;
+            float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
+            if (r < jb) {
+                const float* Lc = L + (j0 + r) + (int64_t)(j0 + 64 * h) * ld;
+                const float* v = sm.wj + 64 * h;
+#pragma unroll 4
+                for (int c = 0; c < 64; c += 4) {
+                    s0 = fmaf(Lc[(int64_t)c * ld], v[c], s0);
+                    s1 = fmaf(Lc[(int64_t)(c + 1) * ld], v[c + 1], s1);
+                    s2 = fmaf(Lc[(int64_t)(c + 2) * ld], v[c + 2], s2);
+                    s3 = fmaf(Lc[(int64_t)(c + 3) * ld], v[c + 3], s3);
+                }
+            }
+            part[tid] = (s0 + s1) + (s2 + s3);
+        }
+        __syncthreads();
+        if (tid < jb) {
+            const float v = part[tid] + part[tid + TBs];
+            w[j0 + tid] = v;
+            sm.wj[tid] = v;
+        }
+        __syncthreads();
+        if (jb == TBs) {
+            for (int r = j0 + TBs + tid; r < k; r += NT) {
+                const float* Lr = L + r + (int64_t)j0 * ld;
+                float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
+#pragma unroll 8
+                for (int c = 0; c < TBs; c += 4) {
+                    s0 = fmaf(Lr[(int64_t)c * ld], sm.wj[c], s0);
+                    s1 = fmaf(Lr[(int64_t)(c + 1) * ld], sm.wj[c + 1], s1);
+                    s2 = fmaf(Lr[(int64_t)(c + 2) * ld], sm.wj[c + 2], s2);
+                    s3 = fmaf(Lr[(int64_t)(c + 3) * ld], sm.wj[c + 3], s3);
+                }
+                w[r] -= (s0 + s1) + (s2 + s3);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// w <- L^-T w, blocks from the last: v = w_J - L[below, J]^T w[below] (warp wp takes
+// columns 16 wp .. 16 wp + 15, lanes walk the rows), then w_J <- L_JJ^-T v (warp per
+// column: the inverse's column is contiguous, lanes split it, warp sum).
+__device__ void backward_inv(SmemM& sm, const float* L, int64_t ld, float* w, int k) {
+    constexpr int TBs = 2 * NB;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nb = (k + TBs - 1) / TBs;
+    for (int J = nb - 1; J >= 0; --J) {
+        const int j0 = J * TBs, jb = min(TBs, k - j0);
+        {
+            const int c0 = warp * 16;
+            float s[16];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) s[q] = 0.0f;
+            if (jb == TBs) {
+                int p = j0 + TBs + lane;
+                for (; p + 32 < k; p += 64) {   // two rows per lane in flight
+                    const float w0 = w[p], w1 = w[p + 32];
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) {
+                        const float* Lq = L + (int64_t)(j0 + c0 + q) * ld;
+                        s[q] = fmaf(Lq[p], w0, fmaf(Lq[p + 32], w1, s[q]));
+                    }
+                }
+                for (; p < k; p += 32) {
+                    const float wp = w[p];
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) s[q] = fmaf(L[p + (int64_t)(j0 + c0 + q) * ld], wp, s[q]);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                float v = s[q];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (lane == 0) {
+                    const int c = c0 + q;
+                    sm.wj[c] = c < jb ? w[j0 + c] - v : 0.0f;
+                }
+            }
+        }
+        __syncthreads();
+        for (int c = warp; c < jb; c += NT / 32) {
+            const float* Lc = L + j0 + (int64_t)(j0 + c) * ld;
+            float v = 0.0f;
+#pragma unroll
+            for (int u = 0; u < TBs / 32; ++u) v = fmaf(Lc[lane + 32 * u], sm.wj[lane + 32 * u], v);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) w[j0 + c] = v;
         }
         __syncthreads();
     }
@@ -710,7 +1050,7 @@ __device__ void residual_df(SmemM& sm, const float* tbl, const SlotM& S, int k, 
 
 // ---------------------------------------------------------------- one task
 
-template <bool TC>
+template <bool TC, class Sch = umma::SplitBF16x3>
 __device__ void run_task(SmemM& sm, SmemKeep& keep, SmemSimt* simt, TcCtx* tc, const TaskArgs& a, int t, int i,
                          int b) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -745,14 +1085,14 @@ __device__ void run_task(SmemM& sm, SmemKeep& keep, SmemSimt* simt, TcCtx* tc, c
     omax = block_max(sm, omax) * (float)sc * 1.0001f;
     // |offset| < 2^eb, grid 2^-(21 - eb): high parts and their differences need <= 23 bits
     const int eb = max(0, ilogbf(fmaxf(omax, 1.0f)) + 1);
-    const double qscale = exp2((double)(21 - eb));
+    const double qscale = exp2((double)(21 - eb)), iqscale = exp2((double)(eb - 21));
 
     // gather
 #pragma unroll 4
     for (int q = tid; q < k; q += NT) {
         const int g = a.T_idx[t0 + q];
         const double dx = (a.X[g] - ox) * sc, dy = (a.Y[g] - oy) * sc;
-        const double hx = rint(dx * qscale) / qscale, hy = rint(dy * qscale) / qscale;
+        const double hx = rint(dx * qscale) * iqscale, hy = rint(dy * qscale) * iqscale;
         S.xh[q] = (float)hx;
         S.xl[q] = (float)(dx - hx);
         S.yh[q] = (float)hy;
@@ -767,7 +1107,7 @@ __device__ void run_task(SmemM& sm, SmemKeep& keep, SmemSimt* simt, TcCtx* tc, c
     // coordinates from shared memory: the operand ring is idle before the factorisation)
     const float *cxh = S.xh, *cxl = S.xl, *cyh = S.yh, *cyl = S.yl;
     if constexpr (TC) {
-        if ((size_t)4 * ld * sizeof(float) <= (size_t)a.tc_stages * kTcStage) {
+        if ((size_t)4 * ld * sizeof(float) <= (size_t)tc_ring_bytes<Sch>(a.tc_stages)) {
             float* f = reinterpret_cast<float*>(tc->stages);
             for (int q = tid; q < k; q += NT) {
                 f[q] = S.xh[q];
@@ -796,7 +1136,10 @@ __device__ void run_task(SmemM& sm, SmemKeep& keep, SmemSimt* simt, TcCtx* tc, c
                 if (r != c) {
                     const float dx = (rxh - cxh[c]) + (rxl - cxl[c]);
                     const float dy = (ryh - cyh[c]) + (ryl - cyl[c]);
-                    v = expf(-sqrtf(fmaf(dx, dx, dy * dy)));
+                    // the FP32 matrix only preconditions the refinement, so the hardware
+                    // approximations of the root and the exponential serve (a few ulp)
+                    const float d2 = fmaf(dx, dx, dy * dy);
+                    v = __expf(-(d2 > 0.0f ? d2 * rsqrtf(d2) : 0.0f));
                 }
                 S.L[r + (int64_t)c * ld] = v;
             }
@@ -805,7 +1148,7 @@ __device__ void run_task(SmemM& sm, SmemKeep& keep, SmemSimt* simt, TcCtx* tc, c
 
     tm.lap(kPhGather);
     bool ok;
-    if constexpr (TC) ok = factor_tc(*tc, S, k, ld, a.phase_cycles);
+    if constexpr (TC) ok = factor_tc<Sch>(*tc, S, k, ld, a.phase_cycles);
     else ok = factor32(sm, *simt, S, k, ld);
     tm.t = a.phase_cycles ? now_cycles() : 0;
     if constexpr (!TC) tm.lap(kPhFactorSimt);
@@ -816,7 +1159,7 @@ __device__ void run_task(SmemM& sm, SmemKeep& keep, SmemSimt* simt, TcCtx* tc, c
     if constexpr (TC) {
         // as many of the vectors as fit, most used first: coordinates and solution
         // (residual and prediction), then the solve vector, then the accumulators
-        const size_t room = (size_t)a.tc_stages * kTcStage - sizeof(SmemM);
+        const size_t room = (size_t)tc_ring_bytes<Sch>(a.tc_stages) - sizeof(SmemM);
         const size_t vec = (size_t)ld * sizeof(float);
         if (ok && room >= 6 * vec) {
             float* f = reinterpret_cast<float*>(tc->stages + sizeof(SmemM));
@@ -848,8 +1191,13 @@ __device__ void run_task(SmemM& sm, SmemKeep& keep, SmemSimt* simt, TcCtx* tc, c
         for (int it = 0; it <= a.refine_max_iter; ++it) {
             for (int q = tid; q < k; q += NT) R.w[q] = (float)R.rr[q];
             __syncthreads();
-            forward32(sm, R.L, ld, R.w, k);
-            backward32(sm, R.L, ld, R.w, k);
+            if constexpr (TC) {
+                forward_inv(sm, R.L, ld, R.w, k);
+                backward_inv(sm, R.L, ld, R.w, k);
+            } else {
+                forward32(sm, R.L, ld, R.w, k);
+                backward32(sm, R.L, ld, R.w, k);
+            }
             tm.lap(kPhSolve);
             float dmax = 0.0f, xmax = 0.0f;
             for (int q = tid; q < k; q += NT) {
@@ -973,22 +1321,24 @@ __global__ void __launch_bounds__(NT, 2) k_cv_mixed(TaskArgs a) {
 constexpr int kSimtSmem = (int)(sizeof(SmemM) + sizeof(SmemKeep) + sizeof(SmemSimt));
 static_assert(sizeof(SmemM) % 16 == 0 && sizeof(SmemSimt) % 16 == 0 && alignof(SmemSimt) == 16,
               "SmemSimt must start on a 16-byte boundary after SmemM");
-// tensor-core kernel layout (offsets from the 1024-aligned base): operand ring, then
-// the persistent struct, then the pipeline barriers (8-byte aligned mbarriers)
 // tensor-core kernel layout (offsets from the 1024-aligned base) for a ring of
-// `nst` stages: operand ring, then the persistent struct, then the pipeline barriers
-__host__ __device__ constexpr int tc_keep_off(int nst) { return nst * kTcStage; }
-__host__ __device__ constexpr int tc_sh_off(int nst) { return (tc_keep_off(nst) + (int)sizeof(SmemKeep) + 127) / 128 * 128; }
-__host__ __device__ constexpr int tc_smem(int nst) { return 1024 + tc_sh_off(nst) + (int)sizeof(TcShared); }
-constexpr int kTcSmem = tc_smem(umma::kStages);
-static_assert(tc_keep_off(2) % 16 == 0 && tc_sh_off(2) % 128 == 0, "shared-memory layout alignment");
+// `ring` bytes: operand ring, then the persistent struct, then the pipeline barriers
+__host__ __device__ constexpr int tc_keep_off(int ring) { return ring; }
+__host__ __device__ constexpr int tc_sh_off(int ring) { return (tc_keep_off(ring) + (int)sizeof(SmemKeep) + 127) / 128 * 128; }
+__host__ __device__ constexpr int tc_smem(int ring) { return 1024 + tc_sh_off(ring) + (int)sizeof(TcShared); }
+constexpr int kTcRingMax = 144 * 1024;
+constexpr int kTcSmem = tc_smem(kTcRingMax);
+static_assert(kTcRingMin % 128 == 0 && tc_sh_off(kTcRingMin) % 128 == 0, "shared-memory layout alignment");
 static_assert(kTcSmem <= 227 * 1024, "tensor-core kernel exceeds the shared memory of one CTA");
-static_assert(sizeof(SmemM) <= (size_t)2 * kTcStage && sizeof(SmemM) % 16 == 0,
-              "phase scratch must fit in a 2-stage ring, vectors after it 16-byte aligned");
-static_assert(TB * DP * 4 + 2 * TB * 4 + 16 <= 2 * kTcStage, "diagonal block must fit in a 2-stage ring");
-static_assert(2 * tc_smem(2) <= 228 * 1024, "two tensor-core CTAs must fit on one SM");
+static_assert(sizeof(SmemM) <= (size_t)kTcRingMin && sizeof(SmemM) % 16 == 0,
+              "phase scratch must fit in the smallest ring, vectors after it 16-byte aligned");
+static_assert(kDiagBytes <= kTcRingMin && kDiagYOff % 16 == 0, "diagonal block must fit in the smallest ring");
+static_assert(2 * tc_smem(kTcRingMin) <= 228 * 1024, "two tensor-core CTAs must fit on one SM");
+static_assert(tc_ring_bytes<umma::SplitBF16x3>(2) == kTcRingMin && tc_ring_bytes<umma::SplitF16x2>(3) == kTcRingMin,
+              "default rings of both schemes");
 
-// Tensor-core variant: two CTAs per SM, 256 TMEM columns each.
+// Tensor-core variant: two CTAs per SM, 256 TMEM columns each; Sch is the operand scheme.
+template <class Sch>
 __global__ void __launch_bounds__(NT, 2) k_cv_mixed_tc(TaskArgs a, const __grid_constant__ CUtensorMap m0,
                                                        const __grid_constant__ CUtensorMap m1,
                                                        const __grid_constant__ CUtensorMap m2) {
@@ -998,16 +1348,17 @@ __global__ void __launch_bounds__(NT, 2) k_cv_mixed_tc(TaskArgs a, const __grid_
     tc.stages = base;
     SmemM& sm = *reinterpret_cast<SmemM*>(base);   // phase scratch shares the operand ring
     const int nst = a.tc_stages;
-    SmemKeep& keep = *reinterpret_cast<SmemKeep*>(base + tc_keep_off(nst));
-    tc.sh = reinterpret_cast<TcShared*>(base + tc_sh_off(nst));
+    const int ring = tc_ring_bytes<Sch>(nst);
+    SmemKeep& keep = *reinterpret_cast<SmemKeep*>(base + tc_keep_off(ring));
+    tc.sh = reinterpret_cast<TcShared*>(base + tc_sh_off(ring));
     tc.m0 = &m0;
     tc.m1 = &m1;
     tc.m2 = &m2;
     const int64_t slot_elems = (int64_t)a.ld * a.ld;
-    __nv_bfloat16* P = reinterpret_cast<__nv_bfloat16*>(a.planes);
-    tc.p0 = P + blockIdx.x * slot_elems;
-    tc.p1 = P + a.plane_elems + blockIdx.x * slot_elems;
-    tc.p2 = P + 2 * a.plane_elems + blockIdx.x * slot_elems;
+    uint16_t* P = reinterpret_cast<uint16_t*>(a.planes);
+#pragma unroll
+    for (int pl = 0; pl < 3; ++pl)
+        tc.p[pl] = pl < Sch::kPlanes ? P + pl * a.plane_elems + blockIdx.x * slot_elems : nullptr;
     tc.row_base = blockIdx.x * a.ld;
     const int warp = threadIdx.x >> 5;
     for (int e = threadIdx.x; e < 2 * dfm::kExpTable; e += NT) keep.tbl[e] = c_exp.tbl[e];
@@ -1016,7 +1367,7 @@ __global__ void __launch_bounds__(NT, 2) k_cv_mixed_tc(TaskArgs a, const __grid_
         tc.sh->dead = 0;
         umma::prefetch_map(&m0);
         umma::prefetch_map(&m1);
-        umma::prefetch_map(&m2);
+        if (Sch::kPlanes > 2) umma::prefetch_map(&m2);
     }
     if (warp == 1) umma::tmem_alloc(&tc.sh->pipe.tmem_base, kTcTmemCols);
     umma::tc_fence_before();
@@ -1029,7 +1380,7 @@ __global__ void __launch_bounds__(NT, 2) k_cv_mixed_tc(TaskArgs a, const __grid_
         const int t = keep.task;
         __syncthreads();
         if (t >= ntask) break;
-        run_task<true>(sm, keep, nullptr, &tc, a, t, a.order[t / a.B], t % a.B);
+        run_task<true, Sch>(sm, keep, nullptr, &tc, a, t, a.order[t / a.B], t % a.B);
     }
     umma::tc_fence_before();
     __syncthreads();
@@ -1056,17 +1407,33 @@ int mixed_prepare(int device) {
     if (e != cudaSuccess) return (int)e;
     e = cudaFuncSetAttribute(k_cv_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, kSimtSmem);
     if (e != cudaSuccess) return (int)e;
-    e = cudaFuncSetAttribute(k_cv_mixed_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+    e = cudaFuncSetAttribute(k_cv_mixed_tc<umma::SplitBF16x3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+    if (e != cudaSuccess) return (int)e;
+    e = cudaFuncSetAttribute(k_cv_mixed_tc<umma::SplitF16x2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
     if (e != cudaSuccess) return (int)e;
     g_prepared[device] = true;
     return 0;
 }
 
+int mixed_planes(int engine) {
+    return engine == kMixedEngineTensor ? umma::SplitF16x2::kPlanes
+           : engine == kMixedEngineTensorBF16 ? umma::SplitBF16x3::kPlanes : 0;
+}
+
+int mixed_default_stages(int engine) { return engine == kMixedEngineTensorBF16 ? 2 : 3; }
+
 int launch_task_mixed(const TaskArgs& a, const void* maps, int engine, int grid, void* stream) {
-    if (engine == kMixedEngineTensor) {
+    if (engine == kMixedEngineTensor || engine == kMixedEngineTensorBF16) {
         const CUtensorMap* m = reinterpret_cast<const CUtensorMap*>(maps);
-        if (a.tc_stages < 2 || a.tc_stages > umma::kStages) return (int)cudaErrorInvalidValue;
-        k_cv_mixed_tc<<<grid, NT, tc_smem(a.tc_stages), (cudaStream_t)stream>>>(a, m[0], m[1], m[2]);
+        const bool bf16 = engine == kMixedEngineTensorBF16;
+        const int ring = bf16 ? tc_ring_bytes<umma::SplitBF16x3>(a.tc_stages)
+                              : tc_ring_bytes<umma::SplitF16x2>(a.tc_stages);
+        if (a.tc_stages < 2 || a.tc_stages > umma::kStages || ring < kTcRingMin || ring > kTcRingMax)
+            return (int)cudaErrorInvalidValue;
+        if (bf16)
+            k_cv_mixed_tc<umma::SplitBF16x3><<<grid, NT, tc_smem(ring), (cudaStream_t)stream>>>(a, m[0], m[1], m[2]);
+        else
+            k_cv_mixed_tc<umma::SplitF16x2><<<grid, NT, tc_smem(ring), (cudaStream_t)stream>>>(a, m[0], m[1], m[2]);
     } else {
         k_cv_mixed<<<grid, NT, kSimtSmem, (cudaStream_t)stream>>>(a);
     }
@@ -1074,12 +1441,12 @@ int launch_task_mixed(const TaskArgs& a, const void* maps, int engine, int grid,
     return (int)cudaGetLastError();
 }
 
-bool mixed_make_maps(void* planes, int64_t plane_elems, int32_t ld, int grid, void* maps_out) {
+bool mixed_make_maps(void* planes, int64_t plane_elems, int32_t ld, int grid, int nplanes, void* maps_out) {
     CUtensorMap* m = reinterpret_cast<CUtensorMap*>(maps_out);
-    __nv_bfloat16* P = reinterpret_cast<__nv_bfloat16*>(planes);
+    uint16_t* P = reinterpret_cast<uint16_t*>(planes);
     const uint64_t tiles = (uint64_t)grid * (ld / umma::kTileM) * (ld / umma::kChunkK);
-    for (int p = 0; p < 3; ++p)
-        if (!umma::make_tiled_map(&m[p], P + p * plane_elems, tiles)) return false;
+    for (int p = 0; p < 3; ++p)   // maps past the scheme's planes repeat the last one (never used)
+        if (!umma::make_tiled_map(&m[p], P + std::min(p, nplanes - 1) * plane_elems, tiles)) return false;
     return true;
 }
 

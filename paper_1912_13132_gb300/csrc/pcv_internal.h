@@ -74,7 +74,7 @@ struct TaskArgs {
 };
 
 // Phases timed by the mixed kernel when phase_cycles is set.
-enum Phase { kPhGather = 0, kPhUpdate, kPhDiag, kPhPanel, kPhSplit, kPhFactorSimt, kPhSolve, kPhResidual,
+enum Phase { kPhGather = 0, kPhUpdate, kPhDiag, kPhPanel, kPhDiagIO, kPhFactorSimt, kPhSolve, kPhResidual,
              kPhPredict, kPhTask, kPhResidualPasses, kPhTasks, kPhFailFactor, kPhFailNaN, kPhFailStall,
              kPhaseCount = 16 };
 
@@ -84,8 +84,12 @@ int64_t slot_bytes_fp64(int32_t ld, int64_t mmax);
 // engine: 0 = tensor cores (split-BF16 tcgen05 trailing updates), 1 = FP32 SIMT.
 // maps: three CUtensorMap (128 bytes each) over the planes (engine 0 only).
 int launch_task_mixed(const TaskArgs& a, const void* maps, int engine, int grid, void* stream);
-bool mixed_make_maps(void* planes, int64_t plane_elems, int32_t ld, int grid, void* maps_out);
-constexpr int kMixedEngineTensor = 0, kMixedEngineSimt = 1;
+bool mixed_make_maps(void* planes, int64_t plane_elems, int32_t ld, int grid, int nplanes, void* maps_out);
+// mixed-path engines: tensor cores with two-term FP16 operands (default), FP32 SIMT,
+// tensor cores with three-term BF16 operands
+constexpr int kMixedEngineTensor = 0, kMixedEngineSimt = 1, kMixedEngineTensorBF16 = 2;
+int mixed_planes(int engine);           // 16-bit planes of the engine's operand scheme (0: none)
+int mixed_default_stages(int engine);   // default operand-ring depth of a tensor engine
 int64_t slot_bytes_mixed(int32_t ld, int64_t mmax);
 int mixed_prepare(int device);   // one-time per-device set-up of the mixed path
 

@@ -67,6 +67,9 @@ struct UmmaTestSmem {
     int err;
 };
 
+constexpr int kTestStages = 3;
+constexpr int kTestStageBytes = pcv::umma::stage_bytes<pcv::umma::SplitBF16x3>(pcv::umma::kTilesPerPass);
+
 __global__ void __launch_bounds__(256, 1) k_umma_test(const __grid_constant__ CUtensorMap m0,
                                                       const __grid_constant__ CUtensorMap m1,
                                                       const __grid_constant__ CUtensorMap m2, int M, int K, float* C,
@@ -75,10 +78,10 @@ __global__ void __launch_bounds__(256, 1) k_umma_test(const __grid_constant__ CU
     extern __shared__ __align__(1024) unsigned char raw[];
     uint8_t* base = (uint8_t*)(((uintptr_t)raw + 1023) & ~(uintptr_t)1023);
     uint8_t* stages = base;
-    UmmaTestSmem& sm = *reinterpret_cast<UmmaTestSmem*>(base + kStages * kStageBytes);
+    UmmaTestSmem& sm = *reinterpret_cast<UmmaTestSmem*>(base + kTestStages * kTestStageBytes);
     const int warp = threadIdx.x >> 5;
     if (threadIdx.x == 0) {
-        pipe_init(sm.pipe);
+        pipe_init(sm.pipe, kTestStages);
         sm.err = 0;
         prefetch_map(&m0);
         prefetch_map(&m1);
@@ -142,7 +145,7 @@ PCV_API pcv_status pcv_selftest_umma(const float* A, int32_t M, const float* B, 
         if (!ok) {
             st = PCV_ERR_CUDA;
         } else {
-            const int smem = kStages * kStageBytes + (int)sizeof(UmmaTestSmem) + 1024;
+            const int smem = kTestStages * kTestStageBytes + (int)sizeof(UmmaTestSmem) + 1024;
             cudaFuncSetAttribute(k_umma_test, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
             k_umma_test<<<1, 256, smem>>>(m[0], m[1], m[2], M, K, dC, dErr);
             pcv::count_launch(2);

@@ -1,14 +1,14 @@
 // umma.cuh -- Blackwell (sm_100a family) tensor-core building blocks in inline PTX:
-// TMEM allocation, tcgen05.mma (kind::f16, BF16 inputs, FP32 accumulators), TMA
-// tile loads, mbarriers with bounded waits, and the warp-specialised pipeline that
-// computes one block-column product
+// TMEM allocation, tcgen05.mma (kind::f16, FP32 accumulators), TMA tile loads,
+// mbarriers with bounded waits, and the warp-specialised pipeline that computes one
+// block-column product
 //
 //     D[rows r0 .. r0+nr, 0 .. 128) = sum over K of A[r, K] * B[c, K]      (K-major)
 //
-// with A and B given as three BF16 planes each (x = hi + mid + lo, each term the
-// BF16 rounding of what the previous terms leave, see split3), so that the six products
-// hi*hi + hi*mid + mid*hi + hi*lo + lo*hi + mid*mid reproduce FP32-accurate
-// products while running on the BF16 tensor pipe.
+// with A and B carried as planes of 16-bit terms whose sum is the FP32 value (an
+// operand scheme, see SplitBF16x3 and SplitF16x2 below); the scheme's cross products
+// of planes, accumulated in FP32, reproduce FP32-accurate products on the 16-bit
+// tensor pipe.
 //
 // Roles (256 threads):  warp 0 lane 0 issues TMA loads into a ring of Pipe::nstages
 // stages, warp 1 lane 0 issues the MMAs, warps 4..7 (one per TMEM lane quadrant)
@@ -20,6 +20,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -29,13 +30,33 @@ namespace umma {
 
 constexpr int kTileM = 128;        // rows per tile (MMA M)
 constexpr int kTileN = 128;        // block-column width (MMA N)
-constexpr int kChunkK = 32;        // BF16 elements per TMA box row (64 bytes, 64B swizzle)
-constexpr int kPlanes = 3;
+constexpr int kChunkK = 32;        // 16-bit elements per TMA box row (64 bytes, 64B swizzle)
 constexpr int kTilesPerPass = 2;   // default tiles per pass (template parameter TPP below)
-constexpr int kStages = 3;          // maximum ring depth (runtime depth in Pipe::nstages)
+constexpr int kStages = 4;         // maximum ring depth (runtime depth in Pipe::nstages)
 constexpr int kTileBytes = kTileM * kChunkK * 2;                    // 8 KB
-constexpr int kStageBytes = kPlanes * (kTilesPerPass + 1) * kTileBytes;   // 72 KB
-__host__ __device__ constexpr int stage_bytes(int tpp) { return kPlanes * (tpp + 1) * kTileBytes; }
+
+// Operand schemes.  SplitBF16x3: x = h + m + l, each term the round-to-nearest BF16
+// of what the previous ones leave (24 significant bits, representation error
+// <= 2^-24 |x|), six products h*h + h*m + m*h + h*l + l*h + m*m (the dropped ones are
+// below 2^-24 |a||b|).  SplitF16x2: x = h + l in FP16 (22 significant bits, error
+// <= 2^-22 |x| for |x| >= 2^-14, an absolute 2^-25 below that), three products
+// h*h + h*l + l*h (the dropped l*l is <= 2^-22 |a||b|): a third fewer bytes per
+// element and half the MMAs, for values of magnitude well below 65504.
+struct SplitBF16x3 {
+    static constexpr int kPlanes = 3, kProducts = 6;
+    static constexpr uint32_t kFmt = 1;   // instruction-descriptor code of BF16
+    __host__ __device__ static constexpr int a(int q) { return q == 2 ? 1 : q == 4 ? 2 : q == 5 ? 1 : 0; }
+    __host__ __device__ static constexpr int b(int q) { return q == 1 ? 1 : q == 3 ? 2 : q == 5 ? 1 : 0; }
+};
+struct SplitF16x2 {
+    static constexpr int kPlanes = 2, kProducts = 3;
+    static constexpr uint32_t kFmt = 0;   // instruction-descriptor code of FP16
+    __host__ __device__ static constexpr int a(int q) { return q == 2 ? 1 : 0; }
+    __host__ __device__ static constexpr int b(int q) { return q == 1 ? 1 : 0; }
+};
+
+template <class Sch = SplitBF16x3>
+__host__ __device__ constexpr int stage_bytes(int tpp) { return Sch::kPlanes * (tpp + 1) * kTileBytes; }
 constexpr uint32_t kTmemCols = 512;
 constexpr uint64_t kWaitNs = 2000000000ull;  // bound of every mbarrier wait (2 s)
 
@@ -138,12 +159,13 @@ __device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t addr) {
     return d;
 }
 
-// Instruction descriptor: kind::f16, A = B = BF16, D = FP32, both K-major, M x N.
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+// Instruction descriptor: kind::f16, A and B of format `fmt` (0 FP16, 1 BF16), D = FP32,
+// both K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_f16kind(int M, int N, uint32_t fmt) {
+    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+__device__ __forceinline__ void mma_f16kind(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
                                          uint32_t accumulate) {
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
@@ -172,7 +194,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// ---------------------------------------------------------------- BF16 splitting
+// ---------------------------------------------------------------- splitting
 
 // x = hi + mid + lo with each term the round-to-nearest BF16 of what is left; the
 // three terms carry 24 significant bits, the representation error is <= 2^-24 |x|.
@@ -182,6 +204,21 @@ __device__ __forceinline__ void split3(float x, __nv_bfloat16& h, __nv_bfloat16&
     m = __float2bfloat16_rn(r1);
     const float r2 = r1 - __bfloat162float(m);
     l = __float2bfloat16_rn(r2);
+}
+
+// The scheme's terms of x as 16-bit patterns, plane by plane.
+__device__ __forceinline__ void split_terms(SplitBF16x3, float x, uint16_t* t) {
+    __nv_bfloat16 h, m, l;
+    split3(x, h, m, l);
+    t[0] = __bfloat16_as_ushort(h);
+    t[1] = __bfloat16_as_ushort(m);
+    t[2] = __bfloat16_as_ushort(l);
+}
+__device__ __forceinline__ void split_terms(SplitF16x2, float x, uint16_t* t) {
+    const __half h = __float2half_rn(x);
+    const __half l = __float2half_rn(x - __half2float(h));
+    t[0] = __half_as_ushort(h);
+    t[1] = __half_as_ushort(l);
 }
 
 // ---------------------------------------------------------------- pipeline state
@@ -214,16 +251,13 @@ __device__ inline void pipe_init(Pipe& p, uint32_t nstages = kStages) {
     fence_mbar_init();
 }
 
-// The six plane products (A plane, B plane): hi*hi, hi*mid, mid*hi, hi*lo, lo*hi, mid*mid.
-__host__ __device__ constexpr int prod_a(int q) { return q == 2 ? 1 : q == 4 ? 2 : q == 5 ? 1 : 0; }
-__host__ __device__ constexpr int prod_b(int q) { return q == 1 ? 1 : q == 3 ? 2 : q == 5 ? 1 : 0; }
-
 // One block-column product over all row tiles:
-//   rows [r0, r0 + nrows) of A against rows [b0, b0 + 128) of B over K in [0, K),
-//   K a multiple of kChunkK.  A and B rows live in the planes' tensor maps at row
-//   offset `row_base` (the task's slot).  For each finished 128-row tile the
-//   epilogue warps call epi(tile_row0, warp_quadrant, taddr_of_tile) and must read
-//   all 128 columns of their 32 lanes.  Returns false if a bounded wait ran out.
+//   rows [r0, r0 + nrows) of A against rows [b0, b0 + 128) of B over the K columns
+//   [kc0 * kChunkK, kc0 * kChunkK + K), K a multiple of kChunkK.  A and B rows live
+//   in the planes' tensor maps at row offset `row_base` (the task's slot).  For each
+//   finished 128-row tile the epilogue warps call epi(tile_row0, warp_quadrant,
+//   taddr_of_tile) and must read all 128 columns of their 32 lanes.  Returns false
+//   if a bounded wait ran out.
 // Operand layouts in global memory.  Row-major: a plane is a row-major matrix and a
 // box is 128 rows x 32 columns of it.  Tiled: a plane is stored as contiguous 8 KB
 // tiles of 128 rows x 32 columns (tile (R, kc) at index R * nkc + kc), so that every
@@ -234,15 +268,15 @@ __device__ __forceinline__ void load_box(void* dst, const CUtensorMap* map, int 
     else tma_load_2d(dst, map, kc * kChunkK, row, bar);
 }
 
-template <bool TILED = false, int TPP = kTilesPerPass, class Epi>
+template <bool TILED = false, int TPP = kTilesPerPass, class Sch = SplitBF16x3, class Epi>
 __device__ bool block_column(Pipe& P, Phases& ph, uint8_t* stages, const CUtensorMap* mapA0,
                              const CUtensorMap* mapA1, const CUtensorMap* mapA2, int row_base, int r0,
-                             int nrows, int b0, int K, Epi&& epi, int nkc = 0) {
+                             int nrows, int b0, int K, Epi&& epi, int nkc = 0, int kc0 = 0) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int ntiles = (nrows + kTileM - 1) / kTileM;
     const int npass = (ntiles + TPP - 1) / TPP;
     const int nk = K / kChunkK;
-    const CUtensorMap* maps[3] = {mapA0, mapA1, mapA2};
+    const CUtensorMap* maps[3] = {mapA0, mapA1, mapA2};   // planes beyond the scheme's are unused
     bool ok = true;
     if (warp == 0 && lane == 0) {
         // TMA producer
@@ -254,12 +288,12 @@ __device__ bool block_column(Pipe& P, Phases& ph, uint8_t* stages, const CUtenso
                 const int s = it % P.nstages;
                 const uint32_t par = ((it / P.nstages) & 1) ^ 1;
                 if (!mbar_wait(&P.empty[s], par)) { ok = false; break; }
-                uint8_t* st = stages + s * stage_bytes(TPP);
-                mbar_expect_tx(&P.full[s], (uint32_t)(kPlanes * (nt + 1) * kTileBytes));
-                for (int pl = 0; pl < kPlanes; ++pl) {
-                    load_box<TILED>(st + pl * kTileBytes, maps[pl], kc, row_base + b0, nkc, &P.full[s]);
+                uint8_t* st = stages + s * stage_bytes<Sch>(TPP);
+                mbar_expect_tx(&P.full[s], (uint32_t)(Sch::kPlanes * (nt + 1) * kTileBytes));
+                for (int pl = 0; pl < Sch::kPlanes; ++pl) {
+                    load_box<TILED>(st + pl * kTileBytes, maps[pl], kc0 + kc, row_base + b0, nkc, &P.full[s]);
                     for (int t = 0; t < nt; ++t)
-                        load_box<TILED>(st + (kPlanes + t * kPlanes + pl) * kTileBytes, maps[pl], kc,
+                        load_box<TILED>(st + (Sch::kPlanes + t * Sch::kPlanes + pl) * kTileBytes, maps[pl], kc0 + kc,
                                         row_base + r0 + (t0 + t) * kTileM, nkc, &P.full[s]);
                 }
             }
@@ -267,7 +301,7 @@ __device__ bool block_column(Pipe& P, Phases& ph, uint8_t* stages, const CUtenso
     } else if (warp == 1 && lane == 0) {
         // MMA issuer
         uint32_t it = ph.stage;
-        const uint32_t idesc = idesc_bf16(kTileM, kTileN);
+        const uint32_t idesc = idesc_f16kind(kTileM, kTileN, Sch::kFmt);
         for (int p = 0; p < npass && ok; ++p) {
             const int t0 = p * TPP;
             const int nt = min(TPP, ntiles - t0);
@@ -279,17 +313,18 @@ __device__ bool block_column(Pipe& P, Phases& ph, uint8_t* stages, const CUtenso
                 const int s = it % P.nstages;
                 if (!mbar_wait(&P.full[s], (it / P.nstages) & 1)) { ok = false; break; }
                 tc_fence_after();
-                const uint32_t st = smem_u32(stages + s * stage_bytes(TPP));
+                const uint32_t st = smem_u32(stages + s * stage_bytes<Sch>(TPP));
                 for (int t = 0; t < nt; ++t) {
                     const uint32_t d = P.tmem_base + buf * (TPP * kTileN) + t * kTileN;
 #pragma unroll
                     for (int kk = 0; kk < kChunkK / 16; ++kk)
 #pragma unroll
-                        for (int q = 0; q < 6; ++q) {
-                            const uint32_t a = st + (kPlanes + t * kPlanes + prod_a(q)) * kTileBytes + kk * 32;
-                            const uint32_t b = st + prod_b(q) * kTileBytes + kk * 32;
-                            mma_bf16(d, smem_desc_sw64(a), smem_desc_sw64(b), idesc,
-                                     (kc > 0 || kk > 0 || q > 0) ? 1u : 0u);
+                        for (int q = 0; q < Sch::kProducts; ++q) {
+                            const uint32_t a =
+                                st + (Sch::kPlanes + t * Sch::kPlanes + Sch::a(q)) * kTileBytes + kk * 32;
+                            const uint32_t b = st + Sch::b(q) * kTileBytes + kk * 32;
+                            mma_f16kind(d, smem_desc_sw64(a), smem_desc_sw64(b), idesc,
+                                        (kc > 0 || kk > 0 || q > 0) ? 1u : 0u);
                         }
                 }
                 mma_commit(&P.empty[s]);

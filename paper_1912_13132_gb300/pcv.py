@@ -193,6 +193,10 @@ def _stream_ptr(stream) -> int | None:
     return int(getattr(stream, "cuda_stream", stream))
 
 
+# mixed-path factorisation engines (pcv_options.factor_engine)
+ENGINES = {"tensor": 0, "simt": 1, "tensor-bf16": 2}
+
+
 class Context:
     """A device-resident dataset with its subset layout (pcv_create ... pcv_destroy)."""
 
@@ -204,7 +208,7 @@ class Context:
         role = np.ascontiguousarray(role, dtype=np.uint8)
         L, keep = make_layout(layout)
         o = pcv_options(ctypes.sizeof(pcv_options), max_slots, workspace_fraction, refine_max_iter,
-                        refine_tol, {"tensor": 0, "simt": 1}[factor_engine], tc_stages)
+                        refine_tol, ENGINES[factor_engine], tc_stages)
         h = _vp()
         _check(_lib.pcv_create(_ptr(xy, _dp), _ptr(v, _dp), _ptr(role, _u8p), len(v), ctypes.byref(L),
                                device, ctypes.byref(o), ctypes.byref(h)), "pcv_create")
@@ -266,7 +270,7 @@ class Context:
         _check(_lib.pcv_kernel_time(self._h, ctypes.byref(t), ctypes.byref(c)), "pcv_kernel_time")
         return t.value, c.value
 
-    PHASES = ("gather_assemble", "tc_update", "diag", "panel_solve", "split", "factor_simt", "solves",
+    PHASES = ("gather_assemble", "tc_update", "diag", "panel_solve", "diag_io", "factor_simt", "solves",
               "residual", "predict_loss", "task", "residual_passes", "tasks", "fail_factor", "fail_nan",
               "fail_stall")
 

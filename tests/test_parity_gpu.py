@@ -162,11 +162,12 @@ def test_paper_scale_sampled(gpu_lib, paper5m, prec, B):
         print("paper-scale", prec, b, worst)
 
 
-@pytest.mark.parametrize("engine", ["tensor", "simt"])
+@pytest.mark.parametrize("engine", ["tensor", "simt", "tensor-bf16"])
 def test_mixed_engines(gpu_lib, engine):
-    """Both factorisation engines of the mixed path (split-BF16 tcgen05 trailing
-    updates, FP32 SIMT) meet the mixed tolerance on subsets spanning several
-    128-row tiles and a ragged tail (uniform 4096 workload, three configurations)."""
+    """Every factorisation engine of the mixed path (tcgen05 with two-term FP16 or
+    three-term BF16 operands, FP32 SIMT) meets the mixed tolerance on subsets spanning
+    several 128-row tiles and a ragged tail (uniform 4096 workload, three
+    configurations, one with a nugget ratio of 5e-4)."""
     w = datagen.config_uniform_4096()
     P = np.array([[1.0, 0.1, 0.05], [0.7, 0.03, 0.2], [2.0, 0.3, 0.001]])
     with gpu_lib.Context(w.xy, w.v, w.role, w.layout, factor_engine=engine) as ctx:
@@ -180,8 +181,8 @@ def test_mixed_engines(gpu_lib, engine):
 
 
 @pytest.mark.parametrize("rho,tau2", [(0.02, 0.001), (0.02, 0.1), (0.2, 0.001), (0.2, 0.01), (0.2, 0.1)])
-@pytest.mark.parametrize("prec", ["mixed", "fp64"])
-def test_grid_precision_stress(gpu_lib, prec, rho, tau2):
+@pytest.mark.parametrize("prec,engine", [("mixed", "tensor"), ("mixed", "tensor-bf16"), ("fp64", "tensor")])
+def test_grid_precision_stress(gpu_lib, prec, engine, rho, tau2):
     """Gridded 1024^2 training set (fine 2048^2 grid, 131 072 validation nodes), 32-cell
     cores with 8-cell shells (k = 1600 / 1920 / 2304): the conditioning sweep of the
     precision-stress workload (rho in {0.02, 0.2}, tau2 in {0.001, 0.01, 0.1}, the
@@ -191,12 +192,15 @@ def test_grid_precision_stress(gpu_lib, prec, rho, tau2):
     P = w.params
     nx = w.layout["nx"]
     pick = [0, nx // 2, nx * (nx // 2) + nx // 2]
-    with gpu_lib.Context(w.xy, w.v, w.role, w.layout) as ctx:
+    with gpu_lib.Context(w.xy, w.v, w.role, w.layout, factor_engine=engine) as ctx:
+        ctx.set_timing(True)
         out = ctx.cv_loss(P, precision=prec, per_subset=True, predictions=True)
+        ph = ctx.phase_cycles() if prec == "mixed" else {}
         V_off = ctx.V_off.copy()
     assert out["status"][0] in (0, 7), out["status"]       # 7: some tasks recomputed in FP64
     cores = oracle.layout_cores(w.layout)
     members = {i: oracle.subset_members(w.xy, w.role, w.layout, i, cores) for i in pick}
     ref = oracle.cv_loss(w.xy, w.v, w.role, w.layout, P, members=members, subsets=pick)
     worst = compare(out, ref, V_off, pick, 1, prec, check_total=False)
-    print("grid stress", prec, rho, tau2, out["status"].tolist(), worst)
+    counts = {k: ph.get(k) for k in ("tasks", "residual_passes", "fail_factor", "fail_nan", "fail_stall")}
+    print("grid stress", prec, engine, rho, tau2, out["status"].tolist(), worst, counts)
