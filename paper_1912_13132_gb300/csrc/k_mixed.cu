@@ -562,8 +562,11 @@ __device__ bool factor_tc(TcCtx& tc, const SlotM& S, int k, int64_t ld, unsigned
             }
             tm.lap(kPhDiagIO);
         }
-        // diagonal block in shared memory: whole 128 x 128 block, four rows per float4
-        // (rows beyond k hold stale values that are never used); 16 independent loads per thread
+        // diagonal block in shared memory: whole 128 x 128 block, four rows per float4,
+        // 16 independent loads per thread.  In the last, partial block everything past jb
+        // becomes identity as it is stored (one writer per element), so the factor and
+        // its inverse are block diagonal with an identity pad: rows and columns past k
+        // never mix in.
         {
             float4 v[TB * TB / 4 / NT];
 #pragma unroll
@@ -574,18 +577,12 @@ __device__ bool factor_tc(TcCtx& tc, const SlotM& S, int k, int64_t ld, unsigned
 #pragma unroll
             for (int i = 0; i < TB * TB / 4 / NT; ++i) {
                 const int e = tid + i * NT, r4 = (e & (TB / 4 - 1)) * 4, c = e / (TB / 4);
-                D[r4][c] = v[i].x;
-                D[r4 + 1][c] = v[i].y;
-                D[r4 + 2][c] = v[i].z;
-                D[r4 + 3][c] = v[i].w;
-            }
-        }
-        if (jb < TB) {
-            // last, partial block: identity beyond jb, so the factor and its inverse are
-            // block diagonal with an identity pad (rows and columns past k never mix in)
-            for (int e = tid; e < TB * TB; e += NT) {
-                const int r = e / TB, c = e % TB;
-                if (r >= jb || c >= jb) D[r][c] = r == c ? 1.0f : 0.0f;
+                const float x[4] = {v[i].x, v[i].y, v[i].z, v[i].w};
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int r = r4 + u;
+                    D[r][c] = (r < jb && c < jb) ? x[u] : (r == c ? 1.0f : 0.0f);
+                }
             }
         }
         if (tid == 0) *flag = 0;

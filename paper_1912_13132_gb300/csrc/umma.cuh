@@ -132,12 +132,14 @@ __device__ __forceinline__ void fence_proxy_async() {
 // ---------------------------------------------------------------- TMEM and MMA
 
 __device__ __forceinline__ void tmem_alloc(uint32_t* dst_smem, uint32_t ncols) {
+    __syncwarp();   // .sync.aligned: the whole warp, converged
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst_smem)),
                  "r"(ncols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
 }
 __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    __syncwarp();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
 }
 __device__ __forceinline__ void tc_fence_before() {
@@ -178,9 +180,12 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                  : "memory");
 }
 
-// 32 lanes x 32 columns of FP32 from TMEM (one register per column).
+// 32 lanes x 32 columns of FP32 from TMEM (one register per column).  The load is a
+// .sync.aligned instruction: the whole warp must execute it converged, so the warp is
+// reconverged first (callers may have branched per lane since the last one).
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
     uint32_t r[32];
+    __syncwarp();
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
         "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
@@ -339,7 +344,10 @@ __device__ bool block_column(Pipe& P, Phases& ph, uint8_t* stages, const CUtenso
             const int nt = min(TPP, ntiles - t0);
             const uint32_t pp = ph.pass + p;
             const int buf = pp & 1;
-            if (!mbar_wait(&P.accf[buf], (pp >> 1) & 1)) { ok = false; break; }
+            // every lane polls the barrier on its own; agree on the outcome (which also
+            // reconverges the warp before the aligned TMEM loads of the epilogue)
+            const bool got = mbar_wait(&P.accf[buf], (pp >> 1) & 1);
+            if (!__all_sync(0xffffffffu, got)) { ok = false; break; }
             tc_fence_after();
             for (int t = 0; t < nt; ++t) {
                 const uint32_t taddr = P.tmem_base + ((uint32_t)(quad * 32) << 16) +
