@@ -166,14 +166,41 @@ def algorithmic_flops(k, m, B):
     return float(B * np.sum(k ** 3 / 3.0 + 2.0 * k ** 2 + 2.0 * m * k))
 
 
-def cpu_baseline(w, params, budget_s: float, active, seed: int = 0):
+def aggregate_rate(local_s: float, units_per_rank: float, world: int, dist=None, device=None):
+    """Whole-job throughput of `world` replicas, each of which processed
+    `units_per_rank` units in `local_s` seconds: the elapsed times are reduced by MAX
+    over the ranks (the job ends with its slowest rank), value = world * units / max.
+    Returns (value, max seconds)."""
+    t = float(local_s)
+    if dist is not None and world > 1:
+        import torch
+        x = torch.tensor([t], dtype=torch.float64, device=device)
+        dist.all_reduce(x, op=dist.ReduceOp.MAX)
+        t = float(x.item())
+    return world * units_per_rank / t, t
+
+
+def cpu_model() -> str:
+    """The host CPU's model name (or its architecture when none is published)."""
+    import platform
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith(("model name", "hardware")):
+                return ln.split(":", 1)[1].strip()
+    except OSError:  # pragma: no cover
+        pass
+    return platform.processor() or platform.machine()
+
+
+def cpu_baseline(w, params, budget_s: float, active, seed: int = 0, threads: int | None = None):
     """FP64 oracle on a bounded random sample of the subsets with validation data,
-    one configuration, a thread per host core.  Returns the wall time and the count
-    done; a full configuration takes about elapsed * len(active) / n_done."""
+    one configuration, `threads` threads (default: one per host core).  Returns the
+    wall time and the count done; a full configuration takes about
+    elapsed * len(active) / n_done."""
     import oracle
     from concurrent.futures import ThreadPoolExecutor
 
-    cores = os.cpu_count() or 1
+    cores = threads or os.cpu_count() or 1
     allc = oracle.layout_cores(w.layout)
     order = np.random.default_rng(seed).permutation(np.asarray(active))
     s2, rho, tau = params
@@ -417,8 +444,10 @@ def run_reference(args, rank: int, world: int):
               f"(~{args.ref_budget:.0f} s on {cb['cores']} threads), extrapolated by subset count")
     line = dict(metric=METRIC, value=v, unit=UNIT, impl="reference", n_gpus=world, steps=args.steps,
                 warmup=args.warmup, higher_is_better=True, dtype="f64", data="synthetic",
-                config=dict(workload=w.name, batch=1),
-                cpu_baseline=dict(value=v, unit=UNIT, cores=cb["cores"], kind="oracle", sample=sample),
+                config=dict(workload=w.name, n_obs=int(len(w.v)), batch=1, precision="fp64",
+                            parallelism="host threads"),
+                cpu_baseline=dict(value=v, unit=UNIT, cores=cb["cores"], kind="oracle", cpu=cpu_model(),
+                                  sample=sample),
                 e2e=dict(value=v, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0),
                 vs_baseline=None)
     print(json.dumps(line), flush=True)
@@ -435,6 +464,7 @@ def main():
     ap.add_argument("--batch", type=int, default=8)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--cpu-budget-1core", type=float, default=6.0)
     ap.add_argument("--ref-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--max-slots", type=int, default=0, help="limit concurrent tasks (profiling runs)")
@@ -531,12 +561,7 @@ def main():
     barrier()
     clk = clocks.stop()
     phases = ctx.phase_cycles() if args.precision == "mixed" else None
-    total_s = sum(step_ms) / 1e3
-    if dist is not None:
-        t = torch.tensor([total_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
-    value = world * B * args.steps / total_s
+    value, total_s = aggregate_rate(sum(step_ms) / 1e3, B * args.steps, world, dist, "cuda")
 
     # end to end through the host-pointer call (params up, results down, per step)
     e2e_s = []
@@ -548,12 +573,9 @@ def main():
         t0 = time.perf_counter()
         out = ctx.cv_loss(host_P[s], precision=args.precision, stream=stream)
         e2e_s.append(time.perf_counter() - t0)
-    e2e_total = sum(e2e_s) if e2e_s else 1.0
-    if dist is not None:
-        t = torch.tensor([e2e_total], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
-    e2e_value = world * B * args.e2e_steps / e2e_total if args.e2e_steps > 0 else None
+    e2e_value, _ = aggregate_rate(sum(e2e_s) if e2e_s else 1.0, B * args.e2e_steps, world, dist, "cuda")
+    if args.e2e_steps <= 0:
+        e2e_value = None
 
     peaks, peak_src = load_peaks()
     flops = algorithmic_flops(k, m, B)
@@ -605,10 +627,15 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu:
         active = np.nonzero(np.diff(ctx.V_off) > 0)[0]
         cb = cpu_baseline(w, P[0], args.cpu_budget, active)
+        c1 = cpu_baseline(w, P[0], args.cpu_budget_1core, active, seed=1, threads=1)
         line["cpu_baseline"] = dict(value=cb["value"], unit=UNIT, cores=cb["cores"], kind="oracle",
+                                    cpu=cpu_model(),
                                     sample=f"{cb['n_done']} of {cb['n_total']} subsets with validation data, one "
                                            f"configuration ({cb['elapsed']:.1f} s), extrapolated by subset count "
-                                           f"to {cb['t_full']:.0f} s per configuration")
+                                           f"to {cb['t_full']:.0f} s per configuration",
+                                    one_core=dict(value=c1["value"], unit=UNIT,
+                                                  sample=f"{c1['n_done']} subsets ({c1['elapsed']:.1f} s), "
+                                                         f"extrapolated to {c1['t_full']:.0f} s per configuration"))
     ctx.close()
     if rank == 0 and world == 1 and args.serve_seconds > 0:
         line["serving"] = run_serving(pcv, local, args.serve_seconds, args.hbm_budget_gb, args.serve_batch,
