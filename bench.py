@@ -8,7 +8,7 @@ split, 40 x 40 cores, shell 0.001, about 1600 subsets of 2250-2630 training
 points), seeded and synthetic.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64]
-                    [--workload paper5m|cluster262k|uniform4096|serving] [--batch B]
+                    [--workload paper5m|paper5m-recursive|cluster262k|uniform4096|serving] [--batch B]
                     [--impl ours|reference] [--serve-seconds S] [--hbm-budget-gb G]
 
 Prints one JSON line (rank 0).  `value` is device-timed (CUDA events around each
@@ -64,6 +64,9 @@ def make_workload(name: str):
     if name == "paper-small":
         # same subset sizes as paper5m (56-node cores, shell 0.001 scaled), 100 subsets: profiling case
         return datagen.config_paper_5m(side=560, nx=10, delta=0.001 * 2236 / 560)
+    if name == "paper5m-recursive":
+        # the paper's weak-scaling layout (Sec. 4.3.2): 512 recursive sub-domains, shells capped at 2000
+        return datagen.config_paper_5m_recursive()
     if name == "cluster262k":
         return datagen.config_cluster_262k()
     if name == "uniform4096":
@@ -201,7 +204,7 @@ def cpu_baseline(w, params, budget_s: float, active, seed: int = 0, threads: int
     from concurrent.futures import ThreadPoolExecutor
 
     cores = threads or os.cpu_count() or 1
-    allc = oracle.layout_cores(w.layout)
+    allc = oracle.layout_cores(w.layout, w.xy)
     order = np.random.default_rng(seed).permutation(np.asarray(active))
     s2, rho, tau = params
 
@@ -431,7 +434,7 @@ def run_reference(args, rank: int, world: int):
     import oracle
 
     w = make_workload(args.workload)
-    core = oracle.core_of(w.layout, w.xy[w.role == datagen.VALID])
+    core = oracle.core_of(w.layout, w.xy[w.role == datagen.VALID], w.xy)
     active = np.unique(core)
     vals = []
     for s in range(args.warmup + args.steps):

@@ -75,15 +75,35 @@ enum { PCV_ROLE_TRAIN = 0, PCV_ROLE_VALID = 1, PCV_ROLE_IGNORE = 2 };
  *                   tolerance (1e-6 relative on losses, 1e-5 on predictions). */
 enum { PCV_PREC_FP64 = 0, PCV_PREC_MIXED = 1 };
 
-enum { PCV_LAYOUT_RECTS = 0, PCV_LAYOUT_GRID = 1 };
+enum { PCV_LAYOUT_RECTS = 0, PCV_LAYOUT_GRID = 1, PCV_LAYOUT_RECURSIVE = 2 };
 
 typedef struct { double x0, x1, y0, y1; } pcv_rect;
 
 /* Subset layout (Sec. 2.3).
  *   kind = PCV_LAYOUT_GRID:  regular nx x ny cores over the domain.
  *   kind = PCV_LAYOUT_RECTS: n_cores explicit cores (caller's array, copied).
+ *   kind = PCV_LAYOUT_RECURSIVE: 2^q cores by the recursive division of Sec. 2.4
+ *       (0 <= q <= 20): a rectangle is cut in two so that both halves, each together
+ *       with its shell, hold similar amounts of data; the cuts alternate, the first
+ *       at depth 0 across x (a line parallel to the y-axis), then across y, and so on.
+ *       "Amount of data" counts every point, whatever its role, in the child's closed
+ *       window of width delta, the shell taken in all of D (with delta = 0 the paper's
+ *       512 subsets of its Sec. 4.3.2 hold 9765 or 9766 residuals each: all data, not
+ *       only training data, are balanced).  Candidate cuts are the midpoints of
+ *       consecutive distinct coordinates of the points inside the parent; the one with
+ *       the smallest |count(left) - count(right)| wins, ties going to the smaller
+ *       coordinate; a parent with fewer than two distinct coordinates is cut at its
+ *       middle.  Cores are numbered depth first, left (lower) child first.
  *   has_domain = 0: the domain is the bounding box of all n points.
- *   delta >= 0: shell width. */
+ *   delta >= 0: shell width.
+ *   shell_cap > 0 (any kind): a subset whose shell holds more than shell_cap TRAIN
+ *       points keeps shell_cap of them, drawn at random without replacement
+ *       (Sec. 4.3.2 caps shells at 2000); the core's points are always kept.  The
+ *       draw is reproducible: every shell point j of subset i gets as key output
+ *       number w + 1 of the SplitMix64 generator (Steele, Lea and Flood, 2014) seeded
+ *       with cap_seed, w = (i << 40) | j, i.e. mix(cap_seed + (w + 1) * 0x9E3779B97F4A7C15)
+ *       with the generator's published output mix, arithmetic modulo 2^64; the
+ *       shell_cap smallest keys (ties: smaller j) are kept, in ascending index order. */
 typedef struct {
     int32_t kind;
     int32_t nx, ny;
@@ -92,6 +112,9 @@ typedef struct {
     int32_t has_domain;
     pcv_rect domain;
     double delta;
+    int32_t q;           /* PCV_LAYOUT_RECURSIVE: levels, 2^q cores */
+    int32_t shell_cap;   /* 0 = no cap */
+    uint64_t cap_seed;
 } pcv_layout;
 
 /* Tuning knobs; pass NULL for defaults.  Zero fields take defaults. */

@@ -13,6 +13,12 @@ Pieces and the passages they follow:
   here (see ``grid_cores``): cores are half-open and closed on D's upper edges,
   the shell is the L-infinity band of width delta, only TRAIN points enter
   the training set.
+* ``recursive_cores``: the recursive division of D into 2^q rectangles of
+  Sec. 2.4 (each cut balances the data of both halves, each with its shell;
+  the cut axis alternates, x first) -- readings in its docstring.
+* ``shell_keys`` / the shell cap in ``subset_members``: shells holding more than
+  a cap of training points keep a random sample of that size (Sec. 4.3.2),
+  drawn with the SplitMix64 generator's published definition.
 * ``krige`` / ``krige_literal``: simple kriging, Eq. 3 (C routine).
 * ``sspe``: Eq. 4 (C routine).
 * ``cv_loss``: Eq. 6, sum over subsets of the local SSPE (Algorithm 1's
@@ -145,6 +151,28 @@ def krige(sT, yT, sP, rho: float, lam: float) -> tuple[np.ndarray, int]:
     return out, st
 
 
+def krige_lapack(sT, yT, sP, rho: float, lam: float) -> tuple[np.ndarray, int]:
+    """Eq. 3, second line, with library routines for the two large steps: LAPACK's
+    Cholesky factorisation and triangular solves (scipy.linalg), the covariances
+    written out with numpy.  For subsets too large for the plain C routine (k of
+    several thousand); pinned against it in tests/test_oracle_pins.py."""
+    import scipy.linalg as sla
+    sT, yT, sP = _f64(sT).reshape(-1, 2), _f64(yT), _f64(sP).reshape(-1, 2)
+    if len(sT) == 0:
+        return np.zeros(len(sP)), OK
+    dT = np.sqrt((sT[:, None, 0] - sT[None, :, 0]) ** 2 + (sT[:, None, 1] - sT[None, :, 1]) ** 2)
+    A = np.exp(-dT / rho)
+    A[np.diag_indices_from(A)] += lam
+    try:
+        L = np.linalg.cholesky(A)
+    except np.linalg.LinAlgError:
+        return np.full(len(sP), np.nan), NOT_SPD
+    w = sla.solve_triangular(L, yT, lower=True)
+    alpha = sla.solve_triangular(L.T, w, lower=False)
+    dP = np.sqrt((sP[:, None, 0] - sT[None, :, 0]) ** 2 + (sP[:, None, 1] - sT[None, :, 1]) ** 2)
+    return np.exp(-dP / rho) @ alpha, OK
+
+
 def krige_literal(sT, yT, sP, sigma2: float, rho: float, tau: float) -> tuple[np.ndarray, int]:
     """Eq. 3, first line: sigma2 Sigma_p^T (sigma2 Sigma + tau I)^{-1} yT."""
     sT, yT, sP = _f64(sT).reshape(-1, 2), _f64(yT), _f64(sP).reshape(-1, 2)
@@ -196,13 +224,99 @@ def grid_cores(layout: dict) -> list[tuple[float, float, bool, float, float, boo
     return out
 
 
-def layout_cores(layout: dict) -> list[tuple[float, float, bool, float, float, bool]]:
+def domain_of(layout: dict, xy=None) -> tuple[float, float, float, float]:
+    """D: the layout's domain, else the bounding box of all points."""
+    if layout.get("domain") is not None:
+        return tuple(float(t) for t in layout["domain"])
+    xy = _f64(xy)
+    return (float(xy[:, 0].min()), float(xy[:, 0].max()), float(xy[:, 1].min()), float(xy[:, 1].max()))
+
+
+def recursive_cores(xy, layout: dict) -> list[tuple[float, float, float, float]]:
+    """The recursive division of D into 2^q sub-domains (Sec. 2.4).
+
+    A rectangle is cut in two so that both halves, each together with its shell,
+    contain a similar amount of data; the cuts alternate between the two axes.
+    Readings where the section leaves details open:
+      * the first cut (depth 0) is a value of x (a line parallel to the y-axis),
+        then y, then x, ...;
+      * "amount of data" counts every point, whatever its role, in the child's
+        closed window [x0 - delta, x1 + delta] x [y0 - delta, y1 + delta] (the
+        shell reaches wherever it reaches; the 512 shell-free subsets of Sec. 4.3.2
+        hold 9765 or 9766 residuals each, so all data are balanced);
+      * candidate cuts are the midpoints of consecutive distinct coordinates of the
+        points inside the parent (half-open, closed on D's upper edges); the cut
+        with the smallest |count(left) - count(right)| wins, ties going to the
+        smaller cut; with fewer than two distinct coordinates the parent is cut in
+        the middle;
+      * the sub-domains are numbered depth first, the left (lower) half first.
+    Returns [(x0, x1, y0, y1)] in that order.
+    """
+    xy = _f64(xy)
+    X0, X1, Y0, Y1 = domain_of(layout, xy)
+    d = float(layout["delta"])
+    q = int(layout["q"])
+    x, y = xy[:, 0], xy[:, 1]
+    out = []
+
+    def in_window(idx, r):
+        px, py = x[idx], y[idx]
+        return idx[(px >= r[0] - d) & (px <= r[1] + d) & (py >= r[2] - d) & (py <= r[3] + d)]
+
+    def in_rect(idx, r):
+        px, py = x[idx], y[idx]
+        okx = (px >= r[0]) & ((px <= r[1]) if r[1] == X1 else (px < r[1]))
+        oky = (py >= r[2]) & ((py <= r[3]) if r[3] == Y1 else (py < r[3]))
+        return idx[okx & oky]
+
+    def divide(r, depth, win):
+        if depth == q:
+            out.append(r)
+            return
+        coord = x if depth % 2 == 0 else y
+        lo, hi = (r[0], r[1]) if depth % 2 == 0 else (r[2], r[3])
+        u = np.unique(coord[in_rect(win, r)])
+        cut = (lo + hi) / 2.0
+        if len(u) >= 2:
+            a = np.sort(coord[win])                      # every point in the parent's window
+            cand = (u[:-1] + u[1:]) / 2.0
+            left = np.searchsorted(a, cand + d, side="right")       # left child's window
+            right = len(a) - np.searchsorted(a, cand - d, side="left")  # right child's window
+            cut = float(cand[int(np.argmin(np.abs(left - right)))])    # first minimum = smaller cut
+        if depth % 2 == 0:
+            halves = ((r[0], cut, r[2], r[3]), (cut, r[1], r[2], r[3]))
+        else:
+            halves = ((r[0], r[1], r[2], cut), (r[0], r[1], cut, r[3]))
+        for h in halves:
+            divide(h, depth + 1, in_window(win, h))
+
+    root = (X0, X1, Y0, Y1)
+    divide(root, 0, in_window(np.arange(len(xy)), root))
+    return out
+
+
+def layout_cores(layout: dict, xy=None) -> list[tuple[float, float, bool, float, float, bool]]:
+    """Cores as (x0, x1, x1_closed, y0, y1, y1_closed); recursive layouts need the points."""
     if layout["kind"] == "grid":
         return grid_cores(layout)
-    if layout["kind"] == "rects":
-        X0, X1, Y0, Y1 = layout["domain"]
-        return [(r[0], r[1], r[1] == X1, r[2], r[3], r[3] == Y1) for r in layout["cores"]]
+    if layout["kind"] in ("rects", "recursive"):
+        X0, X1, Y0, Y1 = domain_of(layout, xy)
+        rects = layout["cores"] if layout["kind"] == "rects" else recursive_cores(xy, layout)
+        return [(r[0], r[1], r[1] == X1, r[2], r[3], r[3] == Y1) for r in rects]
     raise ValueError(f"unknown layout kind {layout['kind']}")
+
+
+_M64 = (1 << 64) - 1
+
+
+def shell_key(seed: int, i: int, j: int) -> int:
+    """Key of shell point j of subset i: output number w + 1, w = (i << 40) | j, of the
+    SplitMix64 generator seeded with `seed` (Steele, Lea and Flood, OOPSLA 2014):
+    the generator adds its golden-ratio increment per output and mixes the sum."""
+    z = (seed + (((i << 40) | j) + 1) * 0x9E3779B97F4A7C15) & _M64
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _M64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _M64
+    return z ^ (z >> 31)
 
 
 def subset_members(xy: np.ndarray, role: np.ndarray, layout: dict, i: int,
@@ -218,7 +332,7 @@ def subset_members(xy: np.ndarray, role: np.ndarray, layout: dict, i: int,
     role = np.ascontiguousarray(role, dtype=np.uint8)
     rp = role.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
     if cores is None:
-        cores = layout_cores(layout)
+        cores = layout_cores(layout, xy)
     x0, x1, xc, y0, y1, yc = cores[i]
     d = float(layout["delta"])
     n = len(role)
@@ -231,11 +345,24 @@ def subset_members(xy: np.ndarray, role: np.ndarray, layout: dict, i: int,
         L.oracle_select(_dp(xy), rp, n, want, rect[0], rect[1], int(rect[2]), rect[3], rect[4],
                         int(rect[5]), idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)))
         out.append(idx)
+    cap = int(layout.get("shell_cap", 0) or 0)
+    if cap > 0:
+        # Sec. 4.3.2: a shell with more than `cap` training points keeps a random
+        # sample of `cap` of them (without replacement); the core keeps all of its own
+        T = out[0]
+        px, py = xy[T, 0], xy[T, 1]
+        in_core = ((px >= x0) & ((px <= x1) if xc else (px < x1)) &
+                   (py >= y0) & ((py <= y1) if yc else (py < y1)))
+        shell = T[~in_core]
+        if len(shell) > cap:
+            seed = int(layout.get("cap_seed", 0)) & _M64
+            ranked = sorted(shell.tolist(), key=lambda j: (shell_key(seed, i, j), j))
+            out[0] = np.sort(np.concatenate([T[in_core], np.array(ranked[:cap], dtype=np.int64)]))
     return out[0], out[1]
 
 
 def all_members(xy, role, layout, threads: int | None = None):
-    cores = layout_cores(layout)
+    cores = layout_cores(layout, xy)
     with ThreadPoolExecutor(threads or os.cpu_count()) as ex:
         return list(ex.map(lambda i: subset_members(xy, role, layout, i, cores), range(len(cores))))
 
@@ -243,21 +370,23 @@ def all_members(xy, role, layout, threads: int | None = None):
 # ----------------------------------------------------------------------------
 # the method: local SSPE per subset and their sum (Eq. 6, Algorithm 1)
 # ----------------------------------------------------------------------------
-def subset_cv(xy, v, T: np.ndarray, V: np.ndarray, sigma2: float, rho: float, tau: float):
+def subset_cv(xy, v, T: np.ndarray, V: np.ndarray, sigma2: float, rho: float, tau: float,
+              lapack: bool = False):
     """Local SSPE z_i = CV(y~_T^i, y_V^i, zeta) with zeta = (tau / sigma2, rho).
 
     Returns (z, yhat_V, status).  A subset with no validation data returns z = 0
-    and is ignored (Sec. 4.3.1).
+    and is ignored (Sec. 4.3.1).  `lapack` selects krige_lapack for large subsets.
     """
     if len(V) == 0:
         return 0.0, np.empty(0), OK
-    yhat, st = krige(xy[T], v[T], xy[V], rho, tau / sigma2)
+    yhat, st = (krige_lapack if lapack else krige)(xy[T], v[T], xy[V], rho, tau / sigma2)
     if st != OK:
         return float("nan"), yhat, st
     return sspe(yhat, v[V]), yhat, st
 
 
-def cv_loss(xy, v, role, layout, params, members=None, subsets=None, threads: int | None = None):
+def cv_loss(xy, v, role, layout, params, members=None, subsets=None, threads: int | None = None,
+            lapack: bool = False):
     """Parallel-CV loss for each parameter row (sigma2, rho, tau).
 
     Returns dict with 'sspe' (B,), 'z' (B, N) local SSPEs (NaN where not evaluated),
@@ -266,7 +395,7 @@ def cv_loss(xy, v, role, layout, params, members=None, subsets=None, threads: in
     """
     xy, v = _f64(xy), _f64(v)
     params = np.atleast_2d(_f64(params))
-    cores = layout_cores(layout)
+    cores = layout_cores(layout, xy)
     N = len(cores)
     if members is None:
         members = all_members(xy, role, layout, threads)
@@ -281,7 +410,7 @@ def cv_loss(xy, v, role, layout, params, members=None, subsets=None, threads: in
         b, i = job
         T, V = members[i]
         s2, rho, tau = params[b]
-        return job, subset_cv(xy, v, T, V, s2, rho, tau)
+        return job, subset_cv(xy, v, T, V, s2, rho, tau, lapack)
 
     with ThreadPoolExecutor(threads or os.cpu_count()) as ex:
         for (b, i), (zi, yh, st) in ex.map(run, jobs):
@@ -298,11 +427,28 @@ def cv_loss(xy, v, role, layout, params, members=None, subsets=None, threads: in
     return dict(sspe=total, z=z, status=status, yhat=yhat, n_valid=n_valid, members=members)
 
 
-def core_of(layout: dict, pts: np.ndarray) -> np.ndarray:
+def core_of(layout: dict, pts: np.ndarray, xy=None) -> np.ndarray:
     """Index of the core containing each point of pts (m, 2), after clamping the point
-    into D (points outside D go to the nearest core)."""
+    into D (points outside D go to the nearest core).  Layouts other than the
+    regular grid take the first core that contains the clamped point, else the
+    nearest one (recursive layouts need the data points `xy`)."""
     if layout["kind"] != "grid":
-        raise NotImplementedError("core lookup implemented for regular layouts")
+        pts = _f64(pts).reshape(-1, 2)
+        X0, X1, Y0, Y1 = domain_of(layout, xy)
+        cores = layout_cores(layout, xy)
+        out = np.empty(len(pts), dtype=np.int64)
+        for j, (px, py) in enumerate(pts):
+            px, py = min(max(px, X0), X1), min(max(py, Y0), Y1)
+            best, bestd = -1, np.inf
+            for i, (x0, x1, xc, y0, y1, yc) in enumerate(cores):
+                if px >= x0 and (px <= x1 if xc else px < x1) and py >= y0 and (py <= y1 if yc else py < y1):
+                    best = i
+                    break
+                dx, dy = max(x0 - px, 0.0, px - x1), max(y0 - py, 0.0, py - y1)
+                if dx * dx + dy * dy < bestd:
+                    best, bestd = i, dx * dx + dy * dy
+            out[j] = best
+        return out
     X0, X1, Y0, Y1 = layout["domain"]
     nx, ny = layout["nx"], layout["ny"]
     bx, by = np.array(grid_bounds(X0, X1, nx)), np.array(grid_bounds(Y0, Y1, ny))
@@ -318,8 +464,8 @@ def predict(xy, v, role, layout, param, pts, members=None):
     subset (core plus shell) whose core contains it, with the given (sigma2, rho, tau)."""
     xy, v, pts = _f64(xy), _f64(v), _f64(pts).reshape(-1, 2)
     s2, rho, tau = [float(t) for t in param]
-    core = core_of(layout, pts)
-    cores = layout_cores(layout)
+    core = core_of(layout, pts, xy)
+    cores = layout_cores(layout, xy)
     out = np.empty(len(pts))
     for i in np.unique(core):
         sel = np.nonzero(core == i)[0]

@@ -17,7 +17,7 @@ from . import build_ext
 PCV_OK, PCV_ERR_ARG, PCV_ERR_OOM, PCV_ERR_CUDA, PCV_ERR_TIMEOUT = 0, 1, 2, 3, 4
 PCV_ERR_BUSY, PCV_NOT_SPD, PCV_REFINE_FALLBACK, PCV_ERR_UNSUPPORTED = 5, 6, 7, 8
 PCV_PREC_FP64, PCV_PREC_MIXED = 0, 1
-PCV_LAYOUT_RECTS, PCV_LAYOUT_GRID = 0, 1
+PCV_LAYOUT_RECTS, PCV_LAYOUT_GRID, PCV_LAYOUT_RECURSIVE = 0, 1, 2
 PRECISIONS = {"fp64": PCV_PREC_FP64, "mixed": PCV_PREC_MIXED}
 
 
@@ -29,7 +29,8 @@ class pcv_rect(ctypes.Structure):
 class pcv_layout(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
                 ("cores", ctypes.POINTER(pcv_rect)), ("n_cores", ctypes.c_int32),
-                ("has_domain", ctypes.c_int32), ("domain", pcv_rect), ("delta", ctypes.c_double)]
+                ("has_domain", ctypes.c_int32), ("domain", pcv_rect), ("delta", ctypes.c_double),
+                ("q", ctypes.c_int32), ("shell_cap", ctypes.c_int32), ("cap_seed", ctypes.c_uint64)]
 
 
 class pcv_options(ctypes.Structure):
@@ -128,7 +129,8 @@ def _ptr(a: np.ndarray, t):
 
 
 def make_layout(layout: dict) -> tuple[pcv_layout, object]:
-    """dict {'kind': 'grid'|'rects', 'nx', 'ny', 'cores', 'delta', 'domain'} -> pcv_layout."""
+    """dict {'kind': 'grid'|'rects'|'recursive', 'nx', 'ny', 'cores', 'q', 'delta', 'domain',
+    'shell_cap', 'cap_seed'} -> pcv_layout."""
     L = pcv_layout()
     keep = None
     if layout["kind"] == "grid":
@@ -140,8 +142,13 @@ def make_layout(layout: dict) -> tuple[pcv_layout, object]:
         L.cores = ctypes.cast(rects, ctypes.POINTER(pcv_rect))
         L.n_cores = len(layout["cores"])
         keep = rects
+    elif layout["kind"] == "recursive":
+        L.kind = PCV_LAYOUT_RECURSIVE
+        L.q = int(layout["q"])
     else:
         raise ValueError(layout["kind"])
+    L.shell_cap = int(layout.get("shell_cap", 0) or 0)
+    L.cap_seed = int(layout.get("cap_seed", 0)) & 0xFFFFFFFFFFFFFFFF
     if layout.get("domain") is not None:
         L.has_domain = 1
         L.domain = pcv_rect(*map(float, layout["domain"]))

@@ -38,7 +38,7 @@ def _compare_members(xy, role, layout):
     for i, (T, V) in enumerate(mem):
         assert np.array_equal(Ti[To[i]:To[i + 1]], T), i
         assert np.array_equal(Vi[Vo[i]:Vo[i + 1]], V), i
-    ref_cores = oracle.layout_cores(layout)
+    ref_cores = oracle.layout_cores(layout, xy)
     assert np.array_equal(cores, np.array([[c[0], c[1], c[3], c[4]] for c in ref_cores]))
     return To, Vo
 

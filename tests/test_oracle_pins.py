@@ -350,3 +350,19 @@ def test_planted_mistakes(name):
         assert failed, f"mutation {name} passed every pin"
     finally:
         shutil.rmtree(d)
+
+
+@pytest.mark.parametrize("k", [1, 2, 57, 420])
+def test_lapack_kriging_matches_plain_routine(k):
+    """The LAPACK-backed kriging used for large subsets agrees with the pinned plain
+    C routine (and, at k = 1, with Eq. 3's closed form e^{-d/rho} y / (1 + lambda))."""
+    r = _rng(40 + k)
+    sT, yT, sP = r.random((k, 2)), r.standard_normal(k), r.random((30, 2))
+    for rho, lam in ((0.05, 0.02), (0.3, 1e-3), (0.1, 0.5)):
+        a, sa = oracle.krige(sT, yT, sP, rho, lam)
+        b, sb = oracle.krige_lapack(sT, yT, sP, rho, lam)
+        assert sa == sb == oracle.OK
+        assert np.max(np.abs(a - b)) <= 1e-10 * max(1.0, np.max(np.abs(a)))
+        if k == 1:
+            d = np.sqrt(((sP - sT[0]) ** 2).sum(1))
+            assert np.allclose(b, np.exp(-d / rho) * yT[0] / (1 + lam), rtol=1e-14, atol=0)

@@ -153,7 +153,7 @@ def test_paper_scale_sampled(gpu_lib, paper5m, prec, B):
     nx = w.layout["nx"]
     pick = sorted(set([0, nx - 1, nx * nx - 1, nx // 2, int(np.argmax(k))] +
                       np.random.default_rng(5).choice(nx * nx, 3, replace=False).tolist()))
-    cores = oracle.layout_cores(w.layout)
+    cores = oracle.layout_cores(w.layout, w.xy)
     members = {i: oracle.subset_members(w.xy, w.role, w.layout, i, cores) for i in pick}
     for b in range(0, B, max(1, B // 2)):
         ref = oracle.cv_loss(w.xy, w.v, w.role, w.layout, P[b:b + 1], members=members, subsets=pick)
@@ -198,7 +198,7 @@ def test_grid_precision_stress(gpu_lib, prec, engine, rho, tau2):
         ph = ctx.phase_cycles() if prec == "mixed" else {}
         V_off = ctx.V_off.copy()
     assert out["status"][0] in (0, 7), out["status"]       # 7: some tasks recomputed in FP64
-    cores = oracle.layout_cores(w.layout)
+    cores = oracle.layout_cores(w.layout, w.xy)
     members = {i: oracle.subset_members(w.xy, w.role, w.layout, i, cores) for i in pick}
     ref = oracle.cv_loss(w.xy, w.v, w.role, w.layout, P, members=members, subsets=pick)
     worst = compare(out, ref, V_off, pick, 1, prec, check_total=False)
@@ -222,3 +222,43 @@ def test_no_pivot_failures_paper_scale(gpu_lib, paper5m):
             fails += ctx.phase_cycles()["fail_factor"]
             assert np.all(np.isin(out["status"], (0, 7)))
     assert fails == 0
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_recursive_layout_with_shell_cap(gpu_lib, prec):
+    """Recursive division (Sec. 2.4) into 16 sub-domains with shells of width 0.05 capped
+    at 150 training points (Sec. 4.3.2): every subset's loss and predictions."""
+    w = datagen.config_uniform_4096()
+    layout = dict(kind="recursive", q=4, delta=0.05, domain=(0.0, 1.0, 0.0, 1.0), shell_cap=150, cap_seed=21)
+    w.layout = layout
+    P = np.array([[1.0, 0.1, 0.05], [0.5, 0.04, 0.01]])
+    out, ref, V_off = _run(gpu_lib, w, P, prec)
+    assert np.all(out["status"] == 0), out["status"]
+    worst = compare(out, ref, V_off, range(16), len(P), prec)
+    print("recursive", prec, worst)
+
+
+@pytest.fixture(scope="module")
+def paper5m_recursive():
+    return datagen.config_paper_5m_recursive()
+
+
+def test_paper_recursive_sampled(gpu_lib, paper5m_recursive):
+    """The paper's weak-scaling layout (Sec. 4.3.2) on the 5M-point field: 512 recursive
+    sub-domains, shell 0.001 capped at 2000, k about 8.3k-8.6k (ld 8704).  Mixed path,
+    two configurations: all statuses clean, and the smallest, the largest and an
+    interior subset compared with the oracle (LAPACK-backed kriging for these sizes)."""
+    w = paper5m_recursive
+    P = w.params[[0, 137]]
+    with gpu_lib.Context(w.xy, w.v, w.role, w.layout) as ctx:
+        out = ctx.cv_loss(P, precision="mixed", per_subset=True, predictions=True)
+        T_off, V_off = ctx.T_off.copy(), ctx.V_off.copy()
+    assert np.all(out["status"] == 0), out["status"]
+    assert np.all(np.isfinite(out["sspe"]))
+    k = np.diff(T_off)
+    pick = sorted({int(np.argmin(k)), int(np.argmax(k)), 300})
+    cores = oracle.layout_cores(w.layout, w.xy)
+    members = {i: oracle.subset_members(w.xy, w.role, w.layout, i, cores) for i in pick}
+    ref = oracle.cv_loss(w.xy, w.v, w.role, w.layout, P, members=members, subsets=pick, lapack=True)
+    worst = compare(out, ref, V_off, pick, len(P), "mixed", check_total=False)
+    print("paper recursive", [int(k[i]) for i in pick], worst)
