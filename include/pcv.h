@@ -197,12 +197,39 @@ pcv_status pcv_cv_loss_device(pcv_ctx* ctx, const double* d_params, int32_t B,
                               int32_t precision, double* d_sspe, double* d_sspe_per_subset,
                               double* d_yhat_valid, int32_t* d_status, void* stream);
 
+/* Local log-likelihood (Eq. 2) of the training data of every subset the CV loss
+ * evaluates (those with validation data; the others contribute 0), a by-product of
+ * the same factorisations:
+ *   -2 log L_i = k_i log(2 pi) + log det(sigma2 Sigma_i + tau2 I)
+ *                + y_T^T (sigma2 Sigma_i + tau2 I)^-1 y_T,
+ * total[b] = the fixed-order sum over subsets (host buffers, like pcv_cv_loss;
+ * per_subset B x N, may be NULL; status as pcv_cv_loss).  FP64: the log-determinant
+ * from the FP64 factor.  Mixed: the quadratic form from the refined solution, the
+ * log-determinant from the FP32 factor, so its error is that of the factorisation,
+ * not the refinement's, and grows with the conditioning (measured: 2e-6 relative of
+ * -2 log L on well-conditioned subsets, 4e-5 at condition ~1e5).  Synchronises. */
+pcv_status pcv_neg2loglik(pcv_ctx* ctx, const double* params, int32_t B, int32_t precision, double* total,
+                          double* per_subset, int32_t* status, void* stream);
+
 /* Kriging predictions (Eq. 3) at m new locations with one configuration.
  * Each location is predicted by the subset whose core contains it (locations
  * outside D are first clamped onto D), from that subset's training data (core
  * and shell).  xy_new: m x 2 host array; yhat: m host outputs.  Synchronises. */
 pcv_status pcv_predict(pcv_ctx* ctx, const double* params3, const double* xy_new, int64_t m,
                        int32_t precision, double* yhat, void* stream);
+
+/* Non-stationary prediction with locally best parameters (Sec. 4.4, where each of the
+ * paper's subsets is scored by its local RMSPE and the hold-out data are predicted
+ * with every subset's best configuration).  Subset i takes the row b of params
+ * (B x 3) with the smallest local SSPE sspe_per_subset[b * N + i] (B x N, as
+ * pcv_cv_loss returns it; NaN rows never chosen, lowest b on ties); a subset without
+ * validation data takes the row with the smallest sum of finite local losses.  Every
+ * location is then predicted as by pcv_predict with the row of the subset whose core
+ * contains it.  best: N host outputs, the chosen row per subset, or NULL; m may be 0
+ * to get the choice alone.  Synchronises. */
+pcv_status pcv_predict_local(pcv_ctx* ctx, const double* params, int32_t B, const double* sspe_per_subset,
+                             const double* xy_new, int64_t m, int32_t precision, double* yhat, int32_t* best,
+                             void* stream);
 
 /* Kernel timing for benchmarks.  When enabled, pcv_cv_loss* records CUDA events
  * on the launching stream around the task kernel and around the combine kernel;

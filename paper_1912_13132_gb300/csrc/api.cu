@@ -93,6 +93,7 @@ struct pcv_ctx {
     DevBuf<unsigned int> fb_count;
     // per-call buffers
     DevBuf<double> z, params, sspe;
+    DevBuf<double> lik, lik_total;          // local -2 log-likelihoods and their sums
     DevBuf<int32_t> tst, status;
     DevBuf<unsigned int> counter;
     Workspace ws[3];                        // FP64, mixed, FP64 fallback of the mixed path
@@ -100,6 +101,7 @@ struct pcv_ctx {
     DevBuf<double> Px, Py, Pyhat;
     DevBuf<int64_t> Poff;
     DevBuf<int32_t> Porder;
+    DevBuf<int32_t> prow;                   // parameter row of each subset (local predictions)
     // optional kernel timing (events on the launching stream)
     bool timing = false;
     bool timed_task = false, timed_combine = false;
@@ -382,13 +384,18 @@ PCV_API pcv_status pcv_subset_info(const pcv_ctx* c, int32_t* N, const int64_t**
 
 static pcv_status run_tasks(pcv_ctx* c, const double* d_params, int32_t B, int32_t prec, const int64_t* P_off,
                             const double* Px, const double* Py, const double* Pv, const int32_t* order,
-                            int32_t n_order, double* d_yhat, int64_t yhat_stride, void* stream) {
+                            int32_t n_order, double* d_yhat, int64_t yhat_stride, void* stream,
+                            bool want_lik = false, const int32_t* d_param_row = nullptr) {
     const int32_t N = c->plan.N;
     CUDA_TRY(c->z.reserve((size_t)B * N));
     CUDA_TRY(c->tst.reserve((size_t)B * N));
     cudaStream_t s = (cudaStream_t)stream;
     CUDA_TRY(cudaMemsetAsync(c->z.p, 0, (size_t)B * N * sizeof(double), s));
     CUDA_TRY(cudaMemsetAsync(c->tst.p, 0, (size_t)B * N * sizeof(int32_t), s));
+    if (want_lik) {
+        CUDA_TRY(c->lik.reserve((size_t)B * N));
+        CUDA_TRY(cudaMemsetAsync(c->lik.p, 0, (size_t)B * N * sizeof(double), s));
+    }
     if ((int64_t)n_order * B == 0) return PCV_OK;
     pcv_status st = ensure_workspace(c, prec);
     if (st != PCV_OK) return st;
@@ -419,6 +426,8 @@ static pcv_status run_tasks(pcv_ctx* c, const double* d_params, int32_t B, int32
     a.B = B;
     a.N = N;
     a.z = c->z.p;
+    a.lik = want_lik ? c->lik.p : nullptr;
+    a.param_row = d_param_row;
     a.tstatus = c->tst.p;
     a.yhat = d_yhat;
     a.yhat_stride = yhat_stride;
@@ -519,35 +528,76 @@ PCV_API pcv_status pcv_cv_loss(pcv_ctx* c, const double* params, int32_t B, int3
     return PCV_OK;
 }
 
-PCV_API pcv_status pcv_predict(pcv_ctx* c, const double* params3, const double* xy_new, int64_t m, int32_t prec,
-                               double* yhat, void* stream) {
+PCV_API pcv_status pcv_neg2loglik(pcv_ctx* c, const double* params, int32_t B, int32_t prec, double* total,
+                                  double* per_subset, int32_t* status, void* stream) {
     if (!c) return fail(PCV_ERR_ARG, "NULL ctx");
-    if (m < 0) return fail(PCV_ERR_ARG, "m < 0");
-    if (m == 0) return PCV_OK;
-    if (!params3 || !xy_new || !yhat) return fail(PCV_ERR_ARG, "NULL argument");
+    if (B < 0) return fail(PCV_ERR_ARG, "B < 0");
+    if (B == 0) return PCV_OK;
+    if (!params || !total) return fail(PCV_ERR_ARG, "NULL params or total");
     if (bad_precision(prec)) return fail(PCV_ERR_ARG, "unknown precision");
+    CUDA_TRY(cudaSetDevice(c->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    const int32_t N = c->plan.N;
+    CUDA_TRY(c->params.reserve((size_t)3 * B));
+    CUDA_TRY(c->lik_total.reserve(B));
+    CUDA_TRY(c->status.reserve(B));
+    CUDA_TRY(c->sspe.reserve(B));
+    CUDA_TRY(cudaMemcpyAsync(c->params.p, params, (size_t)3 * B * sizeof(double), cudaMemcpyHostToDevice, s));
+    pcv_status st = run_tasks(c, c->params.p, B, prec, c->Voff.p, c->Vx.p, c->Vy.p, c->Vv.p, c->order.p,
+                              c->n_active, nullptr, c->nV, stream, true);
+    if (st != PCV_OK) return st;
+    // fixed-order sums: the likelihood's, and the SSPE's for the per-configuration status
+    int e = pcv::launch_combine(c->lik.p, c->tst.p, c->params.p, B, N, c->lik_total.p, nullptr, stream);
+    if (!e) e = pcv::launch_combine(c->z.p, c->tst.p, c->params.p, B, N, c->sspe.p, c->status.p, stream);
+    if (e) return cuda_fail((cudaError_t)e, "combine launch");
+    CUDA_TRY(cudaMemcpyAsync(total, c->lik_total.p, B * sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (status) CUDA_TRY(cudaMemcpyAsync(status, c->status.p, B * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    if (per_subset)
+        CUDA_TRY(cudaMemcpyAsync(per_subset, c->lik.p, (size_t)B * N * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return PCV_OK;
+}
+
+// Core containing each location after clamping onto D: regular layouts search their cut
+// points; other layouts take the first core containing the point, else the nearest.
+static int32_t core_of_point(const pcv::Plan& P, double x, double y) {
+    x = std::min(std::max(x, P.domain.x0), P.domain.x1);
+    y = std::min(std::max(y, P.domain.y0), P.domain.y1);
+    if (P.nx > 0) {
+        auto cell = [](const std::vector<double>& b, double v) {
+            const int n = (int)b.size() - 1;
+            int c = (int)(std::upper_bound(b.begin(), b.end(), v) - b.begin()) - 1;
+            return std::min(std::max(c, 0), n - 1);
+        };
+        return cell(P.by, y) * P.nx + cell(P.bx, x);
+    }
+    int32_t best = -1;
+    double bestd = INFINITY;
+    for (int32_t i = 0; i < P.N; ++i) {
+        const pcv_rect& r = P.cores[i];
+        const bool xc = (r.x1 == P.domain.x1), yc = (r.y1 == P.domain.y1);
+        const bool in = x >= r.x0 && (xc ? x <= r.x1 : x < r.x1) && y >= r.y0 && (yc ? y <= r.y1 : y < r.y1);
+        if (in) return i;
+        const double dx = std::max(std::max(r.x0 - x, 0.0), x - r.x1);
+        const double dy = std::max(std::max(r.y0 - y, 0.0), y - r.y1);
+        const double dd = dx * dx + dy * dy;
+        if (dd < bestd) { bestd = dd; best = i; }
+    }
+    return best;
+}
+
+// Predictions at m locations; params: nrows x 3 host rows, row_of_subset: the row each
+// subset uses (empty: row 0 for all).
+static pcv_status predict_impl(pcv_ctx* c, const double* params, int32_t nrows,
+                               const std::vector<int32_t>& row_of_subset, const double* xy_new, int64_t m,
+                               int32_t prec, double* yhat, void* stream) {
     const pcv::Plan& P = c->plan;
     const int32_t N = P.N;
-    // core containing each point, after clamping onto D
     std::vector<int32_t> core(m);
     for (int64_t j = 0; j < m; ++j) {
-        double x = xy_new[2 * j], y = xy_new[2 * j + 1];
+        const double x = xy_new[2 * j], y = xy_new[2 * j + 1];
         if (!std::isfinite(x) || !std::isfinite(y)) return fail(PCV_ERR_ARG, "non-finite location");
-        x = std::min(std::max(x, P.domain.x0), P.domain.x1);
-        y = std::min(std::max(y, P.domain.y0), P.domain.y1);
-        int32_t best = -1;
-        double bestd = INFINITY;
-        for (int32_t i = 0; i < N; ++i) {
-            const pcv_rect& r = P.cores[i];
-            const bool xc = (r.x1 == P.domain.x1), yc = (r.y1 == P.domain.y1);
-            const bool in = x >= r.x0 && (xc ? x <= r.x1 : x < r.x1) && y >= r.y0 && (yc ? y <= r.y1 : y < r.y1);
-            if (in) { best = i; break; }
-            const double dx = std::max(std::max(r.x0 - x, 0.0), x - r.x1);
-            const double dy = std::max(std::max(r.y0 - y, 0.0), y - r.y1);
-            const double dd = dx * dx + dy * dy;
-            if (dd < bestd) { bestd = dd; best = i; }
-        }
-        core[j] = best;
+        core[j] = core_of_point(P, x, y);
     }
     std::vector<int64_t> off(N + 1, 0);
     for (int64_t j = 0; j < m; ++j) off[core[j] + 1]++;
@@ -573,15 +623,21 @@ PCV_API pcv_status pcv_predict(pcv_ctx* c, const double* params3, const double* 
     CUDA_TRY(c->Pyhat.reserve(m));
     CUDA_TRY(c->Poff.reserve(N + 1));
     CUDA_TRY(c->Porder.reserve(ord.size()));
-    CUDA_TRY(c->params.reserve(3));
+    CUDA_TRY(c->params.reserve((size_t)3 * nrows));
     CUDA_TRY(cudaMemcpyAsync(c->Px.p, px.data(), m * sizeof(double), cudaMemcpyHostToDevice, s));
     CUDA_TRY(cudaMemcpyAsync(c->Py.p, py.data(), m * sizeof(double), cudaMemcpyHostToDevice, s));
     CUDA_TRY(cudaMemcpyAsync(c->Poff.p, off.data(), (N + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
     CUDA_TRY(cudaMemcpyAsync(c->Porder.p, ord.data(), ord.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
-    CUDA_TRY(cudaMemcpyAsync(c->params.p, params3, 3 * sizeof(double), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(c->params.p, params, (size_t)3 * nrows * sizeof(double), cudaMemcpyHostToDevice, s));
+    const int32_t* d_rows = nullptr;
+    if (!row_of_subset.empty()) {
+        CUDA_TRY(c->prow.reserve(N));
+        CUDA_TRY(cudaMemcpyAsync(c->prow.p, row_of_subset.data(), N * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+        d_rows = c->prow.p;
+    }
     // predictions need the slot for matrices as large as the largest training set
     pcv_status st = run_tasks(c, c->params.p, 1, prec, c->Poff.p, c->Px.p, c->Py.p, nullptr, c->Porder.p,
-                              (int32_t)ord.size(), c->Pyhat.p, 0, stream);
+                              (int32_t)ord.size(), c->Pyhat.p, 0, stream, false, d_rows);
     if (st != PCV_OK) return st;
     std::vector<double> out(m);
     std::vector<int32_t> tst(N);
@@ -594,6 +650,48 @@ PCV_API pcv_status pcv_predict(pcv_ctx* c, const double* params3, const double* 
         if (tst[i] != PCV_OK && tst[i] != PCV_REFINE_FALLBACK) worst = (pcv_status)tst[i];
     if (worst != PCV_OK) return fail(worst, "prediction failed for at least one subset");
     return PCV_OK;
+}
+
+PCV_API pcv_status pcv_predict(pcv_ctx* c, const double* params3, const double* xy_new, int64_t m, int32_t prec,
+                               double* yhat, void* stream) {
+    if (!c) return fail(PCV_ERR_ARG, "NULL ctx");
+    if (m < 0) return fail(PCV_ERR_ARG, "m < 0");
+    if (m == 0) return PCV_OK;
+    if (!params3 || !xy_new || !yhat) return fail(PCV_ERR_ARG, "NULL argument");
+    if (bad_precision(prec)) return fail(PCV_ERR_ARG, "unknown precision");
+    return predict_impl(c, params3, 1, {}, xy_new, m, prec, yhat, stream);
+}
+
+PCV_API pcv_status pcv_predict_local(pcv_ctx* c, const double* params, int32_t B, const double* sspe_per_subset,
+                                     const double* xy_new, int64_t m, int32_t prec, double* yhat, int32_t* best,
+                                     void* stream) {
+    if (!c) return fail(PCV_ERR_ARG, "NULL ctx");
+    if (B < 1 || m < 0) return fail(PCV_ERR_ARG, "B < 1 or m < 0");
+    if (!params || !sspe_per_subset || (m > 0 && (!xy_new || !yhat))) return fail(PCV_ERR_ARG, "NULL argument");
+    if (bad_precision(prec)) return fail(PCV_ERR_ARG, "unknown precision");
+    const pcv::Plan& P = c->plan;
+    const int32_t N = P.N;
+    // the globally best row: smallest sum of the local losses, rows with a non-finite one excluded
+    int32_t gbest = -1;
+    double gmin = INFINITY;
+    for (int32_t b = 0; b < B; ++b) {
+        double t = 0.0;
+        for (int32_t i = 0; i < N; ++i) t += sspe_per_subset[(int64_t)b * N + i];
+        if (std::isfinite(t) && t < gmin) { gmin = t; gbest = b; }
+    }
+    if (gbest < 0) return fail(PCV_ERR_ARG, "no configuration has finite local losses");
+    std::vector<int32_t> row(N, gbest);
+    for (int32_t i = 0; i < N; ++i) {
+        if (P.V_off[i + 1] == P.V_off[i]) continue;   // no validation data: the global choice
+        double zmin = INFINITY;
+        for (int32_t b = 0; b < B; ++b) {
+            const double z = sspe_per_subset[(int64_t)b * N + i];
+            if (std::isfinite(z) && z < zmin) { zmin = z; row[i] = b; }
+        }
+    }
+    if (best) std::copy(row.begin(), row.end(), best);
+    if (m == 0) return PCV_OK;
+    return predict_impl(c, params, B, row, xy_new, m, prec, yhat, stream);
 }
 
 PCV_API pcv_status pcv_set_timing(pcv_ctx* c, int32_t enable) {

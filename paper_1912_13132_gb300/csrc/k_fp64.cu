@@ -65,6 +65,7 @@ struct Smem64 {
     double Ta[KC][NB + 1];    // trailing-update staging: rows of the updated tile
     double Tb[KC][NB + 1];    // trailing-update staging: rows of the block column's top
     double red[NT / 32];
+    double red2[NT / 32];
     int flag;
     int task;
 };
@@ -111,7 +112,8 @@ __device__ void update_tile(Smem64& sm, double* A, int64_t ld, int r0, int rb, i
 // Factor task (subset i, configuration b); returns the task status.
 __device__ int run_task(Smem64& sm, const TaskArgs& a, int i, int b) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const double s2 = a.params[3 * b], rho = a.params[3 * b + 1], tau2 = a.params[3 * b + 2];
+    const int pr = a.param_row ? a.param_row[i] : b;   // the subset's own row, or the task's
+    const double s2 = a.params[3 * pr], rho = a.params[3 * pr + 1], tau2 = a.params[3 * pr + 2];
     const int64_t zoff = (int64_t)b * a.N + i;
     const int64_t p0 = a.P_off[i];
     const int m = (int)(a.P_off[i + 1] - p0);
@@ -119,7 +121,11 @@ __device__ int run_task(Smem64& sm, const TaskArgs& a, int i, int b) {
     if (bad) {
         if (a.yhat)
             for (int j = tid; j < m; j += NT) a.yhat[(int64_t)b * a.yhat_stride + p0 + j] = NAN;
-        if (tid == 0) { a.z[zoff] = NAN; a.tstatus[zoff] = PCV_ERR_ARG; }
+        if (tid == 0) {
+            a.z[zoff] = NAN;
+            if (a.lik) a.lik[zoff] = NAN;
+            a.tstatus[zoff] = PCV_ERR_ARG;
+        }
         return PCV_ERR_ARG;
     }
     const double lam = tau2 / s2;
@@ -182,7 +188,11 @@ __device__ int run_task(Smem64& sm, const TaskArgs& a, int i, int b) {
         if (sm.flag) {
             if (a.yhat)
                 for (int j = tid; j < m; j += NT) a.yhat[(int64_t)b * a.yhat_stride + p0 + j] = NAN;
-            if (tid == 0) { a.z[zoff] = NAN; a.tstatus[zoff] = PCV_NOT_SPD; }
+            if (tid == 0) {
+                a.z[zoff] = NAN;
+                if (a.lik) a.lik[zoff] = NAN;
+                a.tstatus[zoff] = PCV_NOT_SPD;
+            }
             __syncthreads();
             return PCV_NOT_SPD;
         }
@@ -235,6 +245,26 @@ __device__ int run_task(Smem64& sm, const TaskArgs& a, int i, int b) {
                 for (int p = c + 1; p < jb; ++p) s -= S.A[(j0 + p) + (int64_t)(j0 + c) * ld] * S.al[j0 + p];
                 S.al[j0 + c] = s / S.A[(j0 + c) + (int64_t)(j0 + c) * ld];
             }
+        __syncthreads();
+    }
+
+    // local -2 log-likelihood (Eq. 2) of the training data from the same factor:
+    // log det(sigma2 A) = k log sigma2 + 2 sum log L_jj, y^T (sigma2 A)^-1 y = y^T alpha / sigma2
+    if (a.lik) {
+        double ldet = 0.0, quad = 0.0;
+        for (int q = tid; q < k; q += NT) {
+            ldet += log(S.A[q + (int64_t)q * ld]);
+            quad += a.Vals[a.T_idx[t0 + q]] * S.al[q];
+        }
+        ldet = warp_sum(ldet);
+        quad = warp_sum(quad);
+        if (lane == 0) { sm.red[warp] = ldet; sm.red2[warp] = quad; }
+        __syncthreads();
+        if (tid == 0) {
+            double l = 0.0, qf = 0.0;
+            for (int w = 0; w < NT / 32; ++w) { l += sm.red[w]; qf += sm.red2[w]; }
+            a.lik[zoff] = k * log(2.0 * M_PI) + k * log(s2) + 2.0 * l + qf / s2;
+        }
         __syncthreads();
     }
 

@@ -102,6 +102,7 @@ struct alignas(16) SmemM {
     float ph[16][NB], pl[16][NB];  // residual partial sums (double-float)
     float wj[2 * NB];              // solve block (128 entries in the tensor-core kernel)
     double dred[NT / 32];
+    double dred2[NT / 32];
     float fred[NT / 32];
     int flag;
 };
@@ -1051,7 +1052,8 @@ template <bool TC, class Sch = umma::SplitBF16x3>
 __device__ void run_task(SmemM& sm, SmemKeep& keep, SmemSimt* simt, TcCtx* tc, const TaskArgs& a, int t, int i,
                          int b) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const double s2 = a.params[3 * b], rho = a.params[3 * b + 1], tau2 = a.params[3 * b + 2];
+    const int pr = a.param_row ? a.param_row[i] : b;   // the subset's own row, or the task's
+    const double s2 = a.params[3 * pr], rho = a.params[3 * pr + 1], tau2 = a.params[3 * pr + 2];
     const int64_t zoff = (int64_t)b * a.N + i;
     const int64_t p0 = a.P_off[i];
     const int m = (int)(a.P_off[i + 1] - p0);
@@ -1059,7 +1061,11 @@ __device__ void run_task(SmemM& sm, SmemKeep& keep, SmemSimt* simt, TcCtx* tc, c
     if (bad) {
         if (a.yhat)
             for (int j = tid; j < m; j += NT) a.yhat[(int64_t)b * a.yhat_stride + p0 + j] = NAN;
-        if (tid == 0) { a.z[zoff] = NAN; a.tstatus[zoff] = PCV_ERR_ARG; }
+        if (tid == 0) {
+            a.z[zoff] = NAN;
+            if (a.lik) a.lik[zoff] = NAN;
+            a.tstatus[zoff] = PCV_ERR_ARG;
+        }
         return;
     }
     const double lam = tau2 / s2;
@@ -1241,6 +1247,34 @@ __device__ void run_task(SmemM& sm, SmemKeep& keep, SmemSimt* simt, TcCtx* tc, c
         }
         __syncthreads();
         return;
+    }
+
+    // local -2 log-likelihood (Eq. 2) of the training data: the quadratic form from
+    // the refined solution, the log-determinant from the FP32 factor's diagonal (the
+    // tensor-core engines keep L_JJ^-1 there, whose diagonal is 1 / L_jj)
+    if (a.lik) {
+        double ldet = 0.0, quad = 0.0;
+        for (int q = tid; q < k; q += NT) {
+            const double d = (double)R.L[q + (int64_t)q * ld];
+            ldet += TC ? -log(d) : log(d);
+            quad += R.yv[q] * R.xs[q];
+        }
+        ldet = warp_sum_d(ldet);
+        quad = warp_sum_d(quad);
+        if (lane == 0) {
+            sm.dred[warp] = ldet;
+            sm.dred2[warp] = quad;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            double l = 0.0, qf = 0.0;
+            for (int w = 0; w < NT / 32; ++w) {
+                l += sm.dred[w];
+                qf += sm.dred2[w];
+            }
+            a.lik[zoff] = k * log(2.0 * M_PI) + k * log(s2) + 2.0 * l + qf / s2;
+        }
+        __syncthreads();
     }
 
     // predict (Eq. 3) in double-float, squared errors in FP64 (Eq. 4)

@@ -21,6 +21,8 @@ struct Plan {
     int32_t N = 0;
     std::vector<int64_t> T_off, T_idx, V_off, V_idx;
     std::vector<pcv_rect> cores;
+    int32_t nx = 0, ny = 0;             // regular layouts: cut points for direct core lookup
+    std::vector<double> bx, by;
     pcv_rect domain{};
     double delta = 0.0;
 };
@@ -47,6 +49,8 @@ struct TaskArgs {
     int32_t B;
     int32_t N;
     double* z;              // B x N local SSPE
+    double* lik;            // B x N local -2 log-likelihood (Eq. 2) of the training data, or NULL
+    const int32_t* param_row;   // N: parameter row of each subset (overrides the task's b), or NULL
     int32_t* tstatus;       // B x N task status
     double* yhat;           // predictions: yhat[b * yhat_stride + P_off[i] + j], or NULL
     int64_t yhat_stride;

@@ -231,6 +231,10 @@ pcv_status build_plan(const double* xy, const uint8_t* role, int64_t n, const pc
         for (int c = 0; c < nx; ++c) { wxl[c] = bx[c] - d; wxh[c] = bx[c + 1] + d; }
         for (int c = 0; c < ny; ++c) { wyl[c] = by[c] - d; wyh[c] = by[c + 1] + d; }
         P.N = N;
+        P.nx = nx;
+        P.ny = ny;
+        P.bx = bx;
+        P.by = by;
         P.cores.resize(N);
         for (int cy = 0; cy < ny; ++cy)
             for (int cx = 0; cx < nx; ++cx) P.cores[cy * nx + cx] = {bx[cx], bx[cx + 1], by[cy], by[cy + 1]};

@@ -72,6 +72,9 @@ _SIGS = {
     "pcv_cv_loss_device": (ctypes.c_int, [_vp, _vp, ctypes.c_int32, ctypes.c_int32, _vp, _vp, _vp,
                                           _vp, _vp]),
     "pcv_predict": (ctypes.c_int, [_vp, _dp, _dp, ctypes.c_int64, ctypes.c_int32, _dp, _vp]),
+    "pcv_neg2loglik": (ctypes.c_int, [_vp, _dp, ctypes.c_int32, ctypes.c_int32, _dp, _dp, _i32p, _vp]),
+    "pcv_predict_local": (ctypes.c_int, [_vp, _dp, ctypes.c_int32, _dp, _dp, ctypes.c_int64, ctypes.c_int32, _dp,
+                                         _i32p, _vp]),
     "pcv_set_timing": (ctypes.c_int, [_vp, ctypes.c_int32]),
     "pcv_kernel_time": (ctypes.c_int, [_vp, _dp, _dp]),
     "pcv_phase_cycles": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_uint64), ctypes.c_int32]),
@@ -286,6 +289,35 @@ class Context:
         out = (ctypes.c_uint64 * 16)()
         _check(_lib.pcv_phase_cycles(self._h, out, 1 if reset else 0), "pcv_phase_cycles")
         return {name: int(out[i]) for i, name in enumerate(self.PHASES)}
+
+    def neg2loglik(self, params, precision: str = "mixed", per_subset: bool = False, stream=None) -> dict:
+        """Local -2 log-likelihoods (Eq. 2) of the subsets' training data (pcv_neg2loglik):
+        'total' (B,), 'status' (B,), and 'per_subset' (B, N) on request."""
+        P = _f64(params).reshape(-1, 3)
+        B = len(P)
+        total = np.empty(B)
+        status = np.empty(B, dtype=np.int32)
+        per = np.empty((B, self.N)) if per_subset else None
+        _check(_lib.pcv_neg2loglik(self._h, _ptr(P, _dp), B, PRECISIONS[precision], _ptr(total, _dp),
+                                   _ptr(per, _dp) if per is not None else None, _ptr(status, _i32p),
+                                   _stream_ptr(stream)), "pcv_neg2loglik")
+        out = dict(total=total, status=status)
+        if per is not None:
+            out["per_subset"] = per
+        return out
+
+    def predict_local(self, params, sspe_per_subset, xy_new, precision="mixed", stream=None):
+        """pcv_predict_local: predictions with each subset's locally best row of params;
+        returns (yhat, best row per subset)."""
+        P = _f64(params).reshape(-1, 3)
+        z = _f64(sspe_per_subset).reshape(len(P), self.N)
+        q = _f64(xy_new).reshape(-1, 2)
+        out = np.empty(len(q))
+        best = np.empty(self.N, dtype=np.int32)
+        _check(_lib.pcv_predict_local(self._h, _ptr(P, _dp), len(P), _ptr(z, _dp), _ptr(q, _dp), len(q),
+                                      PRECISIONS[precision], _ptr(out, _dp), _ptr(best, _i32p),
+                                      _stream_ptr(stream)), "pcv_predict_local")
+        return out, best
 
     def predict(self, params3, xy_new, precision="mixed", stream=None):
         p = _f64(params3).reshape(3)
