@@ -207,7 +207,8 @@ pcv_status pcv_cv_loss_device(pcv_ctx* ctx, const double* d_params, int32_t B,
  * from the FP64 factor.  Mixed: the quadratic form from the refined solution, the
  * log-determinant from the FP32 factor, so its error is that of the factorisation,
  * not the refinement's, and grows with the conditioning (measured: 2e-6 relative of
- * -2 log L on well-conditioned subsets, 4e-5 at condition ~1e5).  Synchronises. */
+ * -2 log L on well-conditioned subsets, 4e-5 at condition ~1e5); mixed precision
+ * needs the default tensor engine or the SIMT engine.  Synchronises. */
 pcv_status pcv_neg2loglik(pcv_ctx* ctx, const double* params, int32_t B, int32_t precision, double* total,
                           double* per_subset, int32_t* status, void* stream);
 
@@ -230,6 +231,22 @@ pcv_status pcv_predict(pcv_ctx* ctx, const double* params3, const double* xy_new
 pcv_status pcv_predict_local(pcv_ctx* ctx, const double* params, int32_t B, const double* sspe_per_subset,
                              const double* xy_new, int64_t m, int32_t precision, double* yhat, int32_t* best,
                              void* stream);
+
+/* Generalised least squares for a linear mean (Sec. 5): with covariates X the model
+ * becomes y ~ N(X beta, sigma2 Sigma + tau2 I) and
+ *     beta = (X^T M^-1 X)^-1 X^T M^-1 y,   M = Sigma + lambda I,  lambda = tau2 / sigma2,
+ * over the TRAIN points.  Sec. 5 rewrites M^-1 v = (v - H v) / lambda, H v the kriging
+ * prediction of v at the observed locations, so M^-1 X comes from prediction
+ * operations on the columns of X; here H v at a training point is the prediction from
+ * the training data of the subset whose core holds the point (the parallel
+ * approximation of H; exact when one subset covers D).  One factorisation per subset
+ * serves all p + 1 columns (the covariates and y), each refined and predicted in turn;
+ * the p x p system (X^T (X - H X)) beta = X^T (y - H y) is summed in subset order and
+ * solved on the host.  X: n x p row-major, host, a row per input point (only TRAIN
+ * rows are used), 1 <= p <= 64; params3 = (sigma2, rho, tau2) with tau2 > 0; beta: p
+ * host outputs.  Mixed precision needs the default tensor engine.  Synchronises. */
+pcv_status pcv_gls(pcv_ctx* ctx, const double* X, int32_t p, const double* params3, int32_t precision,
+                   double* beta, void* stream);
 
 /* Kernel timing for benchmarks.  When enabled, pcv_cv_loss* records CUDA events
  * on the launching stream around the task kernel and around the combine kernel;

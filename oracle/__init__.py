@@ -25,6 +25,9 @@ Pieces and the passages they follow:
   combine step), subsets without validation data contribute nothing
   (Sec. 4.3.1).
 * ``neg2loglik``: Eq. 2 (C routine).
+* ``gls`` / ``gls_exact``: the GLS mean of Sec. 5, beta = (X^T M^-1 X)^-1 X^T M^-1 y,
+  with M^-1 v = (v - H v) / lambda and H v from the subsets' kriging (the
+  parallel approximation), and the same estimate from a dense solve.
 
 Parity of every function is pinned by ``tests/test_oracle_pins.py`` against
 closed forms, exact rational solves, brute force and library routines that the
@@ -473,3 +476,49 @@ def predict(xy, v, role, layout, param, pts, members=None):
         yh, st = krige(xy[T], v[T], pts[sel], rho, tau / s2)
         out[sel] = yh
     return out
+
+
+# ----------------------------------------------------------------------------
+# GLS mean component (Sec. 5)
+# ----------------------------------------------------------------------------
+def gls(xy, v, role, layout, X, param, lapack: bool = False) -> np.ndarray:
+    """beta = (X^T M^-1 X)^-1 X^T M^-1 y over the TRAIN points, M = Sigma + lambda I.
+
+    Sec. 5: M^-1 = (I - H) / lambda with H = Sigma (Sigma + lambda I)^-1 the kriging
+    operator at the observed locations, so M^-1 v is found by predicting v.  Parallel
+    approximation: H v at a training point is the kriging prediction from the training
+    data of the subset whose core holds the point (Eq. 3 applied to the column v).
+    The 1 / lambda cancels.  The sums run over the points subset by subset."""
+    xy, v = _f64(xy), _f64(v)
+    X = _f64(X).reshape(len(v), -1)
+    s2, rho, tau = [float(t) for t in param]
+    lam = tau / s2
+    cores = layout_cores(layout, xy)
+    p = X.shape[1]
+    A = np.zeros((p, p))
+    b = np.zeros(p)
+    kr = krige_lapack if lapack else krige
+    for i, (x0, x1, xc, y0, y1, yc) in enumerate(cores):
+        T, _ = subset_members(xy, role, layout, i, cores)
+        px, py = xy[T, 0], xy[T, 1]
+        C = T[(px >= x0) & ((px <= x1) if xc else (px < x1)) & (py >= y0) & ((py <= y1) if yc else (py < y1))]
+        if len(C) == 0:
+            continue
+        HX = np.stack([kr(xy[T], X[T, c], xy[C], rho, lam)[0] for c in range(p)], 1)
+        Hy, _ = kr(xy[T], v[T], xy[C], rho, lam)
+        A += X[C].T @ (X[C] - HX)
+        b += X[C].T @ (v[C] - Hy)
+    return np.linalg.solve(A, b)
+
+
+def gls_exact(xy, v, role, X, param) -> np.ndarray:
+    """The same estimate with M = Sigma + lambda I over all TRAIN points, by dense solves."""
+    xy, v = _f64(xy), _f64(v)
+    X = _f64(X).reshape(len(v), -1)
+    s2, rho, tau = [float(t) for t in param]
+    T = np.nonzero(np.asarray(role) == TRAIN)[0]
+    d = np.sqrt(((xy[T, None, :] - xy[None, T, :]) ** 2).sum(-1))
+    M = np.exp(-d / rho) + (tau / s2) * np.eye(len(T))
+    MiX = np.linalg.solve(M, X[T])
+    Miy = np.linalg.solve(M, v[T])
+    return np.linalg.solve(X[T].T @ MiX, X[T].T @ Miy)

@@ -102,6 +102,9 @@ struct pcv_ctx {
     DevBuf<int64_t> Poff;
     DevBuf<int32_t> Porder;
     DevBuf<int32_t> prow;                   // parameter row of each subset (local predictions)
+    DevBuf<double> rhs;                     // several right-hand sides (GLS), column-major n x r
+    std::vector<double> hxy;                // host copy of the coordinates (GLS)
+    std::vector<double> hv;                 // host copy of the values (GLS)
     // optional kernel timing (events on the launching stream)
     bool timing = false;
     bool timed_task = false, timed_combine = false;
@@ -313,6 +316,8 @@ PCV_API pcv_status pcv_create(const double* xy, const double* v, const uint8_t* 
     const pcv::Plan& P = c->plan;
     const int32_t N = P.N;
 
+    c->hxy.assign(xy, xy + 2 * n);
+    c->hv.assign(v, v + n);
     // points as SoA
     std::vector<double> hx(n), hy(n);
     for (int64_t j = 0; j < n; ++j) { hx[j] = xy[2 * j]; hy[j] = xy[2 * j + 1]; }
@@ -385,7 +390,8 @@ PCV_API pcv_status pcv_subset_info(const pcv_ctx* c, int32_t* N, const int64_t**
 static pcv_status run_tasks(pcv_ctx* c, const double* d_params, int32_t B, int32_t prec, const int64_t* P_off,
                             const double* Px, const double* Py, const double* Pv, const int32_t* order,
                             int32_t n_order, double* d_yhat, int64_t yhat_stride, void* stream,
-                            bool want_lik = false, const int32_t* d_param_row = nullptr) {
+                            bool want_lik = false, const int32_t* d_param_row = nullptr,
+                            const double* d_rhs = nullptr, int32_t nrhs = 0) {
     const int32_t N = c->plan.N;
     CUDA_TRY(c->z.reserve((size_t)B * N));
     CUDA_TRY(c->tst.reserve((size_t)B * N));
@@ -428,6 +434,9 @@ static pcv_status run_tasks(pcv_ctx* c, const double* d_params, int32_t B, int32
     a.z = c->z.p;
     a.lik = want_lik ? c->lik.p : nullptr;
     a.param_row = d_param_row;
+    a.rhs = d_rhs;
+    a.nrhs = nrhs;
+    a.rhs_stride = (int64_t)c->plan.n;
     a.tstatus = c->tst.p;
     a.yhat = d_yhat;
     a.yhat_stride = yhat_stride;
@@ -692,6 +701,114 @@ PCV_API pcv_status pcv_predict_local(pcv_ctx* c, const double* params, int32_t B
     if (best) std::copy(row.begin(), row.end(), best);
     if (m == 0) return PCV_OK;
     return predict_impl(c, params, B, row, xy_new, m, prec, yhat, stream);
+}
+
+PCV_API pcv_status pcv_gls(pcv_ctx* c, const double* X, int32_t p, const double* params3, int32_t prec,
+                           double* beta, void* stream) {
+    if (!c) return fail(PCV_ERR_ARG, "NULL ctx");
+    if (p < 1 || p > 64) return fail(PCV_ERR_ARG, "need 1 <= p <= 64 covariates");
+    if (!X || !params3 || !beta) return fail(PCV_ERR_ARG, "NULL argument");
+    if (bad_precision(prec)) return fail(PCV_ERR_ARG, "unknown precision");
+    const double s2 = params3[0], rho = params3[1], tau2 = params3[2];
+    if (!(s2 > 0.0) || !(rho > 0.0) || !(tau2 > 0.0) || !std::isfinite(s2) || !std::isfinite(rho) ||
+        !std::isfinite(tau2))
+        return fail(PCV_ERR_ARG, "GLS needs sigma2 > 0, rho > 0 and a nugget tau2 > 0");
+    if (prec == PCV_PREC_MIXED && c->opts.factor_engine != pcv::kMixedEngineTensor)
+        return fail(PCV_ERR_ARG, "GLS in mixed precision needs the default tensor engine");
+    const pcv::Plan& P = c->plan;
+    const int32_t N = P.N;
+    const int64_t n = P.n;
+    // every TRAIN point of D once, from the subset whose core holds it: the prediction
+    // locations of H (core training points of each subset, in subset order)
+    std::vector<int64_t> off(N + 1, 0), who;
+    std::vector<double> px, py;
+    for (int32_t i = 0; i < N; ++i) {
+        const pcv_rect& r = P.cores[i];
+        const bool xc = r.x1 == P.domain.x1, yc = r.y1 == P.domain.y1;
+        for (int64_t q = P.T_off[i]; q < P.T_off[i + 1]; ++q) {
+            const int64_t j = P.T_idx[q];
+            const double x = c->hxy[2 * j], y = c->hxy[2 * j + 1];
+            if (x >= r.x0 && (xc ? x <= r.x1 : x < r.x1) && y >= r.y0 && (yc ? y <= r.y1 : y < r.y1)) {
+                who.push_back(j);
+                px.push_back(x);
+                py.push_back(y);
+            }
+        }
+        off[i + 1] = (int64_t)who.size();
+    }
+    const int64_t m = (int64_t)who.size();
+    if (m == 0) return fail(PCV_ERR_ARG, "no training points inside the cores");
+    std::vector<int32_t> ord;
+    for (int32_t i = 0; i < N; ++i)
+        if (off[i + 1] > off[i]) ord.push_back(i);
+    std::stable_sort(ord.begin(), ord.end(), [&](int32_t a2, int32_t b2) {
+        return (P.T_off[a2 + 1] - P.T_off[a2]) > (P.T_off[b2 + 1] - P.T_off[b2]);
+    });
+    // right-hand sides: the p covariate columns, then y
+    const int32_t nr = p + 1;
+    std::vector<double> R((size_t)nr * n);
+    for (int32_t col = 0; col < p; ++col)
+        for (int64_t j = 0; j < n; ++j) R[(size_t)col * n + j] = X[(size_t)j * p + col];
+    std::copy(c->hv.begin(), c->hv.end(), R.begin() + (size_t)p * n);
+    CUDA_TRY(cudaSetDevice(c->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    CUDA_TRY(c->rhs.reserve((size_t)nr * n));
+    CUDA_TRY(c->Px.reserve(m));
+    CUDA_TRY(c->Py.reserve(m));
+    CUDA_TRY(c->Pyhat.reserve((size_t)nr * m));
+    CUDA_TRY(c->Poff.reserve(N + 1));
+    CUDA_TRY(c->Porder.reserve(ord.size()));
+    CUDA_TRY(c->params.reserve(3));
+    CUDA_TRY(cudaMemcpyAsync(c->rhs.p, R.data(), R.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(c->Px.p, px.data(), m * sizeof(double), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(c->Py.p, py.data(), m * sizeof(double), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(c->Poff.p, off.data(), (N + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(c->Porder.p, ord.data(), ord.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(c->params.p, params3, 3 * sizeof(double), cudaMemcpyHostToDevice, s));
+    // H applied to every column at the core training points: one factorisation per subset
+    pcv_status st = run_tasks(c, c->params.p, 1, prec, c->Poff.p, c->Px.p, c->Py.p, nullptr, c->Porder.p,
+                              (int32_t)ord.size(), c->Pyhat.p, m, stream, false, nullptr, c->rhs.p, nr);
+    if (st != PCV_OK) return st;
+    std::vector<double> H((size_t)nr * m);
+    std::vector<int32_t> tst(N);
+    CUDA_TRY(cudaMemcpyAsync(H.data(), c->Pyhat.p, H.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(tst.data(), c->tst.p, N * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    for (int32_t i : ord)
+        if (tst[i] != PCV_OK && tst[i] != PCV_REFINE_FALLBACK) return fail((pcv_status)tst[i], "GLS solve failed");
+    // M^-1 v = (v - H v) / lambda; the 1 / lambda cancels in beta:
+    // (X^T (X - H X)) beta = X^T (y - H y), summed over the points in subset order
+    std::vector<double> A((size_t)p * p, 0.0), rhsb(p, 0.0);
+    for (int64_t q = 0; q < m; ++q) {
+        const int64_t j = who[q];
+        const double* xj = X + (size_t)j * p;
+        for (int32_t u = 0; u < p; ++u) {
+            for (int32_t w = 0; w < p; ++w) A[(size_t)u * p + w] += xj[u] * (xj[w] - H[(size_t)w * m + q]);
+            rhsb[u] += xj[u] * (c->hv[j] - H[(size_t)p * m + q]);
+        }
+    }
+    // p x p solve: Gaussian elimination with partial pivoting
+    for (int32_t col = 0; col < p; ++col) {
+        int32_t piv = col;
+        for (int32_t r2 = col + 1; r2 < p; ++r2)
+            if (std::fabs(A[(size_t)r2 * p + col]) > std::fabs(A[(size_t)piv * p + col])) piv = r2;
+        if (!(std::fabs(A[(size_t)piv * p + col]) > 0.0)) return fail(PCV_NOT_SPD, "singular GLS system");
+        if (piv != col) {
+            for (int32_t w = 0; w < p; ++w) std::swap(A[(size_t)piv * p + w], A[(size_t)col * p + w]);
+            std::swap(rhsb[piv], rhsb[col]);
+        }
+        for (int32_t r2 = col + 1; r2 < p; ++r2) {
+            const double f = A[(size_t)r2 * p + col] / A[(size_t)col * p + col];
+            for (int32_t w = col; w < p; ++w) A[(size_t)r2 * p + w] -= f * A[(size_t)col * p + w];
+            rhsb[r2] -= f * rhsb[col];
+        }
+    }
+    for (int32_t col = p - 1; col >= 0; --col) {
+        double t = rhsb[col];
+        for (int32_t w = col + 1; w < p; ++w) t -= A[(size_t)col * p + w] * beta[w];
+        beta[col] = t / A[(size_t)col * p + col];
+    }
+    return PCV_OK;
 }
 
 PCV_API pcv_status pcv_set_timing(pcv_ctx* c, int32_t enable) {

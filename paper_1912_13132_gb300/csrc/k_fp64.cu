@@ -211,88 +211,96 @@ __device__ int run_task(Smem64& sm, const TaskArgs& a, int i, int b) {
         __syncthreads();
     }
 
-    // forward substitution L w = y
-    for (int J = 0; J < nb; ++J) {
-        const int j0 = J * NB, jb = min(NB, k - j0);
-        for (int r = warp; r < jb; r += NT / 32) {
-            double s = 0.0;
-            for (int p = lane; p < j0; p += 32) s += S.A[(j0 + r) + (int64_t)p * ld] * S.al[p];
-            s = warp_sum(s);
-            if (lane == 0) S.al[j0 + r] -= s;
+    // several right-hand sides (a.rhs): one factorisation, each column solved and predicted
+    const int nrhs = a.rhs ? a.nrhs : 1;
+    for (int rh = 0; rh < nrhs; ++rh) {
+        if (a.rhs) {   // this column's values (the factor stays)
+            for (int t = tid; t < k; t += NT) S.al[t] = a.rhs[rh * a.rhs_stride + a.T_idx[t0 + t]];
+            __syncthreads();
         }
-        __syncthreads();
-        if (tid == 0)
-            for (int c = 0; c < jb; ++c) {
-                double s = S.al[j0 + c];
-                for (int p = 0; p < c; ++p) s -= S.A[(j0 + c) + (int64_t)(j0 + p) * ld] * S.al[j0 + p];
-                S.al[j0 + c] = s / S.A[(j0 + c) + (int64_t)(j0 + c) * ld];
+        // forward substitution L w = y
+        for (int J = 0; J < nb; ++J) {
+            const int j0 = J * NB, jb = min(NB, k - j0);
+            for (int r = warp; r < jb; r += NT / 32) {
+                double s = 0.0;
+                for (int p = lane; p < j0; p += 32) s += S.A[(j0 + r) + (int64_t)p * ld] * S.al[p];
+                s = warp_sum(s);
+                if (lane == 0) S.al[j0 + r] -= s;
             }
-        __syncthreads();
-    }
-    // back substitution L^T alpha = w
-    for (int J = nb - 1; J >= 0; --J) {
-        const int j0 = J * NB, jb = min(NB, k - j0);
-        for (int c = warp; c < jb; c += NT / 32) {
-            double s = 0.0;
-            for (int p = j0 + jb + lane; p < k; p += 32) s += S.A[p + (int64_t)(j0 + c) * ld] * S.al[p];
-            s = warp_sum(s);
-            if (lane == 0) S.al[j0 + c] -= s;
+            __syncthreads();
+            if (tid == 0)
+                for (int c = 0; c < jb; ++c) {
+                    double s = S.al[j0 + c];
+                    for (int p = 0; p < c; ++p) s -= S.A[(j0 + c) + (int64_t)(j0 + p) * ld] * S.al[j0 + p];
+                    S.al[j0 + c] = s / S.A[(j0 + c) + (int64_t)(j0 + c) * ld];
+                }
+            __syncthreads();
         }
-        __syncthreads();
-        if (tid == 0)
-            for (int c = jb - 1; c >= 0; --c) {
-                double s = S.al[j0 + c];
-                for (int p = c + 1; p < jb; ++p) s -= S.A[(j0 + p) + (int64_t)(j0 + c) * ld] * S.al[j0 + p];
-                S.al[j0 + c] = s / S.A[(j0 + c) + (int64_t)(j0 + c) * ld];
+        // back substitution L^T alpha = w
+        for (int J = nb - 1; J >= 0; --J) {
+            const int j0 = J * NB, jb = min(NB, k - j0);
+            for (int c = warp; c < jb; c += NT / 32) {
+                double s = 0.0;
+                for (int p = j0 + jb + lane; p < k; p += 32) s += S.A[p + (int64_t)(j0 + c) * ld] * S.al[p];
+                s = warp_sum(s);
+                if (lane == 0) S.al[j0 + c] -= s;
             }
-        __syncthreads();
-    }
+            __syncthreads();
+            if (tid == 0)
+                for (int c = jb - 1; c >= 0; --c) {
+                    double s = S.al[j0 + c];
+                    for (int p = c + 1; p < jb; ++p) s -= S.A[(j0 + p) + (int64_t)(j0 + c) * ld] * S.al[j0 + p];
+                    S.al[j0 + c] = s / S.A[(j0 + c) + (int64_t)(j0 + c) * ld];
+                }
+            __syncthreads();
+        }
 
-    // local -2 log-likelihood (Eq. 2) of the training data from the same factor:
-    // log det(sigma2 A) = k log sigma2 + 2 sum log L_jj, y^T (sigma2 A)^-1 y = y^T alpha / sigma2
-    if (a.lik) {
-        double ldet = 0.0, quad = 0.0;
-        for (int q = tid; q < k; q += NT) {
-            ldet += log(S.A[q + (int64_t)q * ld]);
-            quad += a.Vals[a.T_idx[t0 + q]] * S.al[q];
+        // local -2 log-likelihood (Eq. 2) of the training data from the same factor:
+        // log det(sigma2 A) = k log sigma2 + 2 sum log L_jj, y^T (sigma2 A)^-1 y = y^T alpha / sigma2
+        if (a.lik && rh == 0) {
+            double ldet = 0.0, quad = 0.0;
+            for (int q = tid; q < k; q += NT) {
+                ldet += log(S.A[q + (int64_t)q * ld]);
+                quad += a.Vals[a.T_idx[t0 + q]] * S.al[q];
+            }
+            ldet = warp_sum(ldet);
+            quad = warp_sum(quad);
+            if (lane == 0) { sm.red[warp] = ldet; sm.red2[warp] = quad; }
+            __syncthreads();
+            if (tid == 0) {
+                double l = 0.0, qf = 0.0;
+                for (int w = 0; w < NT / 32; ++w) { l += sm.red[w]; qf += sm.red2[w]; }
+                a.lik[zoff] = k * log(2.0 * M_PI) + k * log(s2) + 2.0 * l + qf / s2;
+            }
+            __syncthreads();
         }
-        ldet = warp_sum(ldet);
-        quad = warp_sum(quad);
-        if (lane == 0) { sm.red[warp] = ldet; sm.red2[warp] = quad; }
-        __syncthreads();
-        if (tid == 0) {
-            double l = 0.0, qf = 0.0;
-            for (int w = 0; w < NT / 32; ++w) { l += sm.red[w]; qf += sm.red2[w]; }
-            a.lik[zoff] = k * log(2.0 * M_PI) + k * log(s2) + 2.0 * l + qf / s2;
-        }
-        __syncthreads();
-    }
 
-    // predict (Eq. 3) and squared errors (Eq. 4)
-    for (int j = warp; j < m; j += NT / 32) {
-        const double px = a.Px[p0 + j], py = a.Py[p0 + j];
-        double s = 0.0;
-        for (int t = lane; t < k; t += 32) s += cov64(px, py, S.sx[t], S.sy[t], rho) * S.al[t];
-        s = warp_sum(s);
-        if (lane == 0) {
-            if (a.yhat) a.yhat[(int64_t)b * a.yhat_stride + p0 + j] = s;
-            if (a.Pv) {
-                const double e = s - a.Pv[p0 + j];
-                S.ep[j] = e * e;
+        // predict (Eq. 3) and squared errors (Eq. 4)
+        for (int j = warp; j < m; j += NT / 32) {
+            const double px = a.Px[p0 + j], py = a.Py[p0 + j];
+            double s = 0.0;
+            for (int t = lane; t < k; t += 32) s += cov64(px, py, S.sx[t], S.sy[t], rho) * S.al[t];
+            s = warp_sum(s);
+            if (lane == 0) {
+                if (a.yhat) a.yhat[(int64_t)(a.rhs ? rh : b) * a.yhat_stride + p0 + j] = s;
+                if (a.Pv) {
+                    const double e = s - a.Pv[p0 + j];
+                    S.ep[j] = e * e;
+                }
             }
         }
-    }
-    __syncthreads();
-    if (a.Pv) {
-        double s = 0.0;
-        for (int j = tid; j < m; j += NT) s += S.ep[j];
-        s = warp_sum(s);
-        if (lane == 0) sm.red[warp] = s;
         __syncthreads();
-        if (tid == 0) {
-            double zz = 0.0;
-            for (int w = 0; w < NT / 32; ++w) zz += sm.red[w];
-            a.z[zoff] = zz;
+        if (a.Pv) {
+            double s = 0.0;
+            for (int j = tid; j < m; j += NT) s += S.ep[j];
+            s = warp_sum(s);
+            if (lane == 0) sm.red[warp] = s;
+            __syncthreads();
+            if (tid == 0) {
+                double zz = 0.0;
+                for (int w = 0; w < NT / 32; ++w) zz += sm.red[w];
+                a.z[zoff] = zz;
+            }
         }
     }
     if (tid == 0) a.tstatus[zoff] = a.task_list ? a.list_status : PCV_OK;

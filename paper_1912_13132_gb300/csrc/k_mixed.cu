@@ -1048,7 +1048,7 @@ __device__ void residual_df(SmemM& sm, const float* tbl, const SlotM& S, int k, 
 
 // ---------------------------------------------------------------- one task
 
-template <bool TC, class Sch = umma::SplitBF16x3>
+template <bool TC, class Sch = umma::SplitBF16x3, bool EXT = false>
 __device__ void run_task(SmemM& sm, SmemKeep& keep, SmemSimt* simt, TcCtx* tc, const TaskArgs& a, int t, int i,
                          int b) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -1187,138 +1187,153 @@ __device__ void run_task(SmemM& sm, SmemKeep& keep, SmemSimt* simt, TcCtx* tc, c
         }
     }
     __syncthreads();
-    if (ok) {
-        // iterative refinement: x += L^-T L^-1 r
-        ok = false;
-        float dprev = 0.0f;
-        for (int it = 0; it <= a.refine_max_iter; ++it) {
-            for (int q = tid; q < k; q += NT) R.w[q] = (float)R.rr[q];
-            __syncthreads();
-            if constexpr (TC) {
-                forward_inv(sm, R.L, ld, R.w, k);
-                backward_inv(sm, R.L, ld, R.w, k);
-            } else {
-                forward32(sm, R.L, ld, R.w, k);
-                backward32(sm, R.L, ld, R.w, k);
-            }
-            tm.lap(kPhSolve);
-            float dmax = 0.0f, xmax = 0.0f;
+    // EXT: the extended variant -- several right-hand sides (one factorisation, each
+    // column refined and predicted) and the local log-likelihood; the plain variant
+    // keeps the CV path's registers to itself
+    const int nrhs = EXT && a.rhs ? a.nrhs : 1;
+    for (int rh = 0; rh < nrhs; ++rh) {
+        if (EXT && a.rhs) {   // this column's values (the factor stays)
             for (int q = tid; q < k; q += NT) {
-                const double xn = R.xs[q] + (double)R.w[q];
-                R.xs[q] = xn;
-                dmax = fmaxf(dmax, fabsf(R.w[q]));
-                xmax = fmaxf(xmax, fabsf((float)xn));
+                const double yv = a.rhs[rh * a.rhs_stride + a.T_idx[t0 + q]];
+                R.yv[q] = yv;
+                R.rr[q] = yv;
+                R.xs[q] = 0.0;
             }
-            dmax = block_max(sm, dmax);
-            xmax = block_max(sm, xmax);
-            if (!(dmax == dmax) || !(xmax == xmax)) {                 // NaN: give up
-                if (a.phase_cycles && tid == 0) atomicAdd(a.phase_cycles + kPhFailNaN, 1ull);
-                break;
-            }
-            if (it >= 1) {
-                if (dmax > 0.5f * dprev) {                             // not contracting
-                    if (a.phase_cycles && tid == 0) atomicAdd(a.phase_cycles + kPhFailStall, 1ull);
+            __syncthreads();
+        }
+        if (ok) {
+            // iterative refinement: x += L^-T L^-1 r
+            ok = false;
+            float dprev = 0.0f;
+            for (int it = 0; it <= a.refine_max_iter; ++it) {
+                for (int q = tid; q < k; q += NT) R.w[q] = (float)R.rr[q];
+                __syncthreads();
+                if constexpr (TC) {
+                    forward_inv(sm, R.L, ld, R.w, k);
+                    backward_inv(sm, R.L, ld, R.w, k);
+                } else {
+                    forward32(sm, R.L, ld, R.w, k);
+                    backward32(sm, R.L, ld, R.w, k);
+                }
+                tm.lap(kPhSolve);
+                float dmax = 0.0f, xmax = 0.0f;
+                for (int q = tid; q < k; q += NT) {
+                    const double xn = R.xs[q] + (double)R.w[q];
+                    R.xs[q] = xn;
+                    dmax = fmaxf(dmax, fabsf(R.w[q]));
+                    xmax = fmaxf(xmax, fabsf((float)xn));
+                }
+                dmax = block_max(sm, dmax);
+                xmax = block_max(sm, xmax);
+                if (!(dmax == dmax) || !(xmax == xmax)) {                 // NaN: give up
+                    if (a.phase_cycles && tid == 0) atomicAdd(a.phase_cycles + kPhFailNaN, 1ull);
                     break;
                 }
-                // error left after this correction ~ |d_i| * (|d_i| / |d_i-1|)
-                const float est = dmax * (dmax / fmaxf(dprev, 1e-30f));
-                if (est <= (float)a.refine_tol * xmax) { ok = true; break; }
+                if (it >= 1) {
+                    if (dmax > 0.5f * dprev) {                             // not contracting
+                        if (a.phase_cycles && tid == 0) atomicAdd(a.phase_cycles + kPhFailStall, 1ull);
+                        break;
+                    }
+                    // error left after this correction ~ |d_i| * (|d_i| / |d_i-1|)
+                    const float est = dmax * (dmax / fmaxf(dprev, 1e-30f));
+                    if (est <= (float)a.refine_tol * xmax) { ok = true; break; }
+                }
+                dprev = dmax;
+                if (it == a.refine_max_iter) break;
+                for (int q = tid; q < k; q += NT) {
+                    const df v = dfm::from_double(R.xs[q]);
+                    R.qh[q] = v.h;
+                    R.ql[q] = v.l;
+                }
+                __syncthreads();
+                residual_df(sm, keep.tbl, R, k, lam);
+                tm.lap(kPhResidual);
+                if (a.phase_cycles && tid == 0) atomicAdd(a.phase_cycles + kPhResidualPasses, 1ull);
             }
-            dprev = dmax;
-            if (it == a.refine_max_iter) break;
-            for (int q = tid; q < k; q += NT) {
-                const df v = dfm::from_double(R.xs[q]);
-                R.qh[q] = v.h;
-                R.ql[q] = v.l;
+            if (k == 0) ok = true;
+        }
+        if (!ok) {
+            // hand the task to the FP64 kernel
+            if (tid == 0) {
+                a.tstatus[zoff] = PCV_REFINE_FALLBACK;
+                const unsigned pos = atomicAdd(a.fb_count, 1u);
+                a.fb_list[pos] = t;
             }
             __syncthreads();
-            residual_df(sm, keep.tbl, R, k, lam);
-            tm.lap(kPhResidual);
-            if (a.phase_cycles && tid == 0) atomicAdd(a.phase_cycles + kPhResidualPasses, 1ull);
+            return;
         }
-        if (k == 0) ok = true;
-    }
-    if (!ok) {
-        // hand the task to the FP64 kernel
-        if (tid == 0) {
-            a.tstatus[zoff] = PCV_REFINE_FALLBACK;
-            const unsigned pos = atomicAdd(a.fb_count, 1u);
-            a.fb_list[pos] = t;
-        }
-        __syncthreads();
-        return;
-    }
 
-    // local -2 log-likelihood (Eq. 2) of the training data: the quadratic form from
-    // the refined solution, the log-determinant from the FP32 factor's diagonal (the
-    // tensor-core engines keep L_JJ^-1 there, whose diagonal is 1 / L_jj)
-    if (a.lik) {
-        double ldet = 0.0, quad = 0.0;
+        // local -2 log-likelihood (Eq. 2) of the training data: the quadratic form from
+        // the refined solution, the log-determinant from the FP32 factor's diagonal (the
+        // tensor-core engines keep L_JJ^-1 there, whose diagonal is 1 / L_jj)
+        if (EXT && a.lik && rh == 0) {
+            double ldet = 0.0, quad = 0.0;
+            for (int q = tid; q < k; q += NT) {
+                const double d = (double)R.L[q + (int64_t)q * ld];
+                ldet += TC ? -log(d) : log(d);
+                quad += R.yv[q] * R.xs[q];
+            }
+            ldet = warp_sum_d(ldet);
+            quad = warp_sum_d(quad);
+            if (lane == 0) {
+                sm.dred[warp] = ldet;
+                sm.dred2[warp] = quad;
+            }
+            __syncthreads();
+            if (tid == 0) {
+                double l = 0.0, qf = 0.0;
+                for (int w = 0; w < NT / 32; ++w) {
+                    l += sm.dred[w];
+                    qf += sm.dred2[w];
+                }
+                a.lik[zoff] = k * log(2.0 * M_PI) + k * log(s2) + 2.0 * l + qf / s2;
+            }
+            __syncthreads();
+        }
+
+        // predict (Eq. 3) in double-float, squared errors in FP64 (Eq. 4)
         for (int q = tid; q < k; q += NT) {
-            const double d = (double)R.L[q + (int64_t)q * ld];
-            ldet += TC ? -log(d) : log(d);
-            quad += R.yv[q] * R.xs[q];
-        }
-        ldet = warp_sum_d(ldet);
-        quad = warp_sum_d(quad);
-        if (lane == 0) {
-            sm.dred[warp] = ldet;
-            sm.dred2[warp] = quad;
+            const df v = dfm::from_double(R.xs[q]);
+            R.qh[q] = v.h;
+            R.ql[q] = v.l;
         }
         __syncthreads();
-        if (tid == 0) {
-            double l = 0.0, qf = 0.0;
-            for (int w = 0; w < NT / 32; ++w) {
-                l += sm.dred[w];
-                qf += sm.dred2[w];
+        for (int j0 = 2 * warp; j0 < m; j0 += 2 * (NT / 32)) {   // two prediction points per warp
+            const int j1 = min(j0 + 1, m - 1);
+            const df px0 = dfm::from_double((a.Px[p0 + j0] - ox) * sc), py0 = dfm::from_double((a.Py[p0 + j0] - oy) * sc);
+            const df px1 = dfm::from_double((a.Px[p0 + j1] - ox) * sc), py1 = dfm::from_double((a.Py[p0 + j1] - oy) * sc);
+            const Pt P0{px0.h, px0.l, py0.h, py0.l}, P1{px1.h, px1.l, py1.h, py1.l};
+            dfm::acc s0, s1;
+            for (int q = lane; q < k; q += 32) {
+                const Pt Q{R.xh[q], R.xl[q], R.yh[q], R.yl[q]};
+                const df xq{R.qh[q], R.ql[q]};
+                s0.add_prod(exp_neg_sm(keep.tbl, t_any(P0, Q)), xq);
+                s1.add_prod(exp_neg_sm(keep.tbl, t_any(P1, Q)), xq);
             }
-            a.lik[zoff] = k * log(2.0 * M_PI) + k * log(s2) + 2.0 * l + qf / s2;
-        }
-        __syncthreads();
-    }
-
-    // predict (Eq. 3) in double-float, squared errors in FP64 (Eq. 4)
-    for (int q = tid; q < k; q += NT) {
-        const df v = dfm::from_double(R.xs[q]);
-        R.qh[q] = v.h;
-        R.ql[q] = v.l;
-    }
-    __syncthreads();
-    for (int j0 = 2 * warp; j0 < m; j0 += 2 * (NT / 32)) {   // two prediction points per warp
-        const int j1 = min(j0 + 1, m - 1);
-        const df px0 = dfm::from_double((a.Px[p0 + j0] - ox) * sc), py0 = dfm::from_double((a.Py[p0 + j0] - oy) * sc);
-        const df px1 = dfm::from_double((a.Px[p0 + j1] - ox) * sc), py1 = dfm::from_double((a.Py[p0 + j1] - oy) * sc);
-        const Pt P0{px0.h, px0.l, py0.h, py0.l}, P1{px1.h, px1.l, py1.h, py1.l};
-        dfm::acc s0, s1;
-        for (int q = lane; q < k; q += 32) {
-            const Pt Q{R.xh[q], R.xl[q], R.yh[q], R.yl[q]};
-            const df xq{R.qh[q], R.ql[q]};
-            s0.add_prod(exp_neg_sm(keep.tbl, t_any(P0, Q)), xq);
-            s1.add_prod(exp_neg_sm(keep.tbl, t_any(P1, Q)), xq);
-        }
-        const double v0 = warp_sum_d((double)s0.h + (double)s0.l);
-        const double v1 = warp_sum_d((double)s1.h + (double)s1.l);
-        if (lane < 2 && (lane == 0 || j1 != j0)) {
-            const int j = lane == 0 ? j0 : j1;
-            const double v = lane == 0 ? v0 : v1;
-            if (a.yhat) a.yhat[(int64_t)b * a.yhat_stride + p0 + j] = v;
-            if (a.Pv) {
-                const double e = v - a.Pv[p0 + j];
-                R.ep[j] = e * e;
+            const double v0 = warp_sum_d((double)s0.h + (double)s0.l);
+            const double v1 = warp_sum_d((double)s1.h + (double)s1.l);
+            if (lane < 2 && (lane == 0 || j1 != j0)) {
+                const int j = lane == 0 ? j0 : j1;
+                const double v = lane == 0 ? v0 : v1;
+                if (a.yhat) a.yhat[(int64_t)(EXT && a.rhs ? rh : b) * a.yhat_stride + p0 + j] = v;
+                if (a.Pv) {
+                    const double e = v - a.Pv[p0 + j];
+                    R.ep[j] = e * e;
+                }
             }
         }
-    }
-    __syncthreads();
-    if (a.Pv) {
-        double s = 0.0;
-        for (int j = tid; j < m; j += NT) s += R.ep[j];
-        s = warp_sum_d(s);
-        if (lane == 0) sm.dred[warp] = s;
         __syncthreads();
-        if (tid == 0) {
-            double zz = 0.0;
-            for (int w = 0; w < NT / 32; ++w) zz += sm.dred[w];
-            a.z[zoff] = zz;
+        if (a.Pv) {
+            double s = 0.0;
+            for (int j = tid; j < m; j += NT) s += R.ep[j];
+            s = warp_sum_d(s);
+            if (lane == 0) sm.dred[warp] = s;
+            __syncthreads();
+            if (tid == 0) {
+                double zz = 0.0;
+                for (int w = 0; w < NT / 32; ++w) zz += sm.dred[w];
+                a.z[zoff] = zz;
+            }
         }
     }
     if (tid == 0) a.tstatus[zoff] = PCV_OK;
@@ -1345,7 +1360,7 @@ __global__ void __launch_bounds__(NT, 2) k_cv_mixed(TaskArgs a) {
         const int t = keep.task;
         __syncthreads();
         if (t >= ntask) break;
-        run_task<false>(sm, keep, &simt, nullptr, a, t, a.order[t / a.B], t % a.B);
+        run_task<false, umma::SplitBF16x3, true>(sm, keep, &simt, nullptr, a, t, a.order[t / a.B], t % a.B);
     }
 }
 
@@ -1368,8 +1383,9 @@ static_assert(2 * tc_smem(kTcRingMin) <= 228 * 1024, "two tensor-core CTAs must 
 static_assert(tc_ring_bytes<umma::SplitBF16x3>(2) == kTcRingMin && tc_ring_bytes<umma::SplitF16x2>(3) == kTcRingMin,
               "default rings of both schemes");
 
-// Tensor-core variant: two CTAs per SM, 256 TMEM columns each; Sch is the operand scheme.
-template <class Sch>
+// Tensor-core variant: two CTAs per SM, 256 TMEM columns each; Sch is the operand scheme,
+// EXT the extended variant (several right-hand sides, local log-likelihood).
+template <class Sch, bool EXT = false>
 __global__ void __launch_bounds__(NT, 2) k_cv_mixed_tc(TaskArgs a, const __grid_constant__ CUtensorMap m0,
                                                        const __grid_constant__ CUtensorMap m1,
                                                        const __grid_constant__ CUtensorMap m2) {
@@ -1411,7 +1427,7 @@ __global__ void __launch_bounds__(NT, 2) k_cv_mixed_tc(TaskArgs a, const __grid_
         const int t = keep.task;
         __syncthreads();
         if (t >= ntask) break;
-        run_task<true, Sch>(sm, keep, nullptr, &tc, a, t, a.order[t / a.B], t % a.B);
+        run_task<true, Sch, EXT>(sm, keep, nullptr, &tc, a, t, a.order[t / a.B], t % a.B);
     }
     umma::tc_fence_before();
     __syncthreads();
@@ -1442,6 +1458,9 @@ int mixed_prepare(int device) {
     if (e != cudaSuccess) return (int)e;
     e = cudaFuncSetAttribute(k_cv_mixed_tc<umma::SplitF16x2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
     if (e != cudaSuccess) return (int)e;
+    e = cudaFuncSetAttribute(k_cv_mixed_tc<umma::SplitF16x2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kTcSmem);
+    if (e != cudaSuccess) return (int)e;
     g_prepared[device] = true;
     return 0;
 }
@@ -1461,7 +1480,11 @@ int launch_task_mixed(const TaskArgs& a, const void* maps, int engine, int grid,
                               : tc_ring_bytes<umma::SplitF16x2>(a.tc_stages);
         if (a.tc_stages < 2 || a.tc_stages > umma::kStages || ring < kTcRingMin || ring > kTcRingMax)
             return (int)cudaErrorInvalidValue;
-        if (bf16)
+        const bool ext = a.rhs || a.lik;
+        if (ext && bf16) return (int)cudaErrorInvalidValue;   // the extended variant: FP16 engine only
+        if (ext)
+            k_cv_mixed_tc<umma::SplitF16x2, true><<<grid, NT, tc_smem(ring), (cudaStream_t)stream>>>(a, m[0], m[1], m[2]);
+        else if (bf16)
             k_cv_mixed_tc<umma::SplitBF16x3><<<grid, NT, tc_smem(ring), (cudaStream_t)stream>>>(a, m[0], m[1], m[2]);
         else
             k_cv_mixed_tc<umma::SplitF16x2><<<grid, NT, tc_smem(ring), (cudaStream_t)stream>>>(a, m[0], m[1], m[2]);

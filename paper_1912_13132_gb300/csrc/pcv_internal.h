@@ -51,6 +51,11 @@ struct TaskArgs {
     double* z;              // B x N local SSPE
     double* lik;            // B x N local -2 log-likelihood (Eq. 2) of the training data, or NULL
     const int32_t* param_row;   // N: parameter row of each subset (overrides the task's b), or NULL
+    // several right-hand sides per task (one factorisation, each column refined and
+    // predicted in turn; yhat row = column): values of column r at rhs[r * rhs_stride + g]
+    const double* rhs;
+    int32_t nrhs;
+    int64_t rhs_stride;
     int32_t* tstatus;       // B x N task status
     double* yhat;           // predictions: yhat[b * yhat_stride + P_off[i] + j], or NULL
     int64_t yhat_stride;

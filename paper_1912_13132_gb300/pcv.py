@@ -75,6 +75,7 @@ _SIGS = {
     "pcv_neg2loglik": (ctypes.c_int, [_vp, _dp, ctypes.c_int32, ctypes.c_int32, _dp, _dp, _i32p, _vp]),
     "pcv_predict_local": (ctypes.c_int, [_vp, _dp, ctypes.c_int32, _dp, _dp, ctypes.c_int64, ctypes.c_int32, _dp,
                                          _i32p, _vp]),
+    "pcv_gls": (ctypes.c_int, [_vp, _dp, ctypes.c_int32, _dp, ctypes.c_int32, _dp, _vp]),
     "pcv_set_timing": (ctypes.c_int, [_vp, ctypes.c_int32]),
     "pcv_kernel_time": (ctypes.c_int, [_vp, _dp, _dp]),
     "pcv_phase_cycles": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_uint64), ctypes.c_int32]),
@@ -305,6 +306,19 @@ class Context:
         if per is not None:
             out["per_subset"] = per
         return out
+
+    def gls(self, X, params3, precision="mixed", stream=None) -> np.ndarray:
+        """pcv_gls: GLS coefficients of the covariates X (n x p, a row per input point)."""
+        Xc = _f64(X)
+        if Xc.ndim == 1:
+            Xc = Xc.reshape(-1, 1)
+        Xc = np.ascontiguousarray(Xc)
+        p = Xc.shape[1]
+        pr = _f64(params3).reshape(3)
+        beta = np.empty(p)
+        _check(_lib.pcv_gls(self._h, _ptr(Xc, _dp), p, _ptr(pr, _dp), PRECISIONS[precision], _ptr(beta, _dp),
+                            _stream_ptr(stream)), "pcv_gls")
+        return beta
 
     def predict_local(self, params, sspe_per_subset, xy_new, precision="mixed", stream=None):
         """pcv_predict_local: predictions with each subset's locally best row of params;

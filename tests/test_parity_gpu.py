@@ -341,3 +341,23 @@ def test_predict_local_best(gpu_lib, prec):
         worst = max(worst, e)
         assert e <= TOL[prec]["pred"], (i, e)
     print("predict_local", prec, sorted(set(best.tolist())), worst)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_gls_mean(gpu_lib, prec):
+    """GLS coefficients of a linear mean (Sec. 5) from prediction operations on the
+    covariate columns, against the oracle's same parallel approximation: FP64 within
+    1e-9, mixed within 1e-5 relative (max norm); a planted trend is recovered."""
+    w = datagen.config_uniform_4096()
+    n = len(w.v)
+    X = np.stack([np.ones(n), w.xy[:, 0], w.xy[:, 1], w.xy[:, 0] * w.xy[:, 1]], 1)
+    beta_true = np.array([1.5, -2.0, 0.7, 1.0])
+    v = w.v + X @ beta_true
+    param = (1.0, 0.1, 0.05)
+    with gpu_lib.Context(w.xy, v, w.role, w.layout) as ctx:
+        beta = ctx.gls(X, param, precision=prec)
+    ref = oracle.gls(w.xy, v, w.role, w.layout, X, param)
+    err = np.max(np.abs(beta - ref)) / np.max(np.abs(ref))
+    assert err <= (1e-9 if prec == "fp64" else 1e-5), (beta, ref)
+    assert np.allclose(beta, beta_true, atol=1.0)
+    print("gls", prec, beta.tolist(), err)
