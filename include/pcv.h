@@ -392,6 +392,15 @@ const char* pcv_status_str(int32_t status);
 const char* pcv_last_error(void);
 int32_t pcv_version(void);
 
+/* 1 if every input point lies on one regular lattice (x0 + i hx, y0 + j hy for
+ * integers i, j, within 1e-6 of the spacing), with the spacings; 0 otherwise.  On
+ * lattice data the mixed path's CV loss takes each covariance from a per-task table
+ * indexed by the lattice offsets (|di|, |dj|), computed once per task in FP64, instead
+ * of evaluating the exponential per matrix entry; the distances are then those of the
+ * exact lattice, which differ from the FP64 coordinates' by their rounding (~1e-13
+ * relative). */
+int32_t pcv_lattice(const pcv_ctx* ctx, double* hx, double* hy);
+
 /* Number of kernels of this library launched by the calling thread since the
  * last reset (for launch accounting in benchmarks); reset when reset != 0. */
 int64_t pcv_launch_count(int32_t reset);

@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cfloat>
 #include <cmath>
 #include <cstring>
 #include <memory>
@@ -83,6 +84,11 @@ struct pcv_ctx {
     DevBuf<int64_t> Toff, Voff;
     DevBuf<int32_t> Tidx;
     DevBuf<double> Vx, Vy, Vv;              // validation points in membership order
+    // lattice data: all points at integer multiples of (lat_hx, lat_hy) from one origin
+    bool lattice = false;
+    double lat_hx = 0.0, lat_hy = 0.0;
+    int64_t lat_cap = 0;                    // largest covariance table of a subset (entries)
+    DevBuf<int32_t> LX, LY, VLX, VLY;       // lattice indices of all points and of the validation points
     DevBuf<int32_t> order;                  // subsets with validation data, longest first
     int32_t n_active = 0;
     int32_t kmax = 0;
@@ -155,7 +161,8 @@ void workspace_shape(const pcv_ctx* c, int wi, int64_t& g, int64_t& sb, int64_t&
     ld = round_up(c->kmax, 128);
     const int planes = prec == PCV_PREC_MIXED ? pcv::mixed_planes(c->opts.factor_engine) : 0;
     const bool tensor = planes > 0;
-    sb = prec == PCV_PREC_FP64 ? pcv::slot_bytes_fp64(ld, c->mmax) : pcv::slot_bytes_mixed(ld, c->mmax);
+    sb = prec == PCV_PREC_FP64 ? pcv::slot_bytes_fp64(ld, c->mmax)
+                               : pcv::slot_bytes_mixed(ld, c->mmax, c->lattice ? c->lat_cap : 0);
     pb = (int64_t)planes * ld * ld * 2;   // 16-bit planes per slot
     // CTAs per SM: two for both mixed engines (the tensor engine holds half of an
     // SM's tensor memory per CTA), one for the FP64 kernel
@@ -194,6 +201,39 @@ pcv_status ensure_workspace(pcv_ctx* c, int wi) {
 }
 
 bool bad_precision(int32_t p) { return p != PCV_PREC_FP64 && p != PCV_PREC_MIXED; }
+
+// Whether the values v all lie on v0 + i h for integers 0 <= i < 2^31, h the smallest
+// gap between distinct values refined over the whole range.  The slack is a few FP64
+// ulps of the largest coordinate (16 eps (max|v| / h + steps) in units of h): snapping a
+// point to its lattice node then moves it no more than the rounding of its coordinate
+// already did, so the tabulated covariances equal the exact ones to FP64 input accuracy.
+bool lattice_axis(const std::vector<double>& v, double& v0, double& h, std::vector<int32_t>& idx) {
+    std::vector<double> u(v);
+    std::sort(u.begin(), u.end());
+    u.erase(std::unique(u.begin(), u.end()), u.end());
+    idx.assign(v.size(), 0);
+    if (u.empty()) return false;
+    v0 = u[0];
+    if (u.size() == 1) {
+        h = 1.0;
+        return true;
+    }
+    double g = INFINITY;
+    for (size_t q = 1; q < u.size(); ++q) g = std::min(g, u[q] - u[q - 1]);
+    if (!(g > 0.0)) return false;
+    const double span = u.back() - u[0];
+    const double steps = std::nearbyint(span / g);
+    if (!(steps >= 1.0) || steps > 2147483647.0) return false;
+    h = span / steps;
+    const double tol = 16.0 * DBL_EPSILON * (std::max(std::fabs(u.front()), std::fabs(u.back())) / h + steps);
+    for (size_t q = 0; q < v.size(); ++q) {
+        const double t = (v[q] - v0) / h;
+        const double r = std::nearbyint(t);
+        if (!(std::fabs(t - r) <= tol) || r < 0.0 || r > 2147483647.0) return false;
+        idx[q] = (int32_t)r;
+    }
+    return true;
+}
 
 }  // namespace
 
@@ -376,6 +416,42 @@ PCV_API pcv_status pcv_create(const double* xy, const double* v, const uint8_t* 
     c->coord_scale = wmax > 0.0 ? std::ldexp(1.0, -std::ilogb(wmax) - 1) : 1.0;
     CUDA_TRY(c->order.reserve(ord.size()));
     if (!ord.empty()) CUDA_TRY(cudaMemcpy(c->order.p, ord.data(), ord.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    // lattice data: covariances then depend on the index offsets only, and the mixed
+    // path tabulates them per task (the largest table over the subsets sizes the slots)
+    {
+        double x0 = 0.0, y0 = 0.0;
+        std::vector<int32_t> ix, iy;
+        if (n > 0 && lattice_axis(hx, x0, c->lat_hx, ix) && lattice_axis(hy, y0, c->lat_hy, iy)) {
+            int64_t cap = 0;
+            for (int32_t i : ord) {
+                int32_t a0 = INT32_MAX, a1 = INT32_MIN, b0 = INT32_MAX, b1 = INT32_MIN;
+                auto take = [&](int64_t j) {
+                    a0 = std::min(a0, ix[j]); a1 = std::max(a1, ix[j]);
+                    b0 = std::min(b0, iy[j]); b1 = std::max(b1, iy[j]);
+                };
+                for (int64_t q = P.T_off[i]; q < P.T_off[i + 1]; ++q) take(P.T_idx[q]);
+                for (int64_t q = P.V_off[i]; q < P.V_off[i + 1]; ++q) take(P.V_idx[q]);
+                if (a1 >= a0) cap = std::max<int64_t>(cap, (int64_t)(a1 - a0 + 1) * (b1 - b0 + 1));
+            }
+            // tables up to 2^21 entries (16 MB per slot); beyond that the general path
+            if (cap > 0 && cap <= (1 << 21)) {
+                c->lattice = true;
+                c->lat_cap = cap;
+                std::vector<int32_t> vix(nV), viy(nV);
+                for (int64_t q = 0; q < nV; ++q) { vix[q] = ix[P.V_idx[q]]; viy[q] = iy[P.V_idx[q]]; }
+                CUDA_TRY(c->LX.reserve(n));
+                CUDA_TRY(c->LY.reserve(n));
+                CUDA_TRY(c->VLX.reserve(nV));
+                CUDA_TRY(c->VLY.reserve(nV));
+                CUDA_TRY(cudaMemcpy(c->LX.p, ix.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice));
+                CUDA_TRY(cudaMemcpy(c->LY.p, iy.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice));
+                if (nV) {
+                    CUDA_TRY(cudaMemcpy(c->VLX.p, vix.data(), nV * sizeof(int32_t), cudaMemcpyHostToDevice));
+                    CUDA_TRY(cudaMemcpy(c->VLY.p, viy.data(), nV * sizeof(int32_t), cudaMemcpyHostToDevice));
+                }
+            }
+        }
+    }
     CUDA_TRY(c->counter.reserve(1));
     *out = c.release();
     return PCV_OK;
@@ -391,7 +467,7 @@ static pcv_status run_tasks(pcv_ctx* c, const double* d_params, int32_t B, int32
                             const double* Px, const double* Py, const double* Pv, const int32_t* order,
                             int32_t n_order, double* d_yhat, int64_t yhat_stride, void* stream,
                             bool want_lik = false, const int32_t* d_param_row = nullptr,
-                            const double* d_rhs = nullptr, int32_t nrhs = 0) {
+                            const double* d_rhs = nullptr, int32_t nrhs = 0, bool lattice = false) {
     const int32_t N = c->plan.N;
     CUDA_TRY(c->z.reserve((size_t)B * N));
     CUDA_TRY(c->tst.reserve((size_t)B * N));
@@ -437,6 +513,17 @@ static pcv_status run_tasks(pcv_ctx* c, const double* d_params, int32_t B, int32
     a.rhs = d_rhs;
     a.nrhs = nrhs;
     a.rhs_stride = (int64_t)c->plan.n;
+    // the slots hold the lattice table whenever the data are a lattice; the lattice
+    // variant runs where the prediction points are lattice points too (the CV loss)
+    a.lat_cap = c->lattice ? c->lat_cap : 0;
+    if (lattice && c->lattice) {
+        a.LX = c->LX.p;
+        a.LY = c->LY.p;
+        a.PLX = c->VLX.p;
+        a.PLY = c->VLY.p;
+        a.lat_hx = c->lat_hx;
+        a.lat_hy = c->lat_hy;
+    }
     a.tstatus = c->tst.p;
     a.yhat = d_yhat;
     a.yhat_stride = yhat_stride;
@@ -490,7 +577,7 @@ PCV_API pcv_status pcv_cv_loss_device(pcv_ctx* c, const double* d_params, int32_
     if (bad_precision(prec)) return fail(PCV_ERR_ARG, "unknown precision");
     CUDA_TRY(cudaSetDevice(c->device));
     pcv_status st = run_tasks(c, d_params, B, prec, c->Voff.p, c->Vx.p, c->Vy.p, c->Vv.p, c->order.p, c->n_active,
-                              d_yhat_valid, c->nV, stream);
+                              d_yhat_valid, c->nV, stream, false, nullptr, nullptr, 0, true);
     if (st != PCV_OK) return st;
     const int32_t N = c->plan.N;
     if (c->timing) CUDA_TRY(cudaEventRecord(c->ev[2], (cudaStream_t)stream));
@@ -876,3 +963,10 @@ PCV_API const char* pcv_status_str(int32_t s) {
 PCV_API const char* pcv_last_error(void) { return g_err.c_str(); }
 
 PCV_API int32_t pcv_version(void) { return 1; }
+
+PCV_API int32_t pcv_lattice(const pcv_ctx* c, double* hx, double* hy) {
+    if (!c || !c->lattice) return 0;
+    if (hx) *hx = c->lat_hx;
+    if (hy) *hy = c->lat_hy;
+    return 1;
+}

@@ -19,6 +19,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <mutex>
 
@@ -68,6 +69,7 @@ struct SlotM {
     float* w;      // solve vector
     float *qh, *ql;             // solution in double-float
     float *ah, *al;             // residual accumulators
+    float2* tab;                // lattice data: covariance table (hi, lo) by index offset
 };
 
 __device__ __forceinline__ SlotM slot_of(const TaskArgs& a) {
@@ -89,8 +91,9 @@ __device__ __forceinline__ SlotM slot_of(const TaskArgs& a) {
     s.ql = f + 6 * ld;
     s.ah = f + 7 * ld;
     s.al = f + 8 * ld;
-    // ep is placed after the float arrays (its length is mmax, not ld)
-    s.ep = reinterpret_cast<double*>(f + 9 * ld);
+    // then the lattice table (a.lat_cap entries), then ep (its length is mmax, not ld)
+    s.tab = reinterpret_cast<float2*>(f + 9 * ld);
+    s.ep = reinterpret_cast<double*>(s.tab + a.lat_cap);
     return s;
 }
 
@@ -103,6 +106,7 @@ struct alignas(16) SmemM {
     float wj[2 * NB];              // solve block (128 entries in the tensor-core kernel)
     double dred[NT / 32];
     double dred2[NT / 32];
+    int ired[4][NT / 32];
     float fred[NT / 32];
     int flag;
 };
@@ -849,17 +853,22 @@ __device__ void forward_inv(SmemM& sm, const float* L, int64_t ld, float* w, int
         }
         __syncthreads();
         if (jb == TBs) {
-            for (int r = j0 + TBs + tid; r < k; r += NT) {
-                const float* Lr = L + r + (int64_t)j0 * ld;
-                float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
+            // two rows per thread, so that twice the loads of the streamed factor are in flight
+            for (int r = j0 + TBs + tid; r < k; r += 2 * NT) {
+                const int r2 = r + NT < k ? r + NT : r;
+                const float* La = L + r + (int64_t)j0 * ld;
+                const float* Lb = L + r2 + (int64_t)j0 * ld;
+                float s0 = 0.0f, s1 = 0.0f, t0 = 0.0f, t1 = 0.0f;
 #pragma unroll 8
-                for (int c = 0; c < TBs; c += 4) {
-                    s0 = fmaf(Lr[(int64_t)c * ld], sm.wj[c], s0);
-                    s1 = fmaf(Lr[(int64_t)(c + 1) * ld], sm.wj[c + 1], s1);
-                    s2 = fmaf(Lr[(int64_t)(c + 2) * ld], sm.wj[c + 2], s2);
-                    s3 = fmaf(Lr[(int64_t)(c + 3) * ld], sm.wj[c + 3], s3);
+                for (int c = 0; c < TBs; c += 2) {
+                    const float w0 = sm.wj[c], w1 = sm.wj[c + 1];
+                    s0 = fmaf(La[(int64_t)c * ld], w0, s0);
+                    s1 = fmaf(La[(int64_t)(c + 1) * ld], w1, s1);
+                    t0 = fmaf(Lb[(int64_t)c * ld], w0, t0);
+                    t1 = fmaf(Lb[(int64_t)(c + 1) * ld], w1, t1);
                 }
-                w[r] -= (s0 + s1) + (s2 + s3);
+                w[r] -= s0 + s1;
+                if (r2 != r) w[r2] -= t0 + t1;
             }
         }
         __syncthreads();
@@ -882,12 +891,12 @@ __device__ void backward_inv(SmemM& sm, const float* L, int64_t ld, float* w, in
             for (int q = 0; q < 16; ++q) s[q] = 0.0f;
             if (jb == TBs) {
                 int p = j0 + TBs + lane;
-                for (; p + 32 < k; p += 64) {   // two rows per lane in flight
-                    const float w0 = w[p], w1 = w[p + 32];
+                for (; p + 96 < k; p += 128) {   // four rows per lane in flight
+                    const float w0 = w[p], w1 = w[p + 32], w2 = w[p + 64], w3 = w[p + 96];
 #pragma unroll
                     for (int q = 0; q < 16; ++q) {
                         const float* Lq = L + (int64_t)(j0 + c0 + q) * ld;
-                        s[q] = fmaf(Lq[p], w0, fmaf(Lq[p + 32], w1, s[q]));
+                        s[q] = fmaf(Lq[p], w0, fmaf(Lq[p + 32], w1, fmaf(Lq[p + 64], w2, fmaf(Lq[p + 96], w3, s[q]))));
                     }
                 }
                 for (; p < k; p += 32) {
@@ -957,9 +966,20 @@ __device__ __forceinline__ df exp_neg_sm(const float* tbl, df t) {
     return dfm::exp_neg(t, tbl, c_exp.inv_c, c_exp.c1, c_exp.c2, c_exp.c3);
 }
 
+// Lattice data: a point's lattice indices travel in the high-part slots of Pt (xh, yh)
+// as integer bits, and the covariance of two points is the task's table entry at their
+// index offsets (|di|, |dj|), a (hi, lo) pair of floats.
+__device__ __forceinline__ df lat_cov(const float2* tab, int W, const Pt& p, const Pt& q) {
+    const int di = abs(__float_as_int(p.xh) - __float_as_int(q.xh));
+    const int dj = abs(__float_as_int(p.yh) - __float_as_int(q.yh));
+    const float2 e = __ldg(&tab[di * W + dj]);
+    return df{e.x, e.y};
+}
+
 // r = y - A x with A = Sigma + lambda I: double-float entries, one pass over the
 // lower triangle in 64 x 64 tiles, each entry feeding its row and its column.
-__device__ void residual_df(SmemM& sm, const float* tbl, const SlotM& S, int k, double lam) {
+template <bool LAT = false>
+__device__ void residual_df(SmemM& sm, const float* tbl, const SlotM& S, int k, double lam, int W = 0) {
     const int tid = threadIdx.x;
     const int rg = tid >> 4, cg = tid & 15;   // 16 x 16 threads, 4 x 4 entries each
     for (int a = tid; a < k; a += NT) { S.ah[a] = 0.0f; S.al[a] = 0.0f; }
@@ -993,7 +1013,9 @@ __device__ void residual_df(SmemM& sm, const float* tbl, const SlotM& S, int k, 
                 for (int v = 0; v < 4; ++v) {
                     const int a = I * NB + rg * 4 + u, b = J * NB + cg * 4 + v;
                     if (a < k && b < k && (I != J || a > b)) {
-                        const df e = exp_neg_sm(tbl, t_grid(pa[u], pb[v]));
+                        df e;
+                        if constexpr (LAT) e = lat_cov(S.tab, W, pa[u], pb[v]);
+                        else e = exp_neg_sm(tbl, t_grid(pa[u], pb[v]));
                         racc[u].add_prod(e, xb[v]);
                         cacc[v].add_prod(e, xa[u]);
                     }
@@ -1048,7 +1070,7 @@ __device__ void residual_df(SmemM& sm, const float* tbl, const SlotM& S, int k, 
 
 // ---------------------------------------------------------------- one task
 
-template <bool TC, class Sch = umma::SplitBF16x3, bool EXT = false>
+template <bool TC, class Sch = umma::SplitBF16x3, bool EXT = false, bool LAT = false>
 __device__ void run_task(SmemM& sm, SmemKeep& keep, SmemSimt* simt, TcCtx* tc, const TaskArgs& a, int t, int i,
                          int b) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -1080,79 +1102,170 @@ __device__ void run_task(SmemM& sm, SmemKeep& keep, SmemSimt* simt, TcCtx* tc, c
     // power-of-two grid fine enough that differences of high parts are exact floats
     const double sc = 1.0 / rho;
     const double ox = k > 0 ? a.X[a.T_idx[t0]] : 0.0, oy = k > 0 ? a.Y[a.T_idx[t0]] : 0.0;
-    float omax = 0.0f;
-    for (int q = tid; q < k; q += NT) {
-        const int g = a.T_idx[t0 + q];
-        omax = fmaxf(omax, (float)fmax(fabs(a.X[g] - ox), fabs(a.Y[g] - oy)));
-    }
-    omax = block_max(sm, omax) * (float)sc * 1.0001f;
-    // |offset| < 2^eb, grid 2^-(21 - eb): high parts and their differences need <= 23 bits
-    const int eb = max(0, ilogbf(fmaxf(omax, 1.0f)) + 1);
-    const double qscale = exp2((double)(21 - eb)), iqscale = exp2((double)(eb - 21));
-
-    // gather
-#pragma unroll 4
-    for (int q = tid; q < k; q += NT) {
-        const int g = a.T_idx[t0 + q];
-        const double dx = (a.X[g] - ox) * sc, dy = (a.Y[g] - oy) * sc;
-        const double hx = rint(dx * qscale) * iqscale, hy = rint(dy * qscale) * iqscale;
-        S.xh[q] = (float)hx;
-        S.xl[q] = (float)(dx - hx);
-        S.yh[q] = (float)hy;
-        S.yl[q] = (float)(dy - hy);
-        S.yv[q] = a.Vals[g];
-        S.xs[q] = 0.0;
-        S.rr[q] = a.Vals[g];
-    }
-    __syncthreads();
-
-    // FP32 lower triangle of Sigma + lambda I (the tensor-core kernel reads the
-    // coordinates from shared memory: the operand ring is idle before the factorisation)
-    const float *cxh = S.xh, *cxl = S.xl, *cyh = S.yh, *cyl = S.yl;
-    if constexpr (TC) {
-        if ((size_t)4 * ld * sizeof(float) <= (size_t)tc_ring_bytes<Sch>(a.tc_stages)) {
-            float* f = reinterpret_cast<float*>(tc->stages);
-            for (int q = tid; q < k; q += NT) {
-                f[q] = S.xh[q];
-                f[ld + q] = S.xl[q];
-                f[2 * ld + q] = S.yh[q];
-                f[3 * ld + q] = S.yl[q];
-            }
-            cxh = f;
-            cxl = f + ld;
-            cyh = f + 2 * ld;
-            cyl = f + 3 * ld;
-            __syncthreads();
+    int W = 0;              // lattice data: row length of the covariance table
+    bool lat_ok = true;
+    if constexpr (LAT) {
+        // lattice indices of the training points, carried as integer bits in the
+        // high-part coordinate slots, and the index extents over the training and the
+        // prediction points
+        int e4[4] = {INT_MAX, INT_MIN, INT_MAX, INT_MIN};
+        for (int q = tid; q < k; q += NT) {
+            const int g = a.T_idx[t0 + q];
+            const int ii = a.LX[g], jj = a.LY[g];
+            S.xh[q] = __int_as_float(ii);
+            S.yh[q] = __int_as_float(jj);
+            S.yv[q] = a.Vals[g];
+            S.xs[q] = 0.0;
+            S.rr[q] = a.Vals[g];
+            e4[0] = min(e4[0], ii); e4[1] = max(e4[1], ii); e4[2] = min(e4[2], jj); e4[3] = max(e4[3], jj);
         }
-    }
-    const float lam32 = (float)lam;
-    const int nb = (k + NB - 1) / NB;
-    for (int bj = 0; bj < nb; ++bj)
-        for (int bi = bj; bi < nb; ++bi) {
-            const int r = bi * NB + (tid & (NB - 1));     // fixed row per thread within a tile
-            if (r >= k) continue;
-            const float rxh = cxh[r], rxl = cxl[r], ryh = cyh[r], ryl = cyl[r];
-            for (int cc = tid >> 6; cc < NB; cc += NT / NB) {
-                const int c = bj * NB + cc;
-                if (c > r) break;
-                float v = 1.0f + lam32;
-                if (r != c) {
-                    const float dx = (rxh - cxh[c]) + (rxl - cxl[c]);
-                    const float dy = (ryh - cyh[c]) + (ryl - cyl[c]);
-                    // the FP32 matrix only preconditions the refinement, so the hardware
-                    // approximations of the root and the exponential serve (a few ulp)
-                    const float d2 = fmaf(dx, dx, dy * dy);
-                    v = __expf(-(d2 > 0.0f ? d2 * rsqrtf(d2) : 0.0f));
+        for (int j = tid; j < m; j += NT) {
+            const int ii = a.PLX[p0 + j], jj = a.PLY[p0 + j];
+            e4[0] = min(e4[0], ii); e4[1] = max(e4[1], ii); e4[2] = min(e4[2], jj); e4[3] = max(e4[3], jj);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            e4[0] = min(e4[0], __shfl_xor_sync(0xffffffffu, e4[0], o));
+            e4[1] = max(e4[1], __shfl_xor_sync(0xffffffffu, e4[1], o));
+            e4[2] = min(e4[2], __shfl_xor_sync(0xffffffffu, e4[2], o));
+            e4[3] = max(e4[3], __shfl_xor_sync(0xffffffffu, e4[3], o));
+        }
+        if (lane == 0)
+            for (int u = 0; u < 4; ++u) sm.ired[u][warp] = e4[u];
+        __syncthreads();
+        for (int w = 0; w < NT / 32; ++w) {
+            e4[0] = min(e4[0], sm.ired[0][w]); e4[1] = max(e4[1], sm.ired[1][w]);
+            e4[2] = min(e4[2], sm.ired[2][w]); e4[3] = max(e4[3], sm.ired[3][w]);
+        }
+        const int H = e4[1] >= e4[0] ? e4[1] - e4[0] + 1 : 1;
+        W = e4[3] >= e4[2] ? e4[3] - e4[2] + 1 : 1;
+        lat_ok = (int64_t)H * W <= a.lat_cap;
+        // the task's covariances by index offset, in FP64 (a few thousand entries)
+        if (lat_ok)
+            for (int e = tid; e < H * W; e += NT) {
+                const double dx = (double)(e / W) * a.lat_hx, dy = (double)(e % W) * a.lat_hy;
+                const double v = exp(-sqrt(dx * dx + dy * dy) / rho);
+                const float hi = (float)v;
+                S.tab[e] = make_float2(hi, (float)(v - (double)hi));
+            }
+        __syncthreads();
+        // FP32 lower triangle of Sigma + lambda I from the table's high parts (indices
+        // staged in shared memory: the operand ring is idle before the factorisation)
+        const int* ti = reinterpret_cast<const int*>(S.xh);
+        const int* tj = reinterpret_cast<const int*>(S.yh);
+        if constexpr (TC) {
+            if ((size_t)2 * ld * sizeof(int) <= (size_t)tc_ring_bytes<Sch>(a.tc_stages)) {
+                int* f = reinterpret_cast<int*>(tc->stages);
+                for (int q = tid; q < k; q += NT) {
+                    f[q] = __float_as_int(S.xh[q]);
+                    f[ld + q] = __float_as_int(S.yh[q]);
                 }
-                S.L[r + (int64_t)c * ld] = v;
+                ti = f;
+                tj = f + ld;
+                __syncthreads();
             }
         }
-    __syncthreads();
+        const float lam32 = (float)lam;
+        const int nb = (k + NB - 1) / NB;
+        const float2* __restrict__ tab = S.tab;
+        constexpr int CPT = NB / (NT / NB);     // columns per thread in a 64 x 64 tile
+        if (lat_ok)
+            for (int bj = 0; bj < nb; ++bj)
+                for (int bi = bj; bi < nb; ++bi) {
+                    const int r = bi * NB + (tid & (NB - 1));
+                    if (r >= k) continue;
+                    const int ri = ti[r], rj = tj[r];
+                    // all of the row's lookups first (independent loads in flight), then the stores
+                    float v[CPT];
+#pragma unroll
+                    for (int u = 0; u < CPT; ++u) {
+                        const int c = bj * NB + (tid >> 6) + u * (NT / NB);
+                        v[u] = c < r ? __ldg(&tab[abs(ri - ti[c]) * W + abs(rj - tj[c])]).x : 1.0f + lam32;
+                    }
+#pragma unroll
+                    for (int u = 0; u < CPT; ++u) {
+                        const int c = bj * NB + (tid >> 6) + u * (NT / NB);
+                        if (c <= r) S.L[r + (int64_t)c * ld] = v[u];
+                    }
+                }
+        __syncthreads();
+    } else {
+        float omax = 0.0f;
+        for (int q = tid; q < k; q += NT) {
+            const int g = a.T_idx[t0 + q];
+            omax = fmaxf(omax, (float)fmax(fabs(a.X[g] - ox), fabs(a.Y[g] - oy)));
+        }
+        omax = block_max(sm, omax) * (float)sc * 1.0001f;
+        // |offset| < 2^eb, grid 2^-(21 - eb): high parts and their differences need <= 23 bits
+        const int eb = max(0, ilogbf(fmaxf(omax, 1.0f)) + 1);
+        const double qscale = exp2((double)(21 - eb)), iqscale = exp2((double)(eb - 21));
+
+        // gather
+    #pragma unroll 4
+        for (int q = tid; q < k; q += NT) {
+            const int g = a.T_idx[t0 + q];
+            const double dx = (a.X[g] - ox) * sc, dy = (a.Y[g] - oy) * sc;
+            const double hx = rint(dx * qscale) * iqscale, hy = rint(dy * qscale) * iqscale;
+            S.xh[q] = (float)hx;
+            S.xl[q] = (float)(dx - hx);
+            S.yh[q] = (float)hy;
+            S.yl[q] = (float)(dy - hy);
+            S.yv[q] = a.Vals[g];
+            S.xs[q] = 0.0;
+            S.rr[q] = a.Vals[g];
+        }
+        __syncthreads();
+
+        // FP32 lower triangle of Sigma + lambda I (the tensor-core kernel reads the
+        // coordinates from shared memory: the operand ring is idle before the factorisation)
+        const float *cxh = S.xh, *cxl = S.xl, *cyh = S.yh, *cyl = S.yl;
+        if constexpr (TC) {
+            if ((size_t)4 * ld * sizeof(float) <= (size_t)tc_ring_bytes<Sch>(a.tc_stages)) {
+                float* f = reinterpret_cast<float*>(tc->stages);
+                for (int q = tid; q < k; q += NT) {
+                    f[q] = S.xh[q];
+                    f[ld + q] = S.xl[q];
+                    f[2 * ld + q] = S.yh[q];
+                    f[3 * ld + q] = S.yl[q];
+                }
+                cxh = f;
+                cxl = f + ld;
+                cyh = f + 2 * ld;
+                cyl = f + 3 * ld;
+                __syncthreads();
+            }
+        }
+        const float lam32 = (float)lam;
+        const int nb = (k + NB - 1) / NB;
+        for (int bj = 0; bj < nb; ++bj)
+            for (int bi = bj; bi < nb; ++bi) {
+                const int r = bi * NB + (tid & (NB - 1));     // fixed row per thread within a tile
+                if (r >= k) continue;
+                const float rxh = cxh[r], rxl = cxl[r], ryh = cyh[r], ryl = cyl[r];
+                for (int cc = tid >> 6; cc < NB; cc += NT / NB) {
+                    const int c = bj * NB + cc;
+                    if (c > r) break;
+                    float v = 1.0f + lam32;
+                    if (r != c) {
+                        const float dx = (rxh - cxh[c]) + (rxl - cxl[c]);
+                        const float dy = (ryh - cyh[c]) + (ryl - cyl[c]);
+                        // the FP32 matrix only preconditions the refinement, so the hardware
+                        // approximations of the root and the exponential serve (a few ulp)
+                        const float d2 = fmaf(dx, dx, dy * dy);
+                        v = __expf(-(d2 > 0.0f ? d2 * rsqrtf(d2) : 0.0f));
+                    }
+                    S.L[r + (int64_t)c * ld] = v;
+                }
+            }
+        __syncthreads();
+    }
 
     tm.lap(kPhGather);
-    bool ok;
-    if constexpr (TC) ok = factor_tc<Sch>(*tc, S, k, ld, a.phase_cycles);
-    else ok = factor32(sm, *simt, S, k, ld);
+    bool ok = false;
+    if (lat_ok) {
+        if constexpr (TC) ok = factor_tc<Sch>(*tc, S, k, ld, a.phase_cycles);
+        else ok = factor32(sm, *simt, S, k, ld);
+    }
     tm.t = a.phase_cycles ? now_cycles() : 0;
     if constexpr (!TC) tm.lap(kPhFactorSimt);
     // refinement and prediction work on per-task vectors; in the tensor-core kernel the
@@ -1246,7 +1359,7 @@ __device__ void run_task(SmemM& sm, SmemKeep& keep, SmemSimt* simt, TcCtx* tc, c
                     R.ql[q] = v.l;
                 }
                 __syncthreads();
-                residual_df(sm, keep.tbl, R, k, lam);
+                residual_df<LAT>(sm, keep.tbl, R, k, lam, W);
                 tm.lap(kPhResidual);
                 if (a.phase_cycles && tid == 0) atomicAdd(a.phase_cycles + kPhResidualPasses, 1ull);
             }
@@ -1300,15 +1413,27 @@ __device__ void run_task(SmemM& sm, SmemKeep& keep, SmemSimt* simt, TcCtx* tc, c
         __syncthreads();
         for (int j0 = 2 * warp; j0 < m; j0 += 2 * (NT / 32)) {   // two prediction points per warp
             const int j1 = min(j0 + 1, m - 1);
-            const df px0 = dfm::from_double((a.Px[p0 + j0] - ox) * sc), py0 = dfm::from_double((a.Py[p0 + j0] - oy) * sc);
-            const df px1 = dfm::from_double((a.Px[p0 + j1] - ox) * sc), py1 = dfm::from_double((a.Py[p0 + j1] - oy) * sc);
-            const Pt P0{px0.h, px0.l, py0.h, py0.l}, P1{px1.h, px1.l, py1.h, py1.l};
+            Pt P0, P1;
+            if constexpr (LAT) {
+                P0 = Pt{__int_as_float(a.PLX[p0 + j0]), 0.0f, __int_as_float(a.PLY[p0 + j0]), 0.0f};
+                P1 = Pt{__int_as_float(a.PLX[p0 + j1]), 0.0f, __int_as_float(a.PLY[p0 + j1]), 0.0f};
+            } else {
+                const df px0 = dfm::from_double((a.Px[p0 + j0] - ox) * sc), py0 = dfm::from_double((a.Py[p0 + j0] - oy) * sc);
+                const df px1 = dfm::from_double((a.Px[p0 + j1] - ox) * sc), py1 = dfm::from_double((a.Py[p0 + j1] - oy) * sc);
+                P0 = Pt{px0.h, px0.l, py0.h, py0.l};
+                P1 = Pt{px1.h, px1.l, py1.h, py1.l};
+            }
             dfm::acc s0, s1;
             for (int q = lane; q < k; q += 32) {
                 const Pt Q{R.xh[q], R.xl[q], R.yh[q], R.yl[q]};
                 const df xq{R.qh[q], R.ql[q]};
-                s0.add_prod(exp_neg_sm(keep.tbl, t_any(P0, Q)), xq);
-                s1.add_prod(exp_neg_sm(keep.tbl, t_any(P1, Q)), xq);
+                if constexpr (LAT) {
+                    s0.add_prod(lat_cov(R.tab, W, P0, Q), xq);
+                    s1.add_prod(lat_cov(R.tab, W, P1, Q), xq);
+                } else {
+                    s0.add_prod(exp_neg_sm(keep.tbl, t_any(P0, Q)), xq);
+                    s1.add_prod(exp_neg_sm(keep.tbl, t_any(P1, Q)), xq);
+                }
             }
             const double v0 = warp_sum_d((double)s0.h + (double)s0.l);
             const double v1 = warp_sum_d((double)s1.h + (double)s1.l);
@@ -1384,8 +1509,9 @@ static_assert(tc_ring_bytes<umma::SplitBF16x3>(2) == kTcRingMin && tc_ring_bytes
               "default rings of both schemes");
 
 // Tensor-core variant: two CTAs per SM, 256 TMEM columns each; Sch is the operand scheme,
-// EXT the extended variant (several right-hand sides, local log-likelihood).
-template <class Sch, bool EXT = false>
+// EXT the extended variant (several right-hand sides, local log-likelihood), LAT the
+// lattice-data variant (covariances from a per-task table by index offset).
+template <class Sch, bool EXT = false, bool LAT = false>
 __global__ void __launch_bounds__(NT, 2) k_cv_mixed_tc(TaskArgs a, const __grid_constant__ CUtensorMap m0,
                                                        const __grid_constant__ CUtensorMap m1,
                                                        const __grid_constant__ CUtensorMap m2) {
@@ -1427,7 +1553,7 @@ __global__ void __launch_bounds__(NT, 2) k_cv_mixed_tc(TaskArgs a, const __grid_
         const int t = keep.task;
         __syncthreads();
         if (t >= ntask) break;
-        run_task<true, Sch, EXT>(sm, keep, nullptr, &tc, a, t, a.order[t / a.B], t % a.B);
+        run_task<true, Sch, EXT, LAT>(sm, keep, nullptr, &tc, a, t, a.order[t / a.B], t % a.B);
     }
     umma::tc_fence_before();
     __syncthreads();
@@ -1439,8 +1565,8 @@ bool g_prepared[64] = {false};
 
 }  // namespace
 
-int64_t slot_bytes_mixed(int32_t ld, int64_t mmax) {
-    const int64_t b = (int64_t)ld * ld * 4 + 3 * (int64_t)ld * 8 + 9 * (int64_t)ld * 4 + (mmax + 32) * 8;
+int64_t slot_bytes_mixed(int32_t ld, int64_t mmax, int64_t lat_cap) {
+    const int64_t b = (int64_t)ld * ld * 4 + 3 * (int64_t)ld * 8 + 9 * (int64_t)ld * 4 + lat_cap * 8 + (mmax + 32) * 8;
     return (b + 255) / 256 * 256;
 }
 
@@ -1460,6 +1586,9 @@ int mixed_prepare(int device) {
     if (e != cudaSuccess) return (int)e;
     e = cudaFuncSetAttribute(k_cv_mixed_tc<umma::SplitF16x2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              kTcSmem);
+    if (e != cudaSuccess) return (int)e;
+    e = cudaFuncSetAttribute(k_cv_mixed_tc<umma::SplitF16x2, false, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
     if (e != cudaSuccess) return (int)e;
     g_prepared[device] = true;
     return 0;
@@ -1484,6 +1613,9 @@ int launch_task_mixed(const TaskArgs& a, const void* maps, int engine, int grid,
         if (ext && bf16) return (int)cudaErrorInvalidValue;   // the extended variant: FP16 engine only
         if (ext)
             k_cv_mixed_tc<umma::SplitF16x2, true><<<grid, NT, tc_smem(ring), (cudaStream_t)stream>>>(a, m[0], m[1], m[2]);
+        else if (a.LX && !bf16)
+            k_cv_mixed_tc<umma::SplitF16x2, false, true>
+                <<<grid, NT, tc_smem(ring), (cudaStream_t)stream>>>(a, m[0], m[1], m[2]);
         else if (bf16)
             k_cv_mixed_tc<umma::SplitBF16x3><<<grid, NT, tc_smem(ring), (cudaStream_t)stream>>>(a, m[0], m[1], m[2]);
         else

@@ -77,6 +77,15 @@ struct TaskArgs {
     // plane_elems elements laid out as (slot * ld + row) * ld + column
     void* planes;
     int64_t plane_elems;
+    // lattice data (every point at integer multiples of lat_hx, lat_hy from a common
+    // origin): lattice indices of all points (LX, LY) and of the prediction points (PLX,
+    // PLY), and per slot a table of lat_cap covariances indexed by the index offsets
+    const int32_t* LX;
+    const int32_t* LY;
+    const int32_t* PLX;
+    const int32_t* PLY;
+    double lat_hx, lat_hy;
+    int64_t lat_cap;
     // optional per-phase cycle counters (kPhaseCount entries, summed over CTAs), or NULL
     unsigned long long* phase_cycles;
     int32_t tc_stages;      // TMA ring depth of the tensor-core kernel (2 or 3)
@@ -99,7 +108,7 @@ bool mixed_make_maps(void* planes, int64_t plane_elems, int32_t ld, int grid, in
 constexpr int kMixedEngineTensor = 0, kMixedEngineSimt = 1, kMixedEngineTensorBF16 = 2;
 int mixed_planes(int engine);           // 16-bit planes of the engine's operand scheme (0: none)
 int mixed_default_stages(int engine);   // default operand-ring depth of a tensor engine
-int64_t slot_bytes_mixed(int32_t ld, int64_t mmax);
+int64_t slot_bytes_mixed(int32_t ld, int64_t mmax, int64_t lat_cap = 0);
 int mixed_prepare(int device);   // one-time per-device set-up of the mixed path
 
 // Fixed-order sum of the local SSPEs of each configuration, plus its status.

@@ -98,6 +98,7 @@ _SIGS = {
     "pcv_last_error": (ctypes.c_char_p, []),
     "pcv_version": (ctypes.c_int32, []),
     "pcv_launch_count": (ctypes.c_int64, [ctypes.c_int32]),
+    "pcv_lattice": (ctypes.c_int32, [_vp, _dp, _dp]),
 }
 EXPORTS = tuple(_SIGS)
 
@@ -284,6 +285,11 @@ class Context:
     PHASES = ("gather_assemble", "tc_update", "diag", "panel_solve", "diag_io", "factor_simt", "solves",
               "residual", "predict_loss", "task", "residual_passes", "tasks", "fail_factor", "fail_nan",
               "fail_stall")
+
+    def lattice(self):
+        """(hx, hy) when every point lies on one regular lattice, else None (pcv_lattice)."""
+        hx, hy = ctypes.c_double(), ctypes.c_double()
+        return (hx.value, hy.value) if _lib.pcv_lattice(self._h, ctypes.byref(hx), ctypes.byref(hy)) else None
 
     def phase_cycles(self, reset: bool = False) -> dict:
         """Per-phase SM cycles of the mixed kernel (see include/pcv.h)."""

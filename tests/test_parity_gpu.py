@@ -361,3 +361,42 @@ def test_gls_mean(gpu_lib, prec):
     assert err <= (1e-9 if prec == "fp64" else 1e-5), (beta, ref)
     assert np.allclose(beta, beta_true, atol=1.0)
     print("gls", prec, beta.tolist(), err)
+
+
+def test_lattice_path(gpu_lib):
+    """Lattice data (every point on one regular grid): the mixed CV loss takes its
+    covariances from per-task tables by lattice offset.  The detection, parity with the
+    oracle on every subset, and agreement with the general path (the same data with one
+    point moved off the lattice by 1e-9)."""
+    w = datagen.config_grid_1m(rho=0.05, tau2=0.02, fine=256, cells=32, buf=8, n_valid=2048, seed=77)
+    P = np.array([[1.0, 0.05, 0.02], [0.7, 0.12, 0.005]])
+    with gpu_lib.Context(w.xy, w.v, w.role, w.layout) as ctx:
+        lat = ctx.lattice()
+        out = ctx.cv_loss(P, precision="mixed", per_subset=True, predictions=True)
+        V_off = ctx.V_off.copy()
+    assert lat is not None and abs(lat[0] - 1 / 256) < 1e-15 and abs(lat[1] - 1 / 256) < 1e-15
+    assert np.all(out["status"] == 0)
+    members = oracle.all_members(w.xy, w.role, w.layout)
+    ref = oracle.cv_loss(w.xy, w.v, w.role, w.layout, P, members=members)
+    worst = compare(out, ref, V_off, range(len(members)), len(P), "mixed")
+    xy2 = w.xy.copy()
+    xy2[5, 0] += 1e-9                      # one IGNORE-free point off the lattice
+    with gpu_lib.Context(xy2, w.v, w.role, w.layout) as ctx2:
+        assert ctx2.lattice() is None
+        out2 = ctx2.cv_loss(P, precision="mixed")
+    assert np.all(np.abs(out2["sspe"] - out["sspe"]) <= 1e-6 * np.abs(out["sspe"]))
+    # a whole grid column shifted by 1e-7 of the spacing keeps every gap near h, but
+    # is off the lattice by far more than coordinate rounding: no snapping, and the
+    # general path matches the oracle on the shifted data
+    xy3 = w.xy.copy()
+    col = np.isclose(xy3[:, 0], np.unique(xy3[:, 0])[100], rtol=0, atol=1e-12)
+    assert col.sum() > 0
+    xy3[col, 0] += 1e-7 / 256
+    with gpu_lib.Context(xy3, w.v, w.role, w.layout) as ctx3:
+        assert ctx3.lattice() is None
+        out3 = ctx3.cv_loss(P, precision="mixed", per_subset=True, predictions=True)
+        V_off3 = ctx3.V_off.copy()
+    members3 = oracle.all_members(xy3, w.role, w.layout)
+    ref3 = oracle.cv_loss(xy3, w.v, w.role, w.layout, P, members=members3)
+    worst3 = compare(out3, ref3, V_off3, range(len(members3)), len(P), "mixed")
+    print("lattice", worst, "shifted column", worst3)
