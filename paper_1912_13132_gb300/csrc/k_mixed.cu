@@ -120,6 +120,7 @@ struct alignas(16) SmemSimt {
 // Shared memory kept for the whole kernel.
 struct alignas(8) SmemKeep {
     float tbl[2 * dfm::kExpTable]; // exp table (copy of c_exp.tbl)
+    float fwj[2 * NB];             // w_J of the forward solve fused into the factorisation
     int task;
 };
 
@@ -509,8 +510,15 @@ constexpr int kDiagBytes = kDiagRedOff + (NT / 32) * 4;
 // keeps L_JJ^-1 (zeros above its diagonal) in place of each diagonal block: the
 // solves multiply by it instead of substituting.  False if a pivot is not positive
 // or a bounded wait ran out.
+// With fw (the right-hand side, k floats) the first forward solve w <- L^-1 w runs
+// inside the factorisation: after the diagonal block, w_J <- L_JJ^-1 w_J (the panels
+// of earlier block columns have already subtracted their part), and the panel's
+// epilogue, which holds each row of L[below, J], subtracts L[r, J] w_J from w_r.  The
+// factor is then not streamed for that solve.  fwj: 128 floats of shared memory
+// outside the operand ring.
 template <class Sch>
-__device__ bool factor_tc(TcCtx& tc, const SlotM& S, int k, int64_t ld, unsigned long long* clk) {
+__device__ bool factor_tc(TcCtx& tc, const SlotM& S, int k, int64_t ld, unsigned long long* clk,
+                          float* fw = nullptr, float* fwj = nullptr) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     PhaseTimer tm(clk);
     // the operand ring was written through the generic proxy since the last update
@@ -611,6 +619,26 @@ __device__ bool factor_tc(TcCtx& tc, const SlotM& S, int k, int64_t ld, unsigned
         // L_JJ^-1 in place; the FP32 factor keeps the inverse in the diagonal block's
         // place (the triangular solves multiply by it), zeros above its diagonal
         trinv128(D, rinv, Y);
+        if (fw) {
+            // w_J <- L_JJ^-1 w_J from the inverse in shared memory (two threads per row,
+            // 64 columns each, partial sums through the free Y scratch)
+            if (tid < TB) fwj[tid] = tid < jb ? fw[j0 + tid] : 0.0f;
+            __syncthreads();
+            const int r = tid & (TB - 1), h = tid >> 7;
+            float s0 = 0.0f, s1 = 0.0f;
+#pragma unroll 8
+            for (int c = 64 * h; c < 64 * h + 64; c += 2) {
+                s0 = fmaf(c <= r ? D[r][c] : 0.0f, fwj[c], s0);
+                s1 = fmaf(c + 1 <= r ? D[r][c + 1] : 0.0f, fwj[c + 1], s1);
+            }
+            Y[tid] = s0 + s1;
+            __syncthreads();
+            if (tid < TB) {
+                const float v = Y[tid] + Y[tid + TB];
+                fwj[tid] = tid < jb ? v : 0.0f;
+                if (tid < jb) fw[j0 + tid] = v;
+            }
+        }
         tm.lap(kPhDiag);
 #pragma unroll
         for (int i = 0; i < TB * TB / 4 / NT; ++i) {
@@ -660,6 +688,7 @@ __device__ bool factor_tc(TcCtx& tc, const SlotM& S, int k, int64_t ld, unsigned
         {
             auto epi = [&](int row0, int quad, uint32_t taddr) {
                 const int r = row0 + quad * 32 + (threadIdx.x & 31);
+                float acc = 0.0f;   // L[r, J] w_J of the fused forward solve
 #pragma unroll 1
                 for (int c0 = 0; c0 < TB; c0 += 32) {
                     float v[32];
@@ -671,11 +700,16 @@ __device__ bool factor_tc(TcCtx& tc, const SlotM& S, int k, int64_t ld, unsigned
                             v[j] *= up;
                             Lr[(int64_t)j * ld] = v[j];
                         }
+                        if (fw) {
+#pragma unroll
+                            for (int j = 0; j < 32; ++j) acc = fmaf(v[j], fwj[c0 + j], acc);
+                        }
                         const int64_t off = plane_off(r, j0 + c0, ld);
 #pragma unroll
                         for (int g = 0; g < 4; ++g) store_planes8<Sch>(tc, off + 8 * g, v + 8 * g);
                     }
                 }
+                if (fw && r < k) fw[r] -= acc;
             };
             const bool ok = tc.sh->dead == 0 &&
                             umma::block_column<true, kTcTilesPerPass, Sch>(tc.sh->pipe, tc.ph, tc.stages, tc.m0, tc.m1, tc.m2,
@@ -1262,8 +1296,15 @@ __device__ void run_task(SmemM& sm, SmemKeep& keep, SmemSimt* simt, TcCtx* tc, c
 
     tm.lap(kPhGather);
     bool ok = false;
+    // the tensor-core factorisation also makes the first forward solve of the data
+    // (not of the extended variant's right-hand-side columns)
+    const bool fuse_fw = TC && !(EXT && a.rhs);
     if (lat_ok) {
-        if constexpr (TC) ok = factor_tc<Sch>(*tc, S, k, ld, a.phase_cycles);
+        if constexpr (TC) {
+            if (fuse_fw)
+                for (int q = tid; q < k; q += NT) S.w[q] = (float)S.rr[q];
+            ok = factor_tc<Sch>(*tc, S, k, ld, a.phase_cycles, fuse_fw ? S.w : nullptr, keep.fwj);
+        }
         else ok = factor32(sm, *simt, S, k, ld);
     }
     tm.t = a.phase_cycles ? now_cycles() : 0;
@@ -1319,10 +1360,16 @@ __device__ void run_task(SmemM& sm, SmemKeep& keep, SmemSimt* simt, TcCtx* tc, c
             ok = false;
             float dprev = 0.0f;
             for (int it = 0; it <= a.refine_max_iter; ++it) {
-                for (int q = tid; q < k; q += NT) R.w[q] = (float)R.rr[q];
+                const bool fused = fuse_fw && it == 0 && rh == 0;   // L^-1 y came with the factor
+                if (fused) {
+                    if (R.w != S.w)
+                        for (int q = tid; q < k; q += NT) R.w[q] = S.w[q];
+                } else {
+                    for (int q = tid; q < k; q += NT) R.w[q] = (float)R.rr[q];
+                }
                 __syncthreads();
                 if constexpr (TC) {
-                    forward_inv(sm, R.L, ld, R.w, k);
+                    if (!fused) forward_inv(sm, R.L, ld, R.w, k);
                     backward_inv(sm, R.L, ld, R.w, k);
                 } else {
                     forward32(sm, R.L, ld, R.w, k);
