@@ -20,6 +20,7 @@
 
 #include <algorithm>
 #include <climits>
+#include <cstddef>
 #include <cmath>
 #include <mutex>
 
@@ -100,7 +101,6 @@ __device__ __forceinline__ SlotM slot_of(const TaskArgs& a) {
 // Shared memory used phase by phase (in the tensor-core kernel it lives in the
 // operand ring, which is idle outside the trailing updates).
 struct alignas(16) SmemM {
-    float L[NB][NB + 1];           // diagonal block
     float rinv[NB];                // reciprocals of the diagonal of L_JJ
     float ph[16][NB], pl[16][NB];  // residual partial sums (double-float)
     float wj[2 * NB];              // solve block (128 entries in the tensor-core kernel)
@@ -109,6 +109,8 @@ struct alignas(16) SmemM {
     int ired[4][NT / 32];
     float fred[NT / 32];
     int flag;
+    float L[NB][NB + 1];           // diagonal block of the FP32 engine (last: the tensor-core
+                                   // kernel, which never uses it, puts vectors in its place)
 };
 
 // Trailing-update staging of the FP32 engine (read with float4 loads).
@@ -1006,7 +1008,7 @@ __device__ __forceinline__ df exp_neg_sm(const float* tbl, df t) {
 __device__ __forceinline__ df lat_cov(const float2* tab, int W, const Pt& p, const Pt& q) {
     const int di = abs(__float_as_int(p.xh) - __float_as_int(q.xh));
     const int dj = abs(__float_as_int(p.yh) - __float_as_int(q.yh));
-    const float2 e = __ldg(&tab[di * W + dj]);
+    const float2 e = tab[di * W + dj];   // the table may sit in shared memory
     return df{e.x, e.y};
 }
 
@@ -1027,7 +1029,7 @@ __device__ void residual_df(SmemM& sm, const float* tbl, const SlotM& S, int k, 
         for (int u = 0; u < 4; ++u) {
             const int a = I * NB + rg * 4 + u;
             const bool ok = a < k;
-            pa[u] = ok ? Pt{S.xh[a], S.xl[a], S.yh[a], S.yl[a]} : Pt{0, 0, 0, 0};
+            pa[u] = ok ? Pt{S.xh[a], LAT ? 0.0f : S.xl[a], S.yh[a], LAT ? 0.0f : S.yl[a]} : Pt{0, 0, 0, 0};
             xa[u] = ok ? df{S.qh[a], S.ql[a]} : df{0, 0};
         }
         for (int J = 0; J <= I; ++J) {
@@ -1038,7 +1040,7 @@ __device__ void residual_df(SmemM& sm, const float* tbl, const SlotM& S, int k, 
             for (int v = 0; v < 4; ++v) {
                 const int b = J * NB + cg * 4 + v;
                 const bool ok = b < k;
-                pb[v] = ok ? Pt{S.xh[b], S.xl[b], S.yh[b], S.yl[b]} : Pt{0, 0, 0, 0};
+                pb[v] = ok ? Pt{S.xh[b], LAT ? 0.0f : S.xl[b], S.yh[b], LAT ? 0.0f : S.yl[b]} : Pt{0, 0, 0, 0};
                 xb[v] = ok ? df{S.qh[b], S.ql[b]} : df{0, 0};
             }
 #pragma unroll
@@ -1136,7 +1138,7 @@ __device__ void run_task(SmemM& sm, SmemKeep& keep, SmemSimt* simt, TcCtx* tc, c
     // power-of-two grid fine enough that differences of high parts are exact floats
     const double sc = 1.0 / rho;
     const double ox = k > 0 ? a.X[a.T_idx[t0]] : 0.0, oy = k > 0 ? a.Y[a.T_idx[t0]] : 0.0;
-    int W = 0;              // lattice data: row length of the covariance table
+    int W = 0, H = 0;       // lattice data: row length and rows of the covariance table
     bool lat_ok = true;
     if constexpr (LAT) {
         // lattice indices of the training points, carried as integer bits in the
@@ -1171,7 +1173,7 @@ __device__ void run_task(SmemM& sm, SmemKeep& keep, SmemSimt* simt, TcCtx* tc, c
             e4[0] = min(e4[0], sm.ired[0][w]); e4[1] = max(e4[1], sm.ired[1][w]);
             e4[2] = min(e4[2], sm.ired[2][w]); e4[3] = max(e4[3], sm.ired[3][w]);
         }
-        const int H = e4[1] >= e4[0] ? e4[1] - e4[0] + 1 : 1;
+        H = e4[1] >= e4[0] ? e4[1] - e4[0] + 1 : 1;
         W = e4[3] >= e4[2] ? e4[3] - e4[2] + 1 : 1;
         lat_ok = (int64_t)H * W <= a.lat_cap;
         // the task's covariances by index offset, in FP64 (a few thousand entries)
@@ -1313,13 +1315,48 @@ __device__ void run_task(SmemM& sm, SmemKeep& keep, SmemSimt* simt, TcCtx* tc, c
     // operand ring is idle from here on, so they move to shared memory when they fit
     if (!ok && a.phase_cycles && tid == 0) atomicAdd(a.phase_cycles + kPhFailFactor, 1ull);
     SlotM R = S;
-    if constexpr (TC) {
+    if constexpr (TC && LAT) {
+        // lattice data: the residual and the prediction read the index vectors, the
+        // solution and the task's covariance table (no low coordinate parts); then the
+        // solve vector and the accumulators as room allows
+        const size_t head = (offsetof(SmemM, L) + 15) / 16 * 16;
+        const size_t room = (size_t)tc_ring_bytes<Sch>(a.tc_stages) - head;
+        const size_t vec = (size_t)ld * sizeof(float);
+        const size_t tabb = ((size_t)H * W * sizeof(float2) + 15) / 16 * 16;
+        if (ok && room >= 4 * vec + tabb) {
+            float* f = reinterpret_cast<float*>(tc->stages + head);
+            R.xh = f;
+            R.yh = f + ld;
+            R.qh = f + 2 * ld;
+            R.ql = f + 3 * ld;
+            R.tab = reinterpret_cast<float2*>(f + 4 * ld);
+            float* g = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(R.tab) + tabb);
+            size_t left = room - 4 * vec - tabb;
+            if (left >= vec) {
+                R.w = g;
+                g += ld;
+                left -= vec;
+            }
+            if (left >= 2 * vec) {
+                R.ah = g;
+                R.al = g + ld;
+            }
+            for (int q = tid; q < k; q += NT) {
+                R.xh[q] = S.xh[q];
+                R.yh[q] = S.yh[q];
+            }
+            for (int e = tid; e < H * W; e += NT) R.tab[e] = S.tab[e];
+            __syncthreads();
+        }
+    } else if constexpr (TC) {
         // as many of the vectors as fit, most used first: coordinates and solution
-        // (residual and prediction), then the solve vector, then the accumulators
-        const size_t room = (size_t)tc_ring_bytes<Sch>(a.tc_stages) - sizeof(SmemM);
+        // (residual and prediction), then the solve vector, then the accumulators; the
+        // vectors start at SmemM's FP32-engine block, unused by this kernel
+        const size_t head = (offsetof(SmemM, L) + 15) / 16 * 16;
+        const size_t room = (size_t)tc_ring_bytes<Sch>(a.tc_stages) - head;
         const size_t vec = (size_t)ld * sizeof(float);
         if (ok && room >= 6 * vec) {
-            float* f = reinterpret_cast<float*>(tc->stages + sizeof(SmemM));
+            float* f = reinterpret_cast<float*>(tc->stages + head);
             R.xh = f;
             R.xl = f + ld;
             R.yh = f + 2 * ld;
@@ -1472,7 +1509,7 @@ __device__ void run_task(SmemM& sm, SmemKeep& keep, SmemSimt* simt, TcCtx* tc, c
             }
             dfm::acc s0, s1;
             for (int q = lane; q < k; q += 32) {
-                const Pt Q{R.xh[q], R.xl[q], R.yh[q], R.yl[q]};
+                const Pt Q{R.xh[q], LAT ? 0.0f : R.xl[q], R.yh[q], LAT ? 0.0f : R.yl[q]};
                 const df xq{R.qh[q], R.ql[q]};
                 if constexpr (LAT) {
                     s0.add_prod(lat_cov(R.tab, W, P0, Q), xq);
