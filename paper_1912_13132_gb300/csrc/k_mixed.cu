@@ -113,6 +113,11 @@ struct alignas(16) SmemM {
                                    // kernel, which never uses it, puts vectors in its place)
 };
 
+// the tensor-core forward solve reduces through ph and pl as one 2 x 8 x 128 buffer
+static_assert(offsetof(SmemM, pl) == offsetof(SmemM, ph) + 16 * NB * sizeof(float) && NT / 32 == 8 &&
+                  2 * 16 * NB >= 2 * (NT / 32) * (2 * NB) && offsetof(SmemM, ph) % 16 == 0,
+              "forward-solve reduction buffers");
+
 // Trailing-update staging of the FP32 engine (read with float4 loads).
 struct alignas(16) SmemSimt {
     float Ta[KC][NB + 4];
@@ -858,7 +863,7 @@ __device__ void backward32(SmemM& sm, const float* L, int64_t ld, float* w, int 
 // rows below take w[r] -= L[r, J] w_J.
 __device__ void forward_inv(SmemM& sm, const float* L, int64_t ld, float* w, int k) {
     constexpr int TBs = 2 * NB;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     float* part = &sm.ph[0][0];
     const int nb = (k + TBs - 1) / TBs;
     for (int J = 0; J < nb; ++J) {
@@ -889,22 +894,43 @@ __device__ void forward_inv(SmemM& sm, const float* L, int64_t ld, float* w, int
         }
         __syncthreads();
         if (jb == TBs) {
-            // two rows per thread, so that twice the loads of the streamed factor are in flight
-            for (int r = j0 + TBs + tid; r < k; r += 2 * NT) {
-                const int r2 = r + NT < k ? r + NT : r;
-                const float* La = L + r + (int64_t)j0 * ld;
-                const float* Lb = L + r2 + (int64_t)j0 * ld;
-                float s0 = 0.0f, s1 = 0.0f, t0 = 0.0f, t1 = 0.0f;
-#pragma unroll 8
-                for (int c = 0; c < TBs; c += 2) {
-                    const float w0 = sm.wj[c], w1 = sm.wj[c + 1];
-                    s0 = fmaf(La[(int64_t)c * ld], w0, s0);
-                    s1 = fmaf(La[(int64_t)(c + 1) * ld], w1, s1);
-                    t0 = fmaf(Lb[(int64_t)c * ld], w0, t0);
-                    t1 = fmaf(Lb[(int64_t)(c + 1) * ld], w1, t1);
+            // rows below in chunks of 128: warp wp takes columns 16 wp .. 16 wp + 15, lane l
+            // rows 4 l .. 4 l + 3 of the chunk as one float4 per column (the factor is
+            // column-major), all sixteen loads in flight; the warps' partial sums meet in
+            // shared memory (two buffers, one barrier per chunk).  A float4 that starts
+            // below k stays inside the column (ld is a multiple of 128); its rows past k
+            // are never written back.
+            const int c0 = warp * 16;
+            float* red = &sm.ph[0][0];          // 2 x 8 x 128 floats (ph and pl)
+            float wc[16];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) wc[q] = sm.wj[c0 + q];
+            int buf = 0;
+            for (int rc = j0 + TBs; rc < k; rc += TBs, buf ^= 1) {
+                const int r = rc + 4 * lane;
+                float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                if (r < k) {
+                    float4 l4[16];
+#pragma unroll
+                    for (int q = 0; q < 16; ++q)
+                        l4[q] = *reinterpret_cast<const float4*>(L + r + (int64_t)(j0 + c0 + q) * ld);
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) {
+                        acc.x = fmaf(l4[q].x, wc[q], acc.x);
+                        acc.y = fmaf(l4[q].y, wc[q], acc.y);
+                        acc.z = fmaf(l4[q].z, wc[q], acc.z);
+                        acc.w = fmaf(l4[q].w, wc[q], acc.w);
+                    }
                 }
-                w[r] -= s0 + s1;
-                if (r2 != r) w[r2] -= t0 + t1;
+                *reinterpret_cast<float4*>(red + buf * (8 * TBs) + warp * TBs + 4 * lane) = acc;
+                __syncthreads();
+                if (tid < TBs && rc + tid < k) {
+                    const float* rb = red + buf * (8 * TBs) + tid;
+                    float v = 0.0f;
+#pragma unroll
+                    for (int g = 0; g < 8; ++g) v += rb[g * TBs];
+                    w[rc + tid] -= v;
+                }
             }
         }
         __syncthreads();
@@ -926,16 +952,22 @@ __device__ void backward_inv(SmemM& sm, const float* L, int64_t ld, float* w, in
 #pragma unroll
             for (int q = 0; q < 16; ++q) s[q] = 0.0f;
             if (jb == TBs) {
-                int p = j0 + TBs + lane;
-                for (; p + 96 < k; p += 128) {   // four rows per lane in flight
-                    const float w0 = w[p], w1 = w[p + 32], w2 = w[p + 64], w3 = w[p + 96];
+                // lane l takes rows 4 l .. 4 l + 3 of each 128-row chunk as one float4 per
+                // column (sixteen 16-byte loads in flight), whole float4s below k only;
+                // the last rows (fewer than four) one by one
+                const int rb = j0 + TBs, nq = (k - rb) >> 2;
+                for (int ch = lane; ch < nq; ch += 32) {
+                    const int p = rb + 4 * ch;
+                    const float4 wv = *reinterpret_cast<const float4*>(w + p);
+                    float4 l4[16];
 #pragma unroll
-                    for (int q = 0; q < 16; ++q) {
-                        const float* Lq = L + (int64_t)(j0 + c0 + q) * ld;
-                        s[q] = fmaf(Lq[p], w0, fmaf(Lq[p + 32], w1, fmaf(Lq[p + 64], w2, fmaf(Lq[p + 96], w3, s[q]))));
-                    }
+                    for (int q = 0; q < 16; ++q)
+                        l4[q] = *reinterpret_cast<const float4*>(L + p + (int64_t)(j0 + c0 + q) * ld);
+#pragma unroll
+                    for (int q = 0; q < 16; ++q)
+                        s[q] = fmaf(l4[q].x, wv.x, fmaf(l4[q].y, wv.y, fmaf(l4[q].z, wv.z, fmaf(l4[q].w, wv.w, s[q]))));
                 }
-                for (; p < k; p += 32) {
+                for (int p = rb + 4 * nq + lane; p < k; p += 32) {
                     const float wp = w[p];
 #pragma unroll
                     for (int q = 0; q < 16; ++q) s[q] = fmaf(L[p + (int64_t)(j0 + c0 + q) * ld], wp, s[q]);
