@@ -517,15 +517,28 @@ constexpr int kDiagBytes = kDiagRedOff + (NT / 32) * 4;
 // keeps L_JJ^-1 (zeros above its diagonal) in place of each diagonal block: the
 // solves multiply by it instead of substituting.  False if a pivot is not positive
 // or a bounded wait ran out.
+// LAT (lattice data): entries of A below the diagonal blocks were not assembled; the
+// update epilogue and the first block column take them from the covariance table by
+// index offset (the same FP32 values the assembly would have stored).
 // With fw (the right-hand side, k floats) the first forward solve w <- L^-1 w runs
 // inside the factorisation: after the diagonal block, w_J <- L_JJ^-1 w_J (the panels
 // of earlier block columns have already subtracted their part), and the panel's
 // epilogue, which holds each row of L[below, J], subtracts L[r, J] w_J from w_r.  The
 // factor is then not streamed for that solve.  fwj: 128 floats of shared memory
 // outside the operand ring.
-template <class Sch>
+struct LatView {
+    const float2* tab;   // covariance table (hi, lo) by index offset, rows of length W
+    const int* ti;       // lattice indices of the training points
+    const int* tj;
+    int W;
+    __device__ __forceinline__ float a(int ri, int rj, int c) const {
+        return tab[abs(ri - ti[c]) * W + abs(rj - tj[c])].x;
+    }
+};
+
+template <class Sch, bool LAT = false>
 __device__ bool factor_tc(TcCtx& tc, const SlotM& S, int k, int64_t ld, unsigned long long* clk,
-                          float* fw = nullptr, float* fwj = nullptr) {
+                          float* fw = nullptr, float* fwj = nullptr, LatView lv = LatView{}) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     PhaseTimer tm(clk);
     // the operand ring was written through the generic proxy since the last update
@@ -555,8 +568,17 @@ __device__ bool factor_tc(TcCtx& tc, const SlotM& S, int k, int64_t ld, unsigned
                             for (int j = 0; j < 32; ++j)
                                 if (c0 + j < jb) Lr[(int64_t)j * ld] -= v[j];
                         } else {
+                            if constexpr (LAT) {
+                                const int ri = lv.ti[r], rj = lv.tj[r];
+                                float av[32];
 #pragma unroll
-                            for (int j = 0; j < 32; ++j) v[j] = Lr[(int64_t)j * ld] - v[j];
+                                for (int j = 0; j < 32; ++j) av[j] = lv.a(ri, rj, j0 + c0 + j);
+#pragma unroll
+                                for (int j = 0; j < 32; ++j) v[j] = av[j] - v[j];
+                            } else {
+#pragma unroll
+                                for (int j = 0; j < 32; ++j) v[j] = Lr[(int64_t)j * ld] - v[j];
+                            }
                             const int64_t off = plane_off(r, j0 + c0, ld);
 #pragma unroll
                             for (int g = 0; g < 4; ++g) store_planes8<Sch>(tc, off + 8 * g, v + 8 * g);
@@ -576,8 +598,14 @@ __device__ bool factor_tc(TcCtx& tc, const SlotM& S, int k, int64_t ld, unsigned
             for (int e = tid; e < (k - TB) * (TB / 8); e += NT) {
                 const int r = TB + e % (k - TB), g = e / (k - TB);
                 float x[8];
+                if constexpr (LAT) {
+                    const int ri = lv.ti[r], rj = lv.tj[r];
 #pragma unroll
-                for (int q = 0; q < 8; ++q) x[q] = L[r + (int64_t)(g * 8 + q) * ld];
+                    for (int q = 0; q < 8; ++q) x[q] = lv.a(ri, rj, g * 8 + q);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) x[q] = L[r + (int64_t)(g * 8 + q) * ld];
+                }
                 store_planes8<Sch>(tc, plane_off(r, g * 8, ld), x);
             }
             tm.lap(kPhDiagIO);
@@ -1218,7 +1246,9 @@ __device__ void run_task(SmemM& sm, SmemKeep& keep, SmemSimt* simt, TcCtx* tc, c
             }
         __syncthreads();
         // FP32 lower triangle of Sigma + lambda I from the table's high parts (indices
-        // staged in shared memory: the operand ring is idle before the factorisation)
+        // staged in shared memory: the operand ring is idle before the factorisation);
+        // the tensor-core factorisation reads the entries below its 128 x 128 diagonal
+        // blocks from the table itself, so only those blocks are stored
         const int* ti = reinterpret_cast<const int*>(S.xh);
         const int* tj = reinterpret_cast<const int*>(S.yh);
         if constexpr (TC) {
@@ -1239,7 +1269,7 @@ __device__ void run_task(SmemM& sm, SmemKeep& keep, SmemSimt* simt, TcCtx* tc, c
         constexpr int CPT = NB / (NT / NB);     // columns per thread in a 64 x 64 tile
         if (lat_ok)
             for (int bj = 0; bj < nb; ++bj)
-                for (int bi = bj; bi < nb; ++bi) {
+                for (int bi = bj; bi < (TC ? min(nb, (bj & ~1) + 2) : nb); ++bi) {
                     const int r = bi * NB + (tid & (NB - 1));
                     if (r >= k) continue;
                     const int ri = ti[r], rj = tj[r];
@@ -1248,7 +1278,7 @@ __device__ void run_task(SmemM& sm, SmemKeep& keep, SmemSimt* simt, TcCtx* tc, c
 #pragma unroll
                     for (int u = 0; u < CPT; ++u) {
                         const int c = bj * NB + (tid >> 6) + u * (NT / NB);
-                        v[u] = c < r ? __ldg(&tab[abs(ri - ti[c]) * W + abs(rj - tj[c])]).x : 1.0f + lam32;
+                        v[u] = c < r ? tab[abs(ri - ti[c]) * W + abs(rj - tj[c])].x : 1.0f + lam32;
                     }
 #pragma unroll
                     for (int u = 0; u < CPT; ++u) {
@@ -1337,7 +1367,10 @@ __device__ void run_task(SmemM& sm, SmemKeep& keep, SmemSimt* simt, TcCtx* tc, c
         if constexpr (TC) {
             if (fuse_fw)
                 for (int q = tid; q < k; q += NT) S.w[q] = (float)S.rr[q];
-            ok = factor_tc<Sch>(*tc, S, k, ld, a.phase_cycles, fuse_fw ? S.w : nullptr, keep.fwj);
+            LatView lv{};
+            if constexpr (LAT)
+                lv = LatView{S.tab, reinterpret_cast<const int*>(S.xh), reinterpret_cast<const int*>(S.yh), W};
+            ok = factor_tc<Sch, LAT>(*tc, S, k, ld, a.phase_cycles, fuse_fw ? S.w : nullptr, keep.fwj, lv);
         }
         else ok = factor32(sm, *simt, S, k, ld);
     }
