@@ -125,7 +125,10 @@ typedef struct {
     int32_t refine_max_iter;   /* mixed path: maximum refinement corrections (default 6) */
     double refine_tol;         /* mixed path: stop once the error left after correction i,
                                   estimated as ||d_i|| * ||d_i|| / ||d_i-1||, is at most
-                                  tol * ||x|| (max norms; default 1e-7); tasks whose
+                                  tol * ||x|| (max norms; default 2e-8: the local
+                                  loss amplifies prediction errors by about
+                                  |yhat| / |yhat - y|, so the solution is refined well
+                                  past the loss's 1e-6 target); tasks whose
                                   corrections stop shrinking are recomputed in FP64 */
     int32_t factor_engine;     /* mixed path factorisation: 0 = tensor cores with FP32 values
                                   split in two FP16 terms, three products (default; a task

@@ -130,7 +130,7 @@ pcv_options default_options(const pcv_options* o) {
     d.max_slots = 0;
     d.workspace_fraction = 0.5;
     d.refine_max_iter = 6;
-    d.refine_tol = 1e-7;
+    d.refine_tol = 2e-8;
     d.factor_engine = pcv::kMixedEngineTensor;
     d.tc_stages = 0;
     if (o) {

@@ -81,23 +81,32 @@ def test_bad_parameters(gpu_lib, prec):
         assert rel(out["sspe"][5], ref["sspe"][1]) <= 1e-4
 
 
-@pytest.mark.parametrize("prec", PRECS)
-def test_cluster_batch_sampled(gpu_lib, prec):
-    """Poisson-cluster locations (uneven subsets, many degenerate), a batch of 8
-    configurations in one launch, sampled subsets (smallest, largest, random)."""
+@pytest.fixture(scope="module")
+def cluster():
+    """Poisson-cluster workload (65,536 TRAIN, 16 x 16 cores), 8 configurations, and the
+    oracle on every subset with validation data (LAPACK-backed kriging)."""
     w = datagen.config_cluster_262k(n_train=65536, n_valid=8192, fine=512, nx=16, delta=0.02)
     P = w.params[::8]
+    members = oracle.all_members(w.xy, w.role, w.layout)
+    act = [i for i, (_, V) in enumerate(members) if len(V) > 0]
+    ref = oracle.cv_loss(w.xy, w.v, w.role, w.layout, P, members=members, subsets=act, lapack=True)
+    return w, P, act, ref
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_cluster_batch_all(gpu_lib, cluster, prec):
+    """Poisson-cluster locations (uneven subsets, k from a handful to ~1600, many
+    degenerate), a batch of 8 configurations in one launch, every subset with
+    validation data against the oracle.  The SSPE amplifies prediction errors by about
+    |yhat| / |yhat - y|, so this covers the refinement's stopping rule where its margin
+    is thinnest (a sample of 8 subsets passed at a tolerance whose worst subset did not)."""
+    w, P, act, ref = cluster
     with gpu_lib.Context(w.xy, w.v, w.role, w.layout) as ctx:
         out = ctx.cv_loss(P, precision=prec, per_subset=True, predictions=True)
-        T_off, V_off = ctx.T_off.copy(), ctx.V_off.copy()
-    k = np.diff(T_off)
-    m = np.diff(V_off)
-    act = np.nonzero(m > 0)[0]
-    pick = sorted(set([int(act[np.argmax(k[act])]), int(act[np.argmin(k[act])])] +
-                      np.random.default_rng(0).choice(act, 6, replace=False).tolist()))
-    members = oracle.all_members(w.xy, w.role, w.layout)
-    ref = oracle.cv_loss(w.xy, w.v, w.role, w.layout, P, members=members, subsets=pick)
-    compare(out, ref, V_off, pick, len(P), prec, check_total=False)
+        V_off = ctx.V_off.copy()
+    assert np.all(out["status"] == 0)
+    worst = compare(out, ref, V_off, act, len(P), prec, check_total=False)
+    print(prec, "cluster", len(act), "subsets", worst)
 
 
 @pytest.mark.parametrize("prec", PRECS)
