@@ -395,14 +395,26 @@ const char* pcv_status_str(int32_t status);
 const char* pcv_last_error(void);
 int32_t pcv_version(void);
 
-/* 1 if every input point lies on one regular lattice (x0 + i hx, y0 + j hy for
- * integers i, j, within 1e-6 of the spacing), with the spacings; 0 otherwise.  On
- * lattice data the mixed path's CV loss takes each covariance from a per-task table
- * indexed by the lattice offsets (|di|, |dj|), computed once per task in FP64, instead
- * of evaluating the exponential per matrix entry; the distances are then those of the
- * exact lattice, which differ from the FP64 coordinates' by their rounding (~1e-13
- * relative). */
+/* 1 if the context's data took the lattice path, with the spacings; 0 otherwise.
+ * The data are a lattice when every point lies on x0 + i hx, y0 + j hy for integers
+ * 0 <= i, j < 2^31 (pcv_lattice_detect), and the path is taken when, in addition, the
+ * index extent of every subset (training and validation points) fits a table of 2^21
+ * entries.  On that path the mixed CV loss takes each covariance from a per-task table
+ * indexed by the lattice offsets (|di|, |dj|), computed once per task in FP64 (Eq. 1
+ * evaluated at the lattice distances), instead of evaluating the exponential per matrix
+ * entry. */
 int32_t pcv_lattice(const pcv_ctx* ctx, double* hx, double* hy);
+
+/* Host-only lattice test of n points (xy: n x 2 row-major FP64, read only), the rule
+ * pcv_create applies: per axis, h is the smallest gap between distinct values refined
+ * over the whole range (span / round(span / gap)), and every value v must satisfy
+ * |(v - v_min) / h - round(...)| <= 16 eps (max|v| / h + span / h), a few FP64 ulps
+ * of the largest coordinate, so snapping to the lattice moves no point more than the
+ * rounding of its coordinates already did.  One distinct value on an axis counts as a
+ * lattice of spacing 1.  Returns 1 and writes the origin and spacings (any output
+ * pointer may be NULL) if both axes pass; 0 otherwise (also for n <= 0, NULL xy or a
+ * non-finite coordinate).  No device work; thread-safe. */
+int32_t pcv_lattice_detect(const double* xy, int64_t n, double* x0, double* hx, double* y0, double* hy);
 
 /* Number of kernels of this library launched by the calling thread since the
  * last reset (for launch accounting in benchmarks); reset when reset != 0. */

@@ -970,3 +970,21 @@ PCV_API int32_t pcv_lattice(const pcv_ctx* c, double* hx, double* hy) {
     if (hy) *hy = c->lat_hy;
     return 1;
 }
+
+PCV_API int32_t pcv_lattice_detect(const double* xy, int64_t n, double* x0, double* hx, double* y0, double* hy) {
+    if (!xy || n <= 0) return 0;
+    std::vector<double> vx((size_t)n), vy((size_t)n);
+    for (int64_t q = 0; q < n; ++q) {
+        vx[q] = xy[2 * q];
+        vy[q] = xy[2 * q + 1];
+        if (!std::isfinite(vx[q]) || !std::isfinite(vy[q])) return 0;
+    }
+    double ox = 0.0, oy = 0.0, sx = 0.0, sy = 0.0;
+    std::vector<int32_t> ix, iy;
+    if (!lattice_axis(vx, ox, sx, ix) || !lattice_axis(vy, oy, sy, iy)) return 0;
+    if (x0) *x0 = ox;
+    if (hx) *hx = sx;
+    if (y0) *y0 = oy;
+    if (hy) *hy = sy;
+    return 1;
+}

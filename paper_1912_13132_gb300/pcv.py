@@ -99,6 +99,7 @@ _SIGS = {
     "pcv_version": (ctypes.c_int32, []),
     "pcv_launch_count": (ctypes.c_int64, [ctypes.c_int32]),
     "pcv_lattice": (ctypes.c_int32, [_vp, _dp, _dp]),
+    "pcv_lattice_detect": (ctypes.c_int32, [_dp, ctypes.c_int64, _dp, _dp, _dp, _dp]),
 }
 EXPORTS = tuple(_SIGS)
 
@@ -475,6 +476,15 @@ def pcv_selftest_umma(A, B):
     st = _lib.pcv_selftest_umma(A.ctypes.data_as(fp), A.shape[0], B.ctypes.data_as(fp), A.shape[1],
                                 C.ctypes.data_as(fp))
     return int(st), C
+
+
+def pcv_lattice_detect(xy):
+    """Host-only: ((x0, hx), (y0, hy)) if every point lies on one regular lattice by the
+    rule pcv_create applies (a few FP64 ulps of slack), else None.  No device work."""
+    xy = _f64(xy).reshape(-1, 2)
+    out = [ctypes.c_double() for _ in range(4)]
+    ok = _lib.pcv_lattice_detect(_ptr(xy, _dp), len(xy), *(ctypes.byref(o) for o in out))
+    return ((out[0].value, out[1].value), (out[2].value, out[3].value)) if ok else None
 
 
 def pcv_launch_count(reset: bool = False) -> int:

@@ -123,3 +123,39 @@ def test_invalid_input(case):
     with pytest.raises(pcv.PcvError) as e:
         pcv.pcv_plan_create(xy, role, lay)
     assert e.value.status == pcv.PCV_ERR_ARG
+
+
+def test_lattice_detect():
+    """Host-side lattice test (the rule pcv_create applies to choose the table path):
+    gridded workloads pass with their spacing; a column shifted by 1e-9 of the spacing,
+    scattered points and non-finite input do not; a one-ulp change of a whole column (a
+    rounding-level deviation) still passes; degenerate axes count as spacing 1."""
+    w = datagen.config_paper_5m(side=560, nx=10, delta=0.001 * 2236 / 560)
+    got = pcv.pcv_lattice_detect(w.xy)
+    assert got is not None
+    (x0, hx), (y0, hy) = got
+    assert x0 == w.xy[:, 0].min() and y0 == w.xy[:, 1].min()
+    assert abs(hx * 560 - 1) < 1e-14 and abs(hy * 560 - 1) < 1e-14
+    xs = np.unique(w.xy[:, 0])
+    col = w.xy[:, 0] == xs[200]
+    for shift, ok in [(1e-9 * hx, False), (1e-6 * hx, False)]:
+        xy = w.xy.copy()
+        xy[col, 0] += shift
+        assert (pcv.pcv_lattice_detect(xy) is not None) == ok, shift
+    xy = w.xy.copy()
+    xy[col, 0] = np.nextafter(xy[col, 0], 2.0)
+    assert pcv.pcv_lattice_detect(xy) is not None
+    # large offsets (projected coordinates in metres, 1 m spacing)
+    g = np.stack(np.meshgrid(5.0e5 + np.arange(40.0), 4.2e6 + np.arange(30.0), indexing="ij"), -1).reshape(-1, 2)
+    (gx0, ghx), (gy0, ghy) = pcv.pcv_lattice_detect(g)
+    assert (gx0, ghx, gy0, ghy) == (5.0e5, 1.0, 4.2e6, 1.0)
+    # spacing that is not a binary fraction, with missing nodes
+    g2 = np.stack(np.meshgrid(np.arange(50) * 0.1, np.arange(7) * 0.3, indexing="ij"), -1).reshape(-1, 2)
+    g2 = g2[np.random.default_rng(3).random(len(g2)) < 0.7]
+    (_, h2x), (_, h2y) = pcv.pcv_lattice_detect(g2)
+    assert abs(h2x - 0.1) < 1e-15 and abs(h2y - 0.3) < 1e-15
+    assert pcv.pcv_lattice_detect(np.random.default_rng(1).random((500, 2))) is None
+    assert pcv.pcv_lattice_detect(np.array([[0.25, 0.5]])) == ((0.25, 1.0), (0.5, 1.0))
+    assert pcv.pcv_lattice_detect(np.array([[0.0, 0.0], [0.0, 0.5], [0.0, 1.5]])) == ((0.0, 1.0), (0.0, 0.5))
+    assert pcv.pcv_lattice_detect(np.array([[0.0, 0.0], [np.nan, 0.5]])) is None
+    assert pcv.pcv_lattice_detect(np.zeros((0, 2))) is None

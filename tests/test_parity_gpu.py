@@ -384,6 +384,8 @@ def test_lattice_path(gpu_lib):
         out = ctx.cv_loss(P, precision="mixed", per_subset=True, predictions=True)
         V_off = ctx.V_off.copy()
     assert lat is not None and abs(lat[0] - 1 / 256) < 1e-15 and abs(lat[1] - 1 / 256) < 1e-15
+    det = gpu_lib.pcv_lattice_detect(w.xy)          # the host rule pcv_create applied
+    assert det is not None and (det[0][1], det[1][1]) == lat
     assert np.all(out["status"] == 0)
     members = oracle.all_members(w.xy, w.role, w.layout)
     ref = oracle.cv_loss(w.xy, w.v, w.role, w.layout, P, members=members)
@@ -401,6 +403,7 @@ def test_lattice_path(gpu_lib):
     col = np.isclose(xy3[:, 0], np.unique(xy3[:, 0])[100], rtol=0, atol=1e-12)
     assert col.sum() > 0
     xy3[col, 0] += 1e-7 / 256
+    assert gpu_lib.pcv_lattice_detect(xy3) is None
     with gpu_lib.Context(xy3, w.v, w.role, w.layout) as ctx3:
         assert ctx3.lattice() is None
         out3 = ctx3.cv_loss(P, precision="mixed", per_subset=True, predictions=True)
