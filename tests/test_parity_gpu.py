@@ -130,6 +130,27 @@ def test_deterministic(gpu_lib, prec):
     assert np.array_equal(a, b)
 
 
+def test_forced_fp64_fallback(gpu_lib):
+    """The mixed path's FP64 fallback, forced for every task: one correction allowed
+    and a tolerance no refinement meets, so each task lands on the device-side list and
+    is recomputed by the FP64 kernel in the same stream.  Every configuration reports
+    PCV_REFINE_FALLBACK (a warning: the results stand) and matches the oracle at the
+    FP64 bar; the same data at the default options need no fallback."""
+    w = datagen.make_uniform(800, 400, 3, 0.05, seed=41, name="fallback")
+    P = np.array([[1.0, 0.1, 0.05], [1.0, 0.05, 0.01], [0.5, 0.2, 0.002]])
+    with gpu_lib.Context(w.xy, w.v, w.role, w.layout, refine_max_iter=1, refine_tol=1e-300) as ctx:
+        out = ctx.cv_loss(P, precision="mixed", per_subset=True, predictions=True)
+        V_off = ctx.V_off.copy()
+    assert np.all(out["status"] == gpu_lib.PCV_REFINE_FALLBACK), out["status"]
+    members = oracle.all_members(w.xy, w.role, w.layout)
+    ref = oracle.cv_loss(w.xy, w.v, w.role, w.layout, P, members=members)
+    worst = compare(out, ref, V_off, range(len(members)), len(P), "fp64")
+    with gpu_lib.Context(w.xy, w.v, w.role, w.layout) as ctx:
+        out2 = ctx.cv_loss(P, precision="mixed")
+    assert np.all(out2["status"] == 0)
+    print("forced fallback", worst)
+
+
 def test_sigma2_invariance_gpu(gpu_lib):
     """Only lambda = tau2 / sigma2 and rho matter (remark after Eq. 3)."""
     w = datagen.make_uniform(800, 400, 2, 0.05, seed=37, name="inv")
