@@ -137,3 +137,17 @@ def test_cap_invariants():
         assert np.array_equal(Tc, oracle.subset_members(xy, role, capped, i)[0])   # same seed, same draw
         diff += not np.array_equal(Tc, To)
     assert diff > 0                          # another seed draws other points
+
+
+def test_shell_key_is_splitmix64():
+    """The shell cap's keys are outputs of the SplitMix64 generator (Steele, Lea and Flood,
+    2014): seeded with 0, its first five outputs are the published sequence (the same as
+    Java's SplittableRandom(0).nextLong()), and key (i, j) is output ((i << 40) | j) + 1."""
+    published = [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F, 0xF88BB8A8724C81EC,
+                 0x1B39896A51A8749B]
+    assert [oracle.shell_key(0, 0, j) for j in range(5)] == published
+    # another subset index moves the stream by whole 2^40 blocks: key (1, 0) is output 2^40 + 1,
+    # which a seed shifted by 2^40 increments reaches as its first output
+    gamma = 0x9E3779B97F4A7C15
+    assert oracle.shell_key(0, 1, 0) == oracle.shell_key((gamma << 40) & ((1 << 64) - 1), 0, 0)
+    assert oracle.shell_key(7, 3, 5) != oracle.shell_key(7, 5, 3)
