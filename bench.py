@@ -605,6 +605,12 @@ def main():
     roof = dict(bound=bound, achieved=achieved, peak=peak, unit="TFLOP/s", frac=achieved / peak if peak else None,
                 traffic=traffic, traffic_note=traffic_note, peak_source=peak_note,
                 kernel="task kernel (persistent)", flops_per_launch=flops, launch_ms=t_task * 1e3)
+    if traffic:
+        # the practical bound beside the algorithmic one: the recorded DRAM bytes of a
+        # launch over its event-timed duration, against the measured copy bandwidth
+        dram_gbs = traffic / t_task / 1e9
+        roof.update(dram_gbs=dram_gbs, dram_frac=dram_gbs / peaks["hbm_gbs"],
+                    dram_peak_source=f"hbm_gbs ({peak_src})")
 
     line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
                 ms_per_step=total_s * 1e3 / args.steps, higher_is_better=True, scaling="weak",
