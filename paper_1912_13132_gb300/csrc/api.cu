@@ -61,7 +61,7 @@ struct DevBuf {
 
 struct Workspace {
     DevBuf<unsigned char> mem;
-    DevBuf<unsigned char> planes;          // mixed path, tensor engine: BF16 planes of the factors
+    DevBuf<unsigned char> planes;          // mixed path, tensor engines: 16-bit planes of the factors
     int64_t plane_elems = 0;
     alignas(64) unsigned char maps[3 * 128];   // CUtensorMap x 3 over the planes
     int grid = 0;

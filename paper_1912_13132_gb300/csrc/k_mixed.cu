@@ -5,10 +5,15 @@
 //   gather     training coordinates as offsets from the subset's first training
 //              point in units of rho, split in double-float (high parts on a
 //              power-of-two grid so that differences of high parts are exact)
-//   assemble   A32 = Sigma(rho) + lambda I in FP32                  (Eq. 3, Sec. 3)
+//   assemble   A32 = Sigma(rho) + lambda I in FP32                  (Eq. 3, Sec. 3);
+//              on lattice data (the LAT variant) every entry comes from a per-task
+//              FP64 table of covariances by index offset, and only the 128 x 128
+//              diagonal blocks are stored (the factorisation reads the rest from it)
 //   factor     A32 ~ L L^T, left-looking: tensor engine (k_cv_mixed_tc) with
-//              128-wide block columns whose trailing updates run on tcgen05 from
-//              split-BF16 planes; FP32 engine (k_cv_mixed) with 64-wide blocks
+//              128-wide block columns whose trailing updates and panels run on
+//              tcgen05 from 16-bit planes (two FP16 terms per value by default,
+//              three BF16 terms as an option); FP32 engine (k_cv_mixed) with
+//              64-wide blocks.  The first forward solve rides on the panels.
 //   refine     x <- x + L^-T L^-1 r,  r = y - A x with A's entries and the sums
 //              in double-float (exp by Tang's method, see df.cuh), until the error
 //              left, estimated as |d_i|^2 / |d_i-1|, is below refine_tol |x|
@@ -506,7 +511,7 @@ constexpr int kDiagRedOff = kDiagYOff + 3 * 32 * 32 * 4;   // per-warp maxima
 constexpr int kDiagBytes = kDiagRedOff + (NT / 32) * 4;
 
 // Left-looking blocked Cholesky with 128-wide block columns, all O(k^3) work on the
-// tensor cores from split-BF16 planes.  For block column J:
+// tensor cores from the scheme's 16-bit planes.  For block column J:
 //   update   C = A[j0:, J] - L[j0:, :j0] L[J, :j0]^T   (tensor cores; the diagonal
 //            block's rows stay FP32, the rows below go to the planes only)
 //   diagonal L_JJ L_JJ^T = C_JJ in FP32 (blocked, shared memory), then L_JJ^-1

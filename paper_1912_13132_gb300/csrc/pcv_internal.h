@@ -73,7 +73,7 @@ struct TaskArgs {
     const int32_t* task_list;
     const unsigned int* task_count;
     int32_t list_status;    // status written for a task finished in list mode
-    // mixed path, tensor-core factorisation: three BF16 planes of the factor, each
+    // mixed path, tensor-core factorisation: the scheme's 16-bit planes of the factor, each
     // plane_elems elements laid out as (slot * ld + row) * ld + column
     void* planes;
     int64_t plane_elems;
@@ -99,8 +99,9 @@ enum Phase { kPhGather = 0, kPhUpdate, kPhDiag, kPhPanel, kPhDiagIO, kPhFactorSi
 // Kernel launchers (one per precision); return the cudaError_t as int.
 int launch_task_fp64(const TaskArgs& a, int grid, void* stream);
 int64_t slot_bytes_fp64(int32_t ld, int64_t mmax);
-// engine: 0 = tensor cores (split-BF16 tcgen05 trailing updates), 1 = FP32 SIMT.
-// maps: three CUtensorMap (128 bytes each) over the planes (engine 0 only).
+// engine: 0 = tensor cores (two FP16 terms per value), 1 = FP32 SIMT, 2 = tensor
+// cores (three BF16 terms).  maps: three CUtensorMap (128 bytes each) over the
+// planes (tensor engines only; the FP16 scheme uses the first two).
 int launch_task_mixed(const TaskArgs& a, const void* maps, int engine, int grid, void* stream);
 bool mixed_make_maps(void* planes, int64_t plane_elems, int32_t ld, int grid, int nplanes, void* maps_out);
 // mixed-path engines: tensor cores with two-term FP16 operands (default), FP32 SIMT,
