@@ -385,3 +385,28 @@ def test_gls_one_subset_is_exact_gls():
     b = oracle.gls_exact(xy, v, role, X, param)
     assert np.allclose(a, b, rtol=1e-9, atol=1e-9), (a, b)
     assert np.allclose(a, [2.0, -1.0, 0.5], atol=0.3)
+
+
+def test_gls_invariants():
+    """Pins of both GLS estimates (Sec. 5) by properties of the estimator, on a 3 x 3
+    layout with shells: data in the column space of X (y = X beta0) give beta0 exactly,
+    whatever M (the prediction operator H is linear, so each subset's normal-equation
+    terms are consistent); as the nugget grows, H -> 0 and the estimate tends to
+    ordinary least squares over the training points (a library least-squares solve)."""
+    r = _rng(61)
+    n = 450
+    xy = r.random((n, 2))
+    role = np.zeros(n, dtype=np.uint8)
+    role[::4] = 1
+    X = np.stack([np.ones(n), xy[:, 0], xy[:, 1] ** 2, np.sin(3 * xy[:, 0])], 1)
+    lay = dict(kind="grid", nx=3, ny=3, delta=0.08, domain=(0.0, 1.0, 0.0, 1.0))
+    beta0 = np.array([1.5, -2.0, 0.75, 0.3])
+    y = X @ beta0
+    for param in ((1.0, 0.1, 0.05), (2.0, 0.3, 0.001)):
+        assert np.allclose(oracle.gls(xy, y, role, lay, X, param), beta0, rtol=0, atol=1e-9)
+        assert np.allclose(oracle.gls_exact(xy, y, role, X, param), beta0, rtol=0, atol=1e-9)
+    v = y + 0.5 * r.standard_normal(n)
+    T = role == 0
+    ols = np.linalg.lstsq(X[T], v[T], rcond=None)[0]
+    for est in (oracle.gls(xy, v, role, lay, X, (1.0, 0.1, 1e9)), oracle.gls_exact(xy, v, role, X, (1.0, 0.1, 1e9))):
+        assert np.allclose(est, ols, rtol=1e-6, atol=1e-8), (est, ols)
