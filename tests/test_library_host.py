@@ -159,3 +159,40 @@ def test_lattice_detect():
     assert pcv.pcv_lattice_detect(np.array([[0.0, 0.0], [0.0, 0.5], [0.0, 1.5]])) == ((0.0, 1.0), (0.0, 0.5))
     assert pcv.pcv_lattice_detect(np.array([[0.0, 0.0], [np.nan, 0.5]])) is None
     assert pcv.pcv_lattice_detect(np.zeros((0, 2))) is None
+
+
+def test_null_handles_rejected():
+    """Every entry point that takes a context, plan or server handle rejects NULL with
+    PCV_ERR_ARG before touching the device (the header's error behaviour); destroy calls
+    accept NULL; status strings exist for every status."""
+    lib = pcv.load_library(pcv.LIB_PATH)
+    E = pcv.PCV_ERR_ARG
+    calls = {
+        "pcv_plan_info": (None, None, None, None, None, None),
+        "pcv_plan_cores": (None, None),
+        "pcv_subset_info": (None, None, None, None, None, None),
+        "pcv_cv_loss": (None, None, 1, 1, None, None, None, None, None, None),
+        "pcv_cv_loss_device": (None, None, 1, 1, None, None, None, None, None),
+        "pcv_neg2loglik": (None, None, 1, 1, None, None, None, None),
+        "pcv_predict": (None, None, None, 0, 1, None, None),
+        "pcv_predict_local": (None, None, 1, None, None, 0, 1, None, None, None),
+        "pcv_gls": (None, None, 1, None, 1, None, None),
+        "pcv_set_timing": (None, 1),
+        "pcv_kernel_time": (None, None, None),
+        "pcv_phase_cycles": (None, None, 0),
+        "pcv_server_create": (None, 0, None, None),
+        "pcv_server_submit_cv": (None, 0, None, None),
+        "pcv_server_submit_predict": (None, 0, None, None, 0, None),
+        "pcv_server_wait": (None, 0, 0.0, None, None, None, None),
+        "pcv_server_stats": (None, None, None, None, None, None, None),
+    }
+    for name, args in calls.items():
+        assert getattr(lib, name)(*args) == E, name
+    assert lib.pcv_lattice(None, None, None) == 0
+    lib.pcv_destroy(None)
+    lib.pcv_plan_destroy(None)
+    lib.pcv_server_destroy(None)
+    assert lib.pcv_cv_loss(None, None, 1, 1, None, None, None, None, None, None) == E
+    assert b"NULL" in lib.pcv_last_error()
+    for st in range(9):
+        assert lib.pcv_status_str(st)
