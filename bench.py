@@ -58,6 +58,38 @@ def load_peaks() -> tuple[dict, str]:
     return dict(PEAKS_FALLBACK), "fallback"
 
 
+def load_device_peaks() -> dict:
+    """FP64 / FP32 FMA and tcgen05 TF32 / BF16 / FP16 rates measured on this GPU model by
+    `bench.py --peaks` (pcv_measure_peak), committed as JSON in
+    profiles/device_peaks_gb300.txt; {} when absent."""
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "device_peaks_gb300.txt")))
+        return rec.get("tflops", {})
+    except Exception:  # pragma: no cover
+        return {}
+
+
+def measure_peaks(seconds: float) -> dict:
+    """Peak probes with the clocks sampled during each."""
+    import torch
+    from paper_1912_13132_gb300 import pcv
+
+    torch.cuda.set_device(0)
+    out = dict(device=torch.cuda.get_device_name(0), sms=torch.cuda.get_device_properties(0).multi_processor_count,
+               tflops={}, seconds={}, clocks={},
+               how="pcv_measure_peak: FP64/FP32 = 8 independent FMA chains per thread, 8 x 256 threads per SM; "
+                   "tensor = dense tcgen05 M=128 N=256 MMAs from fixed shared-memory tiles, one CTA per SM, "
+                   "FP32 accumulators in TMEM; 2 flops per multiply-add; ~seconds per probe after calibration")
+    for kind in ("fp64", "fp32", "tf32", "bf16", "fp16"):
+        clk = ClockSampler(0)
+        clk.start()
+        r = pcv.pcv_measure_peak(kind, seconds)
+        out["clocks"][kind] = clk.stop()
+        out["tflops"][kind] = r["tflops"]
+        out["seconds"][kind] = r["seconds"]
+    return out
+
+
 def make_workload(name: str):
     if name == "paper5m":
         return datagen.config_paper_5m()
@@ -427,6 +459,48 @@ def run_serving(pcv, device: int, seconds: float, hbm_budget_gb: float, max_batc
     return out
 
 
+def run_cluster(pcv, device: int, steps: int = 3) -> dict:
+    """The uneven-subset workload (262,144 Poisson-cluster points, 32 x 32 cores, k from
+    about 100 to 900, many cores without validation data): all 64 configurations of its
+    (rho, tau2) grid in one call, size-bucketed with autotuned engines against one launch
+    over slots sized for the largest subset; device-timed, L2 flushed between steps."""
+    import torch
+
+    w = datagen.config_cluster_262k()
+    d_p = torch.tensor(w.params, dtype=torch.float64, device="cuda")
+    B = len(w.params)
+    d_sspe = torch.empty(B, dtype=torch.float64, device="cuda")
+    d_status = torch.empty(B, dtype=torch.int32, device="cuda")
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    out = dict(workload=w.name, batch=B)
+    for label, bucketing in (("bucketed", 0), ("one_launch", 1)):
+        t0 = time.perf_counter()
+        ctx = pcv.Context(w.xy, w.v, w.role, w.layout, device=device, bucketing=bucketing)
+        ctx.cv_loss_device(d_p, d_sspe, precision="mixed", d_status=d_status, stream=stream)   # tunes, allocates
+        torch.cuda.synchronize()
+        first_s = time.perf_counter() - t0
+        ms = []
+        for _ in range(steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.cv_loss_device(d_p, d_sspe, precision="mixed", d_status=d_status, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        st = sorted(set(d_status.cpu().numpy().tolist()))
+        k = np.diff(ctx.T_off)[np.diff(ctx.V_off) > 0]
+        out[label] = dict(value=B * steps / (sum(ms) / 1e3), unit=UNIT, ms_per_step=sum(ms) / steps, steps=steps,
+                          status=st, setup_s=round(first_s, 2), buckets=ctx.buckets().strip().splitlines())
+        out.update(active_subsets=int(len(k)), k_min=int(k.min()), k_max=int(k.max()))
+        ctx.close()
+    out["bucketed_over_one_launch"] = out["bucketed"]["value"] / out["one_launch"]["value"]
+    return out
+
+
 def run_reference(args, rank: int, world: int):
     """The oracle as it stands on the host cores, a bounded sample per step."""
     if rank != 0:
@@ -465,7 +539,13 @@ def main():
     ap.add_argument("--workload", default="paper5m")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--batch", type=int, default=8)
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=0, help="end-to-end steps (0: as many as --steps)")
+    ap.add_argument("--fp64-steps", type=int, default=2,
+                    help="steps of the FP64 arm on the same batches as the first timed steps (0: none)")
+    ap.add_argument("--peaks", action="store_true", help="measure the device peaks (JSON) and exit")
+    ap.add_argument("--cluster-steps", type=int, default=3,
+                    help="steps of the 64-configuration cluster workload, bucketed and in one launch (0: none)")
+    ap.add_argument("--peak-seconds", type=float, default=3.0)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--cpu-budget-1core", type=float, default=6.0)
     ap.add_argument("--ref-budget", type=float, default=12.0)
@@ -488,6 +568,10 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.peaks:
+        if rank == 0:
+            print(json.dumps(measure_peaks(args.peak_seconds)), flush=True)
         return
 
     import torch
@@ -566,26 +650,62 @@ def main():
     phases = ctx.phase_cycles() if args.precision == "mixed" else None
     value, total_s = aggregate_rate(sum(step_ms) / 1e3, B * args.steps, world, dist, "cuda")
 
-    # end to end through the host-pointer call (params up, results down, per step)
+    # end to end through the host-pointer call (params up, results down, per step), over
+    # the same parameter batches as the timed steps
+    e2e_steps = args.e2e_steps or args.steps
     e2e_s = []
-    host_P = [np.ascontiguousarray(d_params[s % nsteps].cpu().numpy()) for s in range(args.e2e_steps)]
-    for s in range(args.e2e_steps):
+    host_P = [np.ascontiguousarray(d_params[args.warmup + s % args.steps].cpu().numpy()) for s in range(e2e_steps)]
+    for s in range(e2e_steps):
         flush.zero_()
         torch.cuda.synchronize()
         barrier()
         t0 = time.perf_counter()
         out = ctx.cv_loss(host_P[s], precision=args.precision, stream=stream)
         e2e_s.append(time.perf_counter() - t0)
-    e2e_value, _ = aggregate_rate(sum(e2e_s) if e2e_s else 1.0, B * args.e2e_steps, world, dist, "cuda")
-    if args.e2e_steps <= 0:
-        e2e_value = None
+    e2e_value, _ = aggregate_rate(sum(e2e_s), B * e2e_steps, world, dist, "cuda")
+
+    # the FP64 arm of the metric: the same batches as the first timed steps, through the
+    # same call, device-timed (one untimed single-configuration call allocates its work
+    # memory first)
+    fp64 = None
+    if args.precision == "mixed" and args.fp64_steps > 0:
+        ctx.cv_loss_device(d_params[0][:1], d_sspe, precision="fp64", d_status=d_status, stream=stream)
+        torch.cuda.synchronize()
+        f_ms, f_task = [], []
+        for s in range(args.warmup, args.warmup + args.fp64_steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.cv_loss_device(d_params[s], d_sspe, precision="fp64", d_status=d_status, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            f_ms.append(e0.elapsed_time(e1))
+            f_task.append(ctx.kernel_time()[0])
+        f_st = d_status.cpu().numpy()
+        f_value, f_total = aggregate_rate(sum(f_ms) / 1e3, B * args.fp64_steps, world, dist, "cuda")
+        dev_peaks = load_device_peaks()
+        f_peak = dev_peaks.get("fp64")
+        f_ach = algorithmic_flops(k, m, B) / (statistics.mean(f_task) / 1e3) / 1e12
+        fp64 = dict(value=f_value, unit=UNIT, steps=args.fp64_steps, ms_per_step=f_total * 1e3 / args.fp64_steps,
+                    batches="the first timed steps' parameter batches", status=sorted(set(f_st.tolist())),
+                    roofline=dict(bound="alu", achieved=f_ach, peak=f_peak, unit="TFLOP/s",
+                                  frac=f_ach / f_peak if f_peak else None,
+                                  peak_source="FP64 FMA probe (measured, profiles/device_peaks_gb300.txt)"
+                                  if f_peak else "no committed FP64 measurement",
+                                  kernel="k_cv_fp64 (persistent)", launch_ms=statistics.mean(f_task)))
 
     peaks, peak_src = load_peaks()
     flops = algorithmic_flops(k, m, B)
     t_task = statistics.mean(task_ms) / 1e3
     achieved = flops / t_task / 1e12
+    dev_peaks = load_device_peaks()
     if args.precision == "fp64":
-        bound, peak, peak_note = "alu", FP64_NOMINAL_TFLOPS, "FP64 nominal (no measured FP64 peak)"
+        if dev_peaks.get("fp64"):
+            bound, peak, peak_note = "alu", dev_peaks["fp64"], "FP64 FMA probe (measured, profiles/device_peaks_gb300.txt)"
+        else:
+            bound, peak, peak_note = "alu", FP64_NOMINAL_TFLOPS, "FP64 nominal (no measured FP64 peak)"
     else:
         if args.engine in SCHEMES:
             # n 16-bit products per FP32-accurate product: the useful-flop ceiling of the
@@ -597,9 +717,12 @@ def main():
             peak_note = f"bf16 sustained ({peak_src}) / {nprod} split products"
         else:
             bound = "alu"
-            sm_max = (clk.get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0))
-            peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12
-            peak_note = "FP32 FMA: 152 SMs x 128 lanes x 2 flop x max SM clock"
+            if dev_peaks.get("fp32"):
+                peak, peak_note = dev_peaks["fp32"], "FP32 FMA probe (measured, profiles/device_peaks_gb300.txt)"
+            else:
+                sm_max = (clk.get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0))
+                peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12
+                peak_note = "FP32 FMA: 152 SMs x 128 lanes x 2 flop x max SM clock"
     traffic, traffic_note = (recorded_traffic(len(k) * B, args.engine) if args.precision == "mixed"
                              else (None, "no ncu record for this kernel"))
     roof = dict(bound=bound, achieved=achieved, peak=peak, unit="TFLOP/s", frac=achieved / peak if peak else None,
@@ -624,9 +747,14 @@ def main():
                             parallelism="replicas" if world > 1 else "single-gpu",
                             l2="flushed between steps (512 MB write)"),
                 e2e=dict(value=e2e_value, unit=UNIT, h2d_bytes_per_step=24 * B, d2h_bytes_per_step=12 * B,
-                         note="pcv_cv_loss host-pointer call; dataset resident since pcv_create"),
+                         steps=e2e_steps,
+                         note="pcv_cv_loss host-pointer call over the timed steps' parameter batches; "
+                              "dataset resident since pcv_create"),
                 gpu_launches=int(launches), roofline=roof, clocks=clk,
                 setup=dict(datagen_s=t_gen, create_s=t_create))
+    if fp64 is not None:
+        fp64["mixed_over_fp64"] = value / fp64["value"]
+        line["fp64"] = fp64
     if phases and phases.get("task"):
         tot = phases["task"]
         counts = ("task", "residual_passes", "tasks", "fail_factor", "fail_nan", "fail_stall")
@@ -646,6 +774,8 @@ def main():
                                                   sample=f"{c1['n_done']} subsets ({c1['elapsed']:.1f} s), "
                                                          f"extrapolated to {c1['t_full']:.0f} s per configuration"))
     ctx.close()
+    if rank == 0 and world == 1 and args.cluster_steps > 0 and args.workload == "paper5m":
+        line["cluster"] = run_cluster(pcv, local, args.cluster_steps)
     if rank == 0 and world == 1 and args.serve_seconds > 0:
         line["serving"] = run_serving(pcv, local, args.serve_seconds, args.hbm_budget_gb, args.serve_batch,
                                       max_slots=args.serve_slots, engine=args.engine)

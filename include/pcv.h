@@ -139,6 +139,43 @@ typedef struct {
     int32_t tc_stages;         /* tensor engines: depth of the TMA operand ring, 2 to 4 (0 =
                                   default: 3 for engine 0, 2 for engine 2); rings above
                                   96 KB leave one CTA per SM */
+    double refine_loss_tol;    /* mixed path, loss-aware stopping rule (default 1e-7; < 0
+                                  turns it off): a CV-loss or prediction task whose solution
+                                  rule (refine_tol) is not met yet also stops once the error
+                                  left in its predictions, estimated as g |K d_i| (K the
+                                  cross-covariances to the prediction points, d_i the last
+                                  correction, g = c / (1 - c) with c the observed
+                                  contraction |d_i| / |d_i-1|), changes its local SSPE by at
+                                  most this fraction (|dz| <= 2 |yhat - y| |dyhat|) and moves
+                                  no prediction by more than ten times this fraction of their
+                                  RMS.  The SSPE amplifies prediction errors by about
+                                  |yhat| / |yhat - y|, which the rule weighs subset by
+                                  subset instead of refining every solution for the worst
+                                  case.  Used where a task's prediction points are no more
+                                  than its training points (their cost stays below a
+                                  residual pass); the local log-likelihood and GLS keep the
+                                  solution rule. */
+    int32_t bucketing;         /* mixed CV loss with the default engine: 0 (default) = size
+                                  buckets, the active subsets grouped by training size, each
+                                  group with slots of its own size and the factorisation
+                                  engine (tensor cores or FP32 SIMT) that an autotuner found
+                                  fastest for it, the groups' persistent launches running
+                                  side by side; 1 = one launch over all subsets in slots
+                                  sized for the largest, engine factor_engine (also the
+                                  behaviour whenever factor_engine is set to a non-default
+                                  engine).  The tuner times both engines on a sample of each
+                                  size class at the first mixed CV call of a context (that
+                                  call synchronises) and caches its choice per process,
+                                  keyed by the histogram of training sizes, the lattice flag
+                                  and the device's SM count; pcv_buckets describes it. */
+    int32_t graph;             /* mixed CV loss: 0 (default) = the second call with a given
+                                  batch size (and the same optional outputs and timing
+                                  state) captures the call's device work -- the buckets'
+                                  launches, the FP64 fallback and the combine -- in a CUDA
+                                  graph, which later calls of that shape replay (parameters
+                                  and results pass through context buffers by
+                                  device-to-device copies on the caller's stream); 1 = every
+                                  call launches its kernels directly */
 } pcv_options;
 
 /* ---------------------------------------------------------------- host-only */
@@ -250,6 +287,12 @@ pcv_status pcv_predict_local(pcv_ctx* ctx, const double* params, int32_t B, cons
  * host outputs.  Mixed precision needs the default tensor engine.  Synchronises. */
 pcv_status pcv_gls(pcv_ctx* ctx, const double* X, int32_t p, const double* params3, int32_t precision,
                    double* beta, void* stream);
+
+/* The size buckets of the context's mixed CV launch as text (one line per bucket:
+ * training-size range, subsets, engine, slot size, slots) into buf (NUL-terminated,
+ * truncated to cap bytes); empty before the first mixed CV call.  Returns the length of
+ * the full description. */
+int32_t pcv_buckets(const pcv_ctx* ctx, char* buf, int32_t cap);
 
 /* Kernel timing for benchmarks.  When enabled, pcv_cv_loss* records CUDA events
  * on the launching stream around the task kernel and around the combine kernel;
@@ -389,6 +432,17 @@ pcv_status pcv_selftest_df_device(int32_t op, const double* d_a, const double* d
  * of 32.  Host arrays; allocates and frees its own device buffers; synchronous.
  * PCV_ERR_TIMEOUT if one of the kernel's bounded waits ran out. */
 pcv_status pcv_selftest_umma(const float* A, int32_t M, const float* B, int32_t K, float* C);
+
+/* Throughput probes for roofline denominators (the paper has no counterpart; they
+ * measure the device, not the method).  kind: 0 FP64 fused multiply-add, 1 FP32 fused
+ * multiply-add (SIMT pipes, every SM), 2 tcgen05 kind::tf32, 3 kind::f16 with BF16
+ * operands, 4 kind::f16 with FP16 operands (dense M = 128, N = 256 MMAs, FP32
+ * accumulators in TMEM, one CTA per SM).  Runs on the current device for about
+ * `seconds` (0 < seconds <= 60) after a short calibration and writes the achieved
+ * rate in TFLOP/s (2 flops per multiply-add) and the timed run's duration (may be
+ * NULL).  Allocates and frees a few bytes of device memory; synchronous.
+ * PCV_ERR_TIMEOUT if a bounded wait of the tensor probe ran out. */
+pcv_status pcv_measure_peak(int32_t kind, double seconds, double* tflops, double* elapsed_s);
 
 /* ----------------------------------------------------------------- utilities */
 const char* pcv_status_str(int32_t status);

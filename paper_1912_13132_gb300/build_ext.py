@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT, "libpcv.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["api.cu", "plan.cpp", "k_fp64.cu", "k_mixed.cu", "k_combine.cu", "no_alloc.cu", "selftest.cu", "server.cpp"]
+SOURCES = ["api.cu", "plan.cpp", "k_fp64.cu", "k_mixed.cu", "k_combine.cu", "no_alloc.cu", "selftest.cu", "server.cpp", "peaks.cu"]
 
 
 def nvcc() -> str:

@@ -11,6 +11,8 @@
 #include <cfloat>
 #include <cmath>
 #include <cstring>
+#include <cstdio>
+#include <map>
 #include <memory>
 #include <mutex>
 #include <numeric>
@@ -69,6 +71,25 @@ struct Workspace {
     int64_t slot_bytes = 0;
 };
 
+// One size bucket of the mixed CV launch: the active subsets whose training sizes fall
+// in [klo, khi], their own slot size (ld), factorisation engine, workspace, task counter
+// and stream (buckets run side by side, forked from and joined to the caller's stream).
+struct Bucket {
+    int32_t klo = 0, khi = 0;
+    int engine = 0;
+    double work = 0.0;                    // sum of k^3 over the bucket's subsets
+    std::vector<int32_t> subsets;         // longest first
+    DevBuf<int32_t> order;
+    Workspace ws;
+    DevBuf<unsigned int> counter;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+    ~Bucket() {
+        if (done) cudaEventDestroy(done);
+        if (stream) cudaStreamDestroy(stream);
+    }
+};
+
 }  // namespace
 
 struct pcv_plan {
@@ -116,7 +137,28 @@ struct pcv_ctx {
     bool timed_task = false, timed_combine = false;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     DevBuf<unsigned long long> phase;       // per-phase cycle counters of the mixed kernel
+    // size buckets of the mixed CV launch (built at the first mixed CV call)
+    std::vector<std::unique_ptr<Bucket>> buckets;
+    bool buckets_tuned = false;             // the engines were chosen by timing, not by rule
+    cudaEvent_t fork = nullptr;
+    std::string bucket_desc;
+    // CUDA graph of the mixed CV call (the buckets' launches, the FP64 fallback and the
+    // combine), captured at the second call of a shape and replayed while the buffers it
+    // names stay in place; parameters and results pass through the context's buffers
+    cudaGraphExec_t gexec = nullptr;
+    int64_t gkey = -1, gseen = -1;
+    std::vector<const void*> gprint;
+    cudaStream_t gcap = nullptr;
+    bool capturing = false;
+    int64_t graph_launches = 0;             // replays so far
+    int64_t graph_kernels = 0;              // kernel launches inside the captured graph
+    DevBuf<double> gparams, gsspe, gyhat;
+    DevBuf<int32_t> gstatus;
     ~pcv_ctx() {
+        if (gexec) cudaGraphExecDestroy(gexec);
+        if (gcap) cudaStreamDestroy(gcap);
+        buckets.clear();
+        if (fork) cudaEventDestroy(fork);
         for (auto& e : ev)
             if (e) cudaEventDestroy(e);
     }
@@ -133,6 +175,9 @@ pcv_options default_options(const pcv_options* o) {
     d.refine_tol = 2e-8;
     d.factor_engine = pcv::kMixedEngineTensor;
     d.tc_stages = 0;
+    d.refine_loss_tol = 1e-7;
+    d.bucketing = 0;
+    d.graph = 0;
     if (o) {
         if (o->struct_size != 0 && o->struct_size != (int32_t)sizeof(pcv_options)) return d;
         if (o->max_slots > 0) d.max_slots = o->max_slots;
@@ -142,6 +187,10 @@ pcv_options default_options(const pcv_options* o) {
         if (o->factor_engine == pcv::kMixedEngineSimt || o->factor_engine == pcv::kMixedEngineTensorBF16)
             d.factor_engine = o->factor_engine;
         if (o->tc_stages >= 2 && o->tc_stages <= 4) d.tc_stages = o->tc_stages;
+        if (o->bucketing == 1) d.bucketing = 1;
+        if (o->graph == 1) d.graph = 1;
+        if (o->refine_loss_tol > 0) d.refine_loss_tol = o->refine_loss_tol;
+        else if (o->refine_loss_tol < 0) d.refine_loss_tol = 0.0;   // solution rule only
     }
     if (d.tc_stages == 0) d.tc_stages = pcv::mixed_default_stages(d.factor_engine);
     return d;
@@ -172,13 +221,10 @@ void workspace_shape(const pcv_ctx* c, int wi, int64_t& g, int64_t& sb, int64_t&
     if (fallback) g = std::min<int64_t>(g, kFallbackSlots);
 }
 
-pcv_status ensure_workspace(pcv_ctx* c, int wi) {
-    Workspace& w = c->ws[wi];
-    if (w.grid > 0) return PCV_OK;
-    int64_t g, sb, pb;
-    int32_t ld;
-    workspace_shape(c, wi, g, sb, pb, ld);
-    const bool tensor = pb > 0;
+// Allocate `g` slots of sb bytes plus pb bytes of planes each (at most the context's
+// share of free device memory) for slots of leading dimension ld, with the tensor maps
+// of a tensor engine's `np` planes.
+pcv_status alloc_workspace(pcv_ctx* c, Workspace& w, int64_t g, int64_t sb, int64_t pb, int32_t ld, int np) {
     size_t free_b = 0, total_b = 0;
     CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
     const double budget = c->opts.workspace_fraction * (double)free_b;
@@ -186,8 +232,7 @@ pcv_status ensure_workspace(pcv_ctx* c, int wi) {
     if (g < 1) return fail(PCV_ERR_OOM, "workspace for one task does not fit in device memory");
     cudaError_t e = w.mem.reserve((size_t)(g * sb));
     if (e != cudaSuccess) return cuda_fail(e, "workspace allocation");
-    if (tensor) {
-        const int np = pcv::mixed_planes(c->opts.factor_engine);
+    if (pb > 0) {
         w.plane_elems = g * (int64_t)ld * ld;
         e = w.planes.reserve((size_t)(np * w.plane_elems * 2));
         if (e != cudaSuccess) return cuda_fail(e, "plane allocation");
@@ -198,6 +243,24 @@ pcv_status ensure_workspace(pcv_ctx* c, int wi) {
     w.ld = ld;
     w.slot_bytes = sb;
     return PCV_OK;
+}
+
+pcv_status ensure_workspace(pcv_ctx* c, int wi) {
+    Workspace& w = c->ws[wi];
+    if (w.grid > 0) return PCV_OK;
+    int64_t g, sb, pb;
+    int32_t ld;
+    workspace_shape(c, wi, g, sb, pb, ld);
+    return alloc_workspace(c, w, g, sb, pb, ld, pb > 0 ? pcv::mixed_planes(c->opts.factor_engine) : 0);
+}
+
+// Mixed-path slot shape of a given slot size and engine (two CTAs per SM).
+void mixed_shape(const pcv_ctx* c, int32_t ld, int engine, int64_t& g, int64_t& sb, int64_t& pb) {
+    const int planes = pcv::mixed_planes(engine);
+    sb = pcv::slot_bytes_mixed(ld, c->mmax, c->lattice ? c->lat_cap : 0);
+    pb = (int64_t)planes * ld * ld * 2;
+    g = c->opts.max_slots > 0 ? c->opts.max_slots : 2 * (int64_t)c->sms;
+    if (planes > 0) g = std::min<int64_t>(g, 2 * (int64_t)c->sms);
 }
 
 bool bad_precision(int32_t p) { return p != PCV_PREC_FP64 && p != PCV_PREC_MIXED; }
@@ -246,6 +309,7 @@ int64_t ctx_workspace_estimate(pcv_ctx* c, int32_t prec) {
     const int list[2] = {prec, prec == PCV_PREC_MIXED ? kFallbackWs : -1};
     for (int wi : list) {
         if (wi < 0 || c->ws[wi].grid > 0) continue;
+        if (wi == PCV_PREC_MIXED && !c->buckets.empty()) continue;   // the CV launch's buckets are held
         int64_t g, sb, pb;
         int32_t ld;
         workspace_shape(c, wi, g, sb, pb, ld);
@@ -257,6 +321,7 @@ int64_t ctx_workspace_estimate(pcv_ctx* c, int32_t prec) {
 int64_t ctx_workspace_resident(pcv_ctx* c) {
     int64_t t = 0;
     for (const auto& w : c->ws) t += (int64_t)(w.mem.n * sizeof(unsigned char) + w.planes.n);
+    for (const auto& b : c->buckets) t += (int64_t)(b->ws.mem.n + b->ws.planes.n);
     return t;
 }
 
@@ -268,6 +333,7 @@ void ctx_release_workspace(pcv_ctx* c) {
         w.grid = 0;
         w.plane_elems = 0;
     }
+    c->buckets.clear();   // rebuilt at the next mixed CV call (the tuner's choice is cached)
 }
 
 int ctx_device(const pcv_ctx* c) { return c->device; }
@@ -463,35 +529,11 @@ PCV_API pcv_status pcv_subset_info(const pcv_ctx* c, int32_t* N, const int64_t**
     return plan_views(c->plan, N, T_off, T_idx, V_off, V_idx);
 }
 
-static pcv_status run_tasks(pcv_ctx* c, const double* d_params, int32_t B, int32_t prec, const int64_t* P_off,
-                            const double* Px, const double* Py, const double* Pv, const int32_t* order,
-                            int32_t n_order, double* d_yhat, int64_t yhat_stride, void* stream,
-                            bool want_lik = false, const int32_t* d_param_row = nullptr,
-                            const double* d_rhs = nullptr, int32_t nrhs = 0, bool lattice = false) {
-    const int32_t N = c->plan.N;
-    CUDA_TRY(c->z.reserve((size_t)B * N));
-    CUDA_TRY(c->tst.reserve((size_t)B * N));
-    cudaStream_t s = (cudaStream_t)stream;
-    CUDA_TRY(cudaMemsetAsync(c->z.p, 0, (size_t)B * N * sizeof(double), s));
-    CUDA_TRY(cudaMemsetAsync(c->tst.p, 0, (size_t)B * N * sizeof(int32_t), s));
-    if (want_lik) {
-        CUDA_TRY(c->lik.reserve((size_t)B * N));
-        CUDA_TRY(cudaMemsetAsync(c->lik.p, 0, (size_t)B * N * sizeof(double), s));
-    }
-    if ((int64_t)n_order * B == 0) return PCV_OK;
-    pcv_status st = ensure_workspace(c, prec);
-    if (st != PCV_OK) return st;
-    if (prec == PCV_PREC_MIXED) {
-        int e = pcv::mixed_prepare(c->device);
-        if (e) return cuda_fail((cudaError_t)e, "mixed-path set-up");
-        st = ensure_workspace(c, kFallbackWs);   // fallback tasks run in FP64
-        if (st != PCV_OK) return st;
-        CUDA_TRY(c->fb_list.reserve((size_t)n_order * B));
-        CUDA_TRY(c->fb_count.reserve(2));
-        CUDA_TRY(cudaMemsetAsync(c->fb_count.p, 0, 2 * sizeof(unsigned int), s));
-    }
-    Workspace& w = c->ws[prec];
-    CUDA_TRY(cudaMemsetAsync(c->counter.p, 0, sizeof(unsigned int), s));
+// The fields of a task-kernel launch that do not depend on the workspace.
+static pcv::TaskArgs base_args(pcv_ctx* c, const double* d_params, int32_t B, const int64_t* P_off, const double* Px,
+                               const double* Py, const double* Pv, const int32_t* order, int32_t n_order,
+                               double* d_yhat, int64_t yhat_stride, bool want_lik, const int32_t* d_param_row,
+                               const double* d_rhs, int32_t nrhs, bool lattice) {
     pcv::TaskArgs a{};
     a.X = c->X.p;
     a.Y = c->Y.p;
@@ -506,7 +548,7 @@ static pcv_status run_tasks(pcv_ctx* c, const double* d_params, int32_t B, int32
     a.n_order = n_order;
     a.params = d_params;
     a.B = B;
-    a.N = N;
+    a.N = c->plan.N;
     a.z = c->z.p;
     a.lik = want_lik ? c->lik.p : nullptr;
     a.param_row = d_param_row;
@@ -528,24 +570,277 @@ static pcv_status run_tasks(pcv_ctx* c, const double* d_params, int32_t B, int32
     a.yhat = d_yhat;
     a.yhat_stride = yhat_stride;
     a.counter = c->counter.p;
-    a.work = reinterpret_cast<double*>(w.mem.p);
-    a.slot_bytes = w.slot_bytes;
-    a.ld = w.ld;
     a.refine_max_iter = c->opts.refine_max_iter;
     a.refine_tol = c->opts.refine_tol;
+    a.refine_loss_tol = c->opts.refine_loss_tol;
     a.coord_scale = c->coord_scale;
     a.fb_list = c->fb_list.p;
     a.fb_count = c->fb_count.p;
-    a.planes = w.planes.p;
-    a.plane_elems = w.plane_elems;
     a.phase_cycles = c->timing ? c->phase.p : nullptr;
     a.tc_stages = c->opts.tc_stages;
-    const int grid = (int)std::min<int64_t>(w.grid, (int64_t)n_order * B);
-    if (c->timing) CUDA_TRY(cudaEventRecord(c->ev[0], s));
-    int e = prec == PCV_PREC_FP64 ? pcv::launch_task_fp64(a, grid, stream)
-                                  : pcv::launch_task_mixed(a, w.maps, c->opts.factor_engine, grid, stream);
-    if (e) return cuda_fail((cudaError_t)e, "task kernel launch");
-    if (c->timing) {
+    return a;
+}
+
+static void with_workspace(pcv::TaskArgs& a, const Workspace& w) {
+    a.work = reinterpret_cast<double*>(w.mem.p);
+    a.slot_bytes = w.slot_bytes;
+    a.ld = w.ld;
+    a.planes = w.planes.p;
+    a.plane_elems = w.plane_elems;
+}
+
+// ---------------------------------------------------------------- size buckets
+
+// Training-size classes of the autotuner: class c holds sizes below kClassEdge[c] (and at
+// least the previous edge).  Adjacent classes that take the same engine form one bucket.
+static const int32_t kClassEdge[] = {128, 256, 384, 512, 768, 1024, 1536, 2048, 3072, 4096, 6144, 8192,
+                                     12288, 16384, INT32_MAX};
+constexpr int kClasses = (int)(sizeof(kClassEdge) / sizeof(kClassEdge[0]));
+constexpr int32_t kSimtMaxK = 2048;   // the FP32 SIMT engine is a candidate below this size
+
+static int size_class(int32_t k) {
+    int c = 0;
+    while (k >= kClassEdge[c]) ++c;
+    return c;
+}
+
+static std::mutex g_tune_mu;
+static std::map<std::string, std::vector<int>> g_tune_cache;   // key -> engine per class
+
+// Time the mixed task kernel with `engine` on a sample of subsets (each evaluated with
+// Bt copies of one parameter row, enough tasks to fill the device); ms per task.
+static pcv_status time_engine(pcv_ctx* c, const std::vector<int32_t>& sample, int engine, int32_t ld,
+                              const double* d_prow, int32_t Bt, cudaStream_t s, double& ms_per_task) {
+    Workspace w;
+    int64_t g, sb, pb;
+    mixed_shape(c, ld, engine, g, sb, pb);
+    g = std::min<int64_t>(g, (int64_t)sample.size() * Bt);
+    pcv_status st = alloc_workspace(c, w, g, sb, pb, ld, pcv::mixed_planes(engine));
+    if (st != PCV_OK) return st;
+    DevBuf<int32_t> ord;
+    DevBuf<unsigned int> cnt;
+    CUDA_TRY(ord.reserve(sample.size()));
+    CUDA_TRY(cnt.reserve(1));
+    CUDA_TRY(cudaMemcpyAsync(ord.p, sample.data(), sample.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    const int32_t N = c->plan.N;
+    CUDA_TRY(c->z.reserve((size_t)Bt * N));
+    CUDA_TRY(c->tst.reserve((size_t)Bt * N));
+    CUDA_TRY(c->fb_list.reserve((size_t)sample.size() * Bt));
+    CUDA_TRY(c->fb_count.reserve(2));
+    pcv::TaskArgs a = base_args(c, d_prow, Bt, c->Voff.p, c->Vx.p, c->Vy.p, c->Vv.p, ord.p, (int32_t)sample.size(),
+                                nullptr, 0, false, nullptr, nullptr, 0, true);
+    a.phase_cycles = nullptr;
+    a.counter = cnt.p;
+    with_workspace(a, w);
+    cudaEvent_t e0, e1;
+    CUDA_TRY(cudaEventCreate(&e0));
+    CUDA_TRY(cudaEventCreate(&e1));
+    float ms = 0.f;
+    cudaError_t err = cudaSuccess;
+    for (int rep = 0; rep < 2 && err == cudaSuccess; ++rep) {   // the first launch warms up
+        cudaMemsetAsync(cnt.p, 0, sizeof(unsigned int), s);
+        cudaMemsetAsync(c->fb_count.p, 0, 2 * sizeof(unsigned int), s);
+        cudaEventRecord(e0, s);
+        err = (cudaError_t)pcv::launch_task_mixed(a, w.maps, engine, (int)w.grid, s);
+        cudaEventRecord(e1, s);
+        if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+        if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (err != cudaSuccess) return cuda_fail(err, "autotuner launch");
+    ms_per_task = (double)ms / (double)(sample.size() * Bt);
+    return PCV_OK;
+}
+
+// Build the size buckets of the mixed CV launch (once per context).  With bucketing on
+// and the default engine, every training-size class present gets the engine that ran
+// its sample fastest (cached per process by the class histogram); adjacent classes with
+// the same engine merge.  Otherwise one bucket takes every subset with factor_engine.
+static pcv_status ensure_buckets(pcv_ctx* c, const double* d_params, int32_t B, cudaStream_t s) {
+    if (!c->buckets.empty()) return PCV_OK;
+    const pcv::Plan& P = c->plan;
+    std::vector<int32_t> act;
+    for (int32_t i = 0; i < P.N; ++i)
+        if (P.V_off[i + 1] > P.V_off[i]) act.push_back(i);
+    std::stable_sort(act.begin(), act.end(), [&](int32_t a2, int32_t b2) {
+        return (P.T_off[a2 + 1] - P.T_off[a2]) > (P.T_off[b2 + 1] - P.T_off[b2]);
+    });
+    auto ksz = [&](int32_t i) { return (int32_t)(P.T_off[i + 1] - P.T_off[i]); };
+    std::vector<int> eng(kClasses, c->opts.factor_engine);
+    std::vector<std::vector<int32_t>> cls(kClasses);
+    for (int32_t i : act) cls[size_class(ksz(i))].push_back(i);
+    const bool tune = c->opts.bucketing == 0 && c->opts.factor_engine == pcv::kMixedEngineTensor;
+    c->buckets_tuned = false;
+    if (tune) {
+        std::string key = "sms=" + std::to_string(c->sms) + ";lat=" + std::to_string((int)c->lattice) +
+                          ";tc=" + std::to_string(c->opts.tc_stages) + ";hist=";
+        for (int q = 0; q < kClasses; ++q)
+            if (!cls[q].empty()) key += std::to_string(q) + ":" + std::to_string(cls[q].size()) + ",";
+        bool cached = false;
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            auto it = g_tune_cache.find(key);
+            if (it != g_tune_cache.end()) {
+                eng = it->second;
+                cached = true;
+            }
+        }
+        if (!cached) {
+            // the first valid parameter row of the call, repeated to fill the device
+            std::vector<double> hp((size_t)3 * B);
+            CUDA_TRY(cudaMemcpyAsync(hp.data(), d_params, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+            CUDA_TRY(cudaStreamSynchronize(s));
+            int32_t row = -1;
+            for (int32_t b = 0; b < B && row < 0; ++b) {
+                const double s2 = hp[3 * b], rho = hp[3 * b + 1], t2 = hp[3 * b + 2];
+                if (s2 > 0 && rho > 0 && t2 >= 0 && std::isfinite(s2) && std::isfinite(rho) && std::isfinite(t2))
+                    row = b;
+            }
+            bool timed = false;
+            if (row >= 0) {
+                const int64_t fill = 2 * (int64_t)c->sms;
+                for (int q = 0; q < kClasses; ++q) {
+                    const auto& L = cls[q];
+                    if (L.empty() || ksz(L.front()) >= kSimtMaxK) continue;   // one candidate: no timing
+                    const int64_t ns = std::min<int64_t>((int64_t)L.size(), fill);
+                    std::vector<int32_t> sample;
+                    for (int64_t j = 0; j < ns; ++j) sample.push_back(L[(size_t)(j * (int64_t)L.size() / ns)]);
+                    const int32_t Bt = (int32_t)std::min<int64_t>(8, (fill + ns - 1) / ns);
+                    DevBuf<double> prow;
+                    CUDA_TRY(prow.reserve((size_t)3 * Bt));
+                    for (int32_t b = 0; b < Bt; ++b)
+                        CUDA_TRY(cudaMemcpyAsync(prow.p + 3 * b, hp.data() + 3 * row, 3 * sizeof(double),
+                                                 cudaMemcpyHostToDevice, s));
+                    const int32_t ld = round_up(ksz(L.front()), 128);
+                    double t_tc = 0.0, t_simt = 0.0;
+                    pcv_status st = time_engine(c, sample, pcv::kMixedEngineTensor, ld, prow.p, Bt, s, t_tc);
+                    if (st == PCV_OK) st = time_engine(c, sample, pcv::kMixedEngineSimt, ld, prow.p, Bt, s, t_simt);
+                    if (st != PCV_OK) return st;
+                    // the SIMT engine must win clearly (timing noise must not flip the choice)
+                    eng[q] = t_simt < 0.9 * t_tc ? pcv::kMixedEngineSimt : pcv::kMixedEngineTensor;
+                    timed = true;
+                }
+            }
+            c->buckets_tuned = timed;
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            g_tune_cache[key] = eng;
+        } else {
+            c->buckets_tuned = true;
+        }
+    }
+    // merge classes into buckets (largest sizes first), one bucket when not tuning
+    c->bucket_desc.clear();
+    for (int q = kClasses - 1; q >= 0; --q) {
+        if (cls[q].empty()) continue;
+        const int e = tune ? eng[q] : c->opts.factor_engine;
+        if (c->buckets.empty() || (tune && c->buckets.back()->engine != e)) {
+            c->buckets.emplace_back(new Bucket);
+            c->buckets.back()->engine = e;
+        }
+        Bucket& bk = *c->buckets.back();
+        bk.subsets.insert(bk.subsets.end(), cls[q].begin(), cls[q].end());
+    }
+    for (auto& bp : c->buckets) {
+        Bucket& bk = *bp;
+        bk.khi = ksz(bk.subsets.front());
+        bk.klo = ksz(bk.subsets.back());
+        for (int32_t i : bk.subsets) bk.work += std::pow((double)ksz(i), 3.0);
+        const int32_t ld = round_up(bk.khi, 128);
+        int64_t g, sb, pb;
+        mixed_shape(c, ld, bk.engine, g, sb, pb);
+        g = std::min<int64_t>(g, (int64_t)bk.subsets.size() * std::max(B, 1));
+        pcv_status st = alloc_workspace(c, bk.ws, g, sb, pb, ld, pcv::mixed_planes(bk.engine));
+        if (st != PCV_OK) return st;
+        CUDA_TRY(bk.order.reserve(bk.subsets.size()));
+        CUDA_TRY(cudaMemcpy(bk.order.p, bk.subsets.data(), bk.subsets.size() * sizeof(int32_t),
+                            cudaMemcpyHostToDevice));
+        CUDA_TRY(bk.counter.reserve(1));
+        CUDA_TRY(cudaStreamCreateWithFlags(&bk.stream, cudaStreamNonBlocking));
+        CUDA_TRY(cudaEventCreateWithFlags(&bk.done, cudaEventDisableTiming));
+        static const char* names[] = {"tensor-f16x2", "simt-f32", "tensor-bf16x3"};
+        char line[256];
+        std::snprintf(line, sizeof line, "k %d-%d: %zu subsets, engine %s, ld %d, %d slots%s\n", bk.klo, bk.khi,
+                      bk.subsets.size(), names[bk.engine], ld, bk.ws.grid, c->buckets_tuned ? " (tuned)" : "");
+        c->bucket_desc += line;
+    }
+    std::stable_sort(c->buckets.begin(), c->buckets.end(),
+                     [](const std::unique_ptr<Bucket>& x, const std::unique_ptr<Bucket>& y) { return x->work > y->work; });
+    if (!c->fork) CUDA_TRY(cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming));
+    return PCV_OK;
+}
+
+static pcv_status run_tasks(pcv_ctx* c, const double* d_params, int32_t B, int32_t prec, const int64_t* P_off,
+                            const double* Px, const double* Py, const double* Pv, const int32_t* order,
+                            int32_t n_order, double* d_yhat, int64_t yhat_stride, void* stream,
+                            bool want_lik = false, const int32_t* d_param_row = nullptr,
+                            const double* d_rhs = nullptr, int32_t nrhs = 0, bool lattice = false,
+                            bool bucketed = false) {
+    const int32_t N = c->plan.N;
+    CUDA_TRY(c->z.reserve((size_t)B * N));
+    CUDA_TRY(c->tst.reserve((size_t)B * N));
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((int64_t)n_order * B > 0 && prec == PCV_PREC_MIXED) {
+        int e = pcv::mixed_prepare(c->device);
+        if (e) return cuda_fail((cudaError_t)e, "mixed-path set-up");
+        if (bucketed) {
+            pcv_status st = ensure_buckets(c, d_params, B, s);
+            if (st != PCV_OK) return st;
+            CUDA_TRY(c->z.reserve((size_t)B * N));
+            CUDA_TRY(c->tst.reserve((size_t)B * N));
+        }
+    }
+    CUDA_TRY(cudaMemsetAsync(c->z.p, 0, (size_t)B * N * sizeof(double), s));
+    CUDA_TRY(cudaMemsetAsync(c->tst.p, 0, (size_t)B * N * sizeof(int32_t), s));
+    if (want_lik) {
+        CUDA_TRY(c->lik.reserve((size_t)B * N));
+        CUDA_TRY(cudaMemsetAsync(c->lik.p, 0, (size_t)B * N * sizeof(double), s));
+    }
+    if ((int64_t)n_order * B == 0) return PCV_OK;
+    pcv_status st = PCV_OK;
+    if (!(prec == PCV_PREC_MIXED && bucketed)) {
+        st = ensure_workspace(c, prec);
+        if (st != PCV_OK) return st;
+    }
+    if (prec == PCV_PREC_MIXED) {
+        st = ensure_workspace(c, kFallbackWs);   // fallback tasks run in FP64
+        if (st != PCV_OK) return st;
+        CUDA_TRY(c->fb_list.reserve((size_t)n_order * B));
+        CUDA_TRY(c->fb_count.reserve(2));
+        CUDA_TRY(cudaMemsetAsync(c->fb_count.p, 0, 2 * sizeof(unsigned int), s));
+    }
+    pcv::TaskArgs a = base_args(c, d_params, B, P_off, Px, Py, Pv, order, n_order, d_yhat, yhat_stride, want_lik,
+                                d_param_row, d_rhs, nrhs, lattice);
+    const bool timing = c->timing && !c->capturing;   // a captured record would not time the replay
+    if (timing) CUDA_TRY(cudaEventRecord(c->ev[0], s));
+    if (prec == PCV_PREC_MIXED && bucketed) {
+        // the buckets' persistent launches side by side, forked from and joined to `s`
+        CUDA_TRY(cudaEventRecord(c->fork, s));
+        for (auto& bp : c->buckets) {
+            Bucket& bk = *bp;
+            CUDA_TRY(cudaStreamWaitEvent(bk.stream, c->fork, 0));
+            CUDA_TRY(cudaMemsetAsync(bk.counter.p, 0, sizeof(unsigned int), bk.stream));
+            pcv::TaskArgs ab = a;
+            ab.order = bk.order.p;
+            ab.n_order = (int32_t)bk.subsets.size();
+            ab.counter = bk.counter.p;
+            with_workspace(ab, bk.ws);
+            const int grid = (int)std::min<int64_t>(bk.ws.grid, (int64_t)ab.n_order * B);
+            int e = pcv::launch_task_mixed(ab, bk.ws.maps, bk.engine, grid, bk.stream);
+            if (e) return cuda_fail((cudaError_t)e, "task kernel launch");
+            CUDA_TRY(cudaEventRecord(bk.done, bk.stream));
+            CUDA_TRY(cudaStreamWaitEvent(s, bk.done, 0));
+        }
+    } else {
+        Workspace& w = c->ws[prec];
+        CUDA_TRY(cudaMemsetAsync(c->counter.p, 0, sizeof(unsigned int), s));
+        with_workspace(a, w);
+        const int grid = (int)std::min<int64_t>(w.grid, (int64_t)n_order * B);
+        int e = prec == PCV_PREC_FP64 ? pcv::launch_task_fp64(a, grid, stream)
+                                      : pcv::launch_task_mixed(a, w.maps, c->opts.factor_engine, grid, stream);
+        if (e) return cuda_fail((cudaError_t)e, "task kernel launch");
+    }
+    if (timing) {
         CUDA_TRY(cudaEventRecord(c->ev[1], s));
         c->timed_task = true;
     }
@@ -554,17 +849,84 @@ static pcv_status run_tasks(pcv_ctx* c, const double* d_params, int32_t B, int32
         // its length stay on the device; CTAs beyond the list exit at once)
         Workspace& w64 = c->ws[kFallbackWs];
         pcv::TaskArgs f = a;
-        f.work = reinterpret_cast<double*>(w64.mem.p);
-        f.slot_bytes = w64.slot_bytes;
-        f.ld = w64.ld;
+        with_workspace(f, w64);
+        f.planes = nullptr;
         f.counter = c->fb_count.p + 1;
+        f.order = nullptr;                 // list entries are subset * B + configuration
         f.task_list = c->fb_list.p;
         f.task_count = c->fb_count.p;
         f.list_status = PCV_REFINE_FALLBACK;
-        e = pcv::launch_task_fp64(f, (int)std::min<int64_t>(w64.grid, (int64_t)n_order * B), stream);
+        int e = pcv::launch_task_fp64(f, (int)std::min<int64_t>(w64.grid, (int64_t)n_order * B), stream);
         if (e) return cuda_fail((cudaError_t)e, "fallback kernel launch");
     }
     return PCV_OK;
+}
+
+// Device buffers a captured graph of the CV call names; a graph is replayed only while
+// they are all where they were at capture time.
+static std::vector<const void*> graph_fingerprint(const pcv_ctx* c) {
+    std::vector<const void*> f = {c->z.p, c->tst.p, c->fb_list.p, c->fb_count.p, c->ws[kFallbackWs].mem.p,
+                                  c->phase.p, c->gparams.p, c->gsspe.p, c->gstatus.p, c->gyhat.p};
+    for (const auto& b : c->buckets) {
+        f.push_back(b->ws.mem.p);
+        f.push_back(b->ws.planes.p);
+        f.push_back(b->order.p);
+        f.push_back(b->counter.p);
+    }
+    return f;
+}
+
+// The CV call's device work: the task launches (bucketed for the mixed path), the FP64
+// fallback and the fixed-order combine.
+static pcv_status cv_work(pcv_ctx* c, const double* d_params, int32_t B, int32_t prec, double* d_sspe,
+                          double* d_yhat_valid, int32_t* d_status, cudaStream_t s) {
+    pcv_status st = run_tasks(c, d_params, B, prec, c->Voff.p, c->Vx.p, c->Vy.p, c->Vv.p, c->order.p, c->n_active,
+                              d_yhat_valid, c->nV, s, false, nullptr, nullptr, 0, true, true);
+    if (st != PCV_OK) return st;
+    const bool timing = c->timing && !c->capturing;
+    if (timing) CUDA_TRY(cudaEventRecord(c->ev[2], s));
+    int e = pcv::launch_combine(c->z.p, c->tst.p, d_params, B, c->plan.N, d_sspe, d_status, s);
+    if (e) return cuda_fail((cudaError_t)e, "combine launch");
+    if (timing) {
+        CUDA_TRY(cudaEventRecord(c->ev[3], s));
+        c->timed_combine = true;
+    }
+    return PCV_OK;
+}
+
+// Capture cv_work for B configurations into c->gexec (on the context's own capture
+// stream, so that any caller stream can replay it).  False if the capture did not work
+// out (the call then runs eagerly and this shape is not captured again).
+static bool capture_cv_graph(pcv_ctx* c, int32_t B, bool want_yhat) {
+    if (c->gexec) {
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+    }
+    if (c->gparams.reserve((size_t)3 * B) != cudaSuccess || c->gsspe.reserve(B) != cudaSuccess ||
+        c->gstatus.reserve(B) != cudaSuccess || (want_yhat && c->gyhat.reserve((size_t)B * c->nV) != cudaSuccess))
+        return false;
+    if (!c->gcap && cudaStreamCreateWithFlags(&c->gcap, cudaStreamNonBlocking) != cudaSuccess) return false;
+    if (cudaStreamBeginCapture(c->gcap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return false;
+    c->capturing = true;
+    const int64_t launches0 = pcv_launch_count(0);
+    const pcv_status st = cv_work(c, c->gparams.p, B, PCV_PREC_MIXED, c->gsspe.p, want_yhat ? c->gyhat.p : nullptr,
+                                  c->gstatus.p, c->gcap);
+    c->capturing = false;
+    // the captured kernels run at each replay, not now
+    c->graph_kernels = pcv_launch_count(0) - launches0;
+    pcv::count_launch((int)-c->graph_kernels);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(c->gcap, &g);
+    bool ok = st == PCV_OK && e == cudaSuccess && g;
+    if (ok) ok = cudaGraphInstantiate(&c->gexec, g, 0) == cudaSuccess;
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();   // a failed capture leaves no sticky error
+    if (!ok) {
+        c->gexec = nullptr;
+        return false;
+    }
+    c->gprint = graph_fingerprint(c);
+    return true;
 }
 
 PCV_API pcv_status pcv_cv_loss_device(pcv_ctx* c, const double* d_params, int32_t B, int32_t prec, double* d_sspe,
@@ -576,20 +938,45 @@ PCV_API pcv_status pcv_cv_loss_device(pcv_ctx* c, const double* d_params, int32_
     if (!d_params || !d_sspe) return fail(PCV_ERR_ARG, "NULL params or sspe");
     if (bad_precision(prec)) return fail(PCV_ERR_ARG, "unknown precision");
     CUDA_TRY(cudaSetDevice(c->device));
-    pcv_status st = run_tasks(c, d_params, B, prec, c->Voff.p, c->Vx.p, c->Vy.p, c->Vv.p, c->order.p, c->n_active,
-                              d_yhat_valid, c->nV, stream, false, nullptr, nullptr, 0, true);
-    if (st != PCV_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
     const int32_t N = c->plan.N;
-    if (c->timing) CUDA_TRY(cudaEventRecord(c->ev[2], (cudaStream_t)stream));
-    int e = pcv::launch_combine(c->z.p, c->tst.p, d_params, B, N, d_sspe, d_status, stream);
-    if (e) return cuda_fail((cudaError_t)e, "combine launch");
-    if (c->timing) {
-        CUDA_TRY(cudaEventRecord(c->ev[3], (cudaStream_t)stream));
-        c->timed_combine = true;
+    // repeated mixed calls of one shape replay a captured graph of the whole call
+    const bool graphable = prec == PCV_PREC_MIXED && c->opts.graph == 0 && c->n_active > 0;
+    const int64_t key = (int64_t)B * 4 + (d_yhat_valid ? 2 : 0) + (c->timing ? 1 : 0);
+    bool replay = false;
+    if (graphable) {
+        if (c->gexec && c->gkey == key && graph_fingerprint(c) == c->gprint) {
+            replay = true;
+        } else if (c->gseen == key) {
+            replay = capture_cv_graph(c, B, d_yhat_valid != nullptr);
+            c->gkey = replay ? key : -1;
+            if (!replay) c->gseen = -2;
+        } else if (c->gseen != -2) {
+            c->gseen = key;
+        }
+    }
+    if (replay) {
+        CUDA_TRY(cudaMemcpyAsync(c->gparams.p, d_params, (size_t)3 * B * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        if (c->timing) CUDA_TRY(cudaEventRecord(c->ev[0], s));
+        CUDA_TRY(cudaGraphLaunch(c->gexec, s));
+        pcv::count_launch((int)c->graph_kernels);
+        ++c->graph_launches;
+        if (c->timing) {
+            CUDA_TRY(cudaEventRecord(c->ev[1], s));
+            c->timed_task = true;
+            c->timed_combine = false;   // the combine is inside the timed graph
+        }
+        CUDA_TRY(cudaMemcpyAsync(d_sspe, c->gsspe.p, B * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        if (d_status) CUDA_TRY(cudaMemcpyAsync(d_status, c->gstatus.p, B * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+        if (d_yhat_valid && c->nV)
+            CUDA_TRY(cudaMemcpyAsync(d_yhat_valid, c->gyhat.p, (size_t)B * c->nV * sizeof(double),
+                                     cudaMemcpyDeviceToDevice, s));
+    } else {
+        pcv_status st = cv_work(c, d_params, B, prec, d_sspe, d_yhat_valid, d_status, s);
+        if (st != PCV_OK) return st;
     }
     if (d_sspe_per_subset)
-        CUDA_TRY(cudaMemcpyAsync(d_sspe_per_subset, c->z.p, (size_t)B * N * sizeof(double), cudaMemcpyDeviceToDevice,
-                                 (cudaStream_t)stream));
+        CUDA_TRY(cudaMemcpyAsync(d_sspe_per_subset, c->z.p, (size_t)B * N * sizeof(double), cudaMemcpyDeviceToDevice, s));
     return PCV_OK;
 }
 
@@ -963,6 +1350,17 @@ PCV_API const char* pcv_status_str(int32_t s) {
 PCV_API const char* pcv_last_error(void) { return g_err.c_str(); }
 
 PCV_API int32_t pcv_version(void) { return 1; }
+
+PCV_API int32_t pcv_buckets(const pcv_ctx* c, char* buf, int32_t cap) {
+    if (!c) return 0;
+    const std::string& d = c->bucket_desc;
+    if (buf && cap > 0) {
+        const size_t n = std::min<size_t>(d.size(), (size_t)cap - 1);
+        std::memcpy(buf, d.data(), n);
+        buf[n] = 0;
+    }
+    return (int32_t)d.size();
+}
 
 PCV_API int32_t pcv_lattice(const pcv_ctx* c, double* hx, double* hy) {
     if (!c || !c->lattice) return 0;

@@ -319,7 +319,7 @@ __global__ void __launch_bounds__(NT, 1) k_cv_fp64(TaskArgs a) {
         __syncthreads();
         if (t >= ntask) break;
         if (a.task_list) t = a.task_list[t];
-        run_task(sm, a, a.order[t / a.B], t % a.B);
+        run_task(sm, a, a.order ? a.order[t / a.B] : t / a.B, t % a.B);
     }
 }
 

@@ -1169,6 +1169,165 @@ __device__ void residual_df(SmemM& sm, const float* tbl, const SlotM& S, int k, 
     __syncthreads();
 }
 
+// Lattice data: r = y - A x over the whole matrix, each row owned by one warp.  A warp
+// takes RB rows at a time; its lanes walk the columns (the column's lattice indices and
+// solution value loaded once for all RB rows), each entry a table read by index offset
+// and one double-float product added to the row's accumulator; a butterfly of
+// double-float additions then sums the lanes.  Every entry is read twice (A_ab and
+// A_ba) instead of feeding a row and a column sum, which costs one table read more per
+// entry but no block-wide reduction or barrier per tile.  The diagonal comes from the
+// table's (0, 0) entry, exactly 1, so the sum holds Sigma x and r = y - (sum + lambda x)
+// in FP64.
+template <int RB>
+__device__ void residual_lat(const SlotM& S, int k, double lam, int W) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int* ti = reinterpret_cast<const int*>(S.xh);
+    const int* tj = reinterpret_cast<const int*>(S.yh);
+    const float2* __restrict__ tab = S.tab;
+    for (int a0 = warp * RB; a0 < k; a0 += (NT / 32) * RB) {
+        int ia[RB], ja[RB];
+        dfm::acc racc[RB];
+#pragma unroll
+        for (int u = 0; u < RB; ++u) {
+            const int a = min(a0 + u, k - 1);
+            ia[u] = ti[a];
+            ja[u] = tj[a];
+        }
+        for (int b = lane; b < k; b += 32) {
+            const int ib = ti[b], jb = tj[b];
+            const df xb{S.qh[b], S.ql[b]};
+            float2 e[RB];
+#pragma unroll
+            for (int u = 0; u < RB; ++u) e[u] = tab[abs(ia[u] - ib) * W + abs(ja[u] - jb)];
+#pragma unroll
+            for (int u = 0; u < RB; ++u) racc[u].add_prod(df{e[u].x, e[u].y}, xb);
+        }
+        double mine = 0.0;
+#pragma unroll
+        for (int u = 0; u < RB; ++u) {
+            df v = racc[u].value();
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const df w{__shfl_xor_sync(0xffffffffu, v.h, o), __shfl_xor_sync(0xffffffffu, v.l, o)};
+                v = dfm::add(v, w);
+            }
+            if (lane == u) mine = (double)v.h + (double)v.l;
+        }
+        const int a = a0 + lane;
+        if (lane < RB && a < k) S.rr[a] = S.yv[a] - (mine + lam * S.xs[a]);
+    }
+    __syncthreads();
+}
+
+// Predictions (Eq. 3) of the task's m points in double-float from the solution in
+// (R.qh, R.ql), two points per warp, lanes over the training points; each written to
+// yhat (row yrow) when a.yhat is set, its squared error (Eq. 4) to R.ep when a.Pv is.
+// With dc (a correction of the solution, FP32, k entries) each point also gets
+// u_j = sum_a Sigma_ja dc_a in plain FP32 -- the change dc makes to the prediction, for
+// the refinement's stopping rule -- and the block-wide statistics are returned:
+// sum (yhat - y)^2, sum yhat^2, sum u^2 and max |u|.  Block-synchronous.
+struct PredStats {
+    double sse, ysq, usq;
+    float umax;
+};
+
+template <bool LAT>
+__device__ PredStats predict_points(SmemM& sm, const SmemKeep& keep, const TaskArgs& a, const SlotM& R, int k,
+                                    int m, int64_t p0, double ox, double oy, double sc, int W, int64_t yrow,
+                                    const float* dc) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    double ysq = 0.0, usq = 0.0;
+    float umax = 0.0f;
+    for (int j0 = 2 * warp; j0 < m; j0 += 2 * (NT / 32)) {   // two prediction points per warp
+        const int j1 = min(j0 + 1, m - 1);
+        Pt P0, P1;
+        if constexpr (LAT) {
+            P0 = Pt{__int_as_float(a.PLX[p0 + j0]), 0.0f, __int_as_float(a.PLY[p0 + j0]), 0.0f};
+            P1 = Pt{__int_as_float(a.PLX[p0 + j1]), 0.0f, __int_as_float(a.PLY[p0 + j1]), 0.0f};
+        } else {
+            const df px0 = dfm::from_double((a.Px[p0 + j0] - ox) * sc), py0 = dfm::from_double((a.Py[p0 + j0] - oy) * sc);
+            const df px1 = dfm::from_double((a.Px[p0 + j1] - ox) * sc), py1 = dfm::from_double((a.Py[p0 + j1] - oy) * sc);
+            P0 = Pt{px0.h, px0.l, py0.h, py0.l};
+            P1 = Pt{px1.h, px1.l, py1.h, py1.l};
+        }
+        dfm::acc s0, s1;
+        float u0 = 0.0f, u1 = 0.0f;
+        for (int q = lane; q < k; q += 32) {
+            const Pt Q{R.xh[q], LAT ? 0.0f : R.xl[q], R.yh[q], LAT ? 0.0f : R.yl[q]};
+            const df xq{R.qh[q], R.ql[q]};
+            df e0, e1;
+            if constexpr (LAT) {
+                e0 = lat_cov(R.tab, W, P0, Q);
+                e1 = lat_cov(R.tab, W, P1, Q);
+            } else {
+                e0 = exp_neg_sm(keep.tbl, t_any(P0, Q));
+                e1 = exp_neg_sm(keep.tbl, t_any(P1, Q));
+            }
+            s0.add_prod(e0, xq);
+            s1.add_prod(e1, xq);
+            if (dc) {
+                const float d = dc[q];
+                u0 = fmaf(e0.h, d, u0);
+                u1 = fmaf(e1.h, d, u1);
+            }
+        }
+        const double v0 = warp_sum_d((double)s0.h + (double)s0.l);
+        const double v1 = warp_sum_d((double)s1.h + (double)s1.l);
+        if (dc) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                u0 += __shfl_xor_sync(0xffffffffu, u0, o);
+                u1 += __shfl_xor_sync(0xffffffffu, u1, o);
+            }
+        }
+        if (lane < 2 && (lane == 0 || j1 != j0)) {
+            const int j = lane == 0 ? j0 : j1;
+            const double v = lane == 0 ? v0 : v1;
+            const float u = lane == 0 ? u0 : u1;
+            if (a.yhat) a.yhat[yrow * a.yhat_stride + p0 + j] = v;
+            if (a.Pv) {
+                const double e = v - a.Pv[p0 + j];
+                R.ep[j] = e * e;
+            }
+            ysq += v * v;
+            usq += (double)u * (double)u;
+            umax = fmaxf(umax, fabsf(u));
+        }
+    }
+    __syncthreads();
+    PredStats st{0.0, 0.0, 0.0, 0.0f};
+    double sse = 0.0;
+    if (a.Pv)
+        for (int j = tid; j < m; j += NT) sse += R.ep[j];
+    sse = warp_sum_d(sse);
+    if (dc) {
+        ysq = warp_sum_d(ysq);
+        usq = warp_sum_d(usq);
+        umax = warp_max(umax);
+    }
+    if (lane == 0) {
+        sm.dred[warp] = sse;
+        sm.dred2[warp] = ysq;
+        sm.fred[warp] = umax;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int w = 0; w < NT / 32; ++w) {
+        st.sse += sm.dred[w];
+        st.ysq += sm.dred2[w];
+        st.umax = fmaxf(st.umax, sm.fred[w]);
+    }
+    __syncthreads();
+    if (dc) {
+        if (lane == 0) sm.dred[warp] = usq;
+        __syncthreads();
+#pragma unroll
+        for (int w = 0; w < NT / 32; ++w) st.usq += sm.dred[w];
+        __syncthreads();
+    }
+    return st;
+}
+
 // ---------------------------------------------------------------- one task
 
 template <bool TC, class Sch = umma::SplitBF16x3, bool EXT = false, bool LAT = false>
@@ -1462,6 +1621,10 @@ __device__ void run_task(SmemM& sm, SmemKeep& keep, SmemSimt* simt, TcCtx* tc, c
             }
             __syncthreads();
         }
+        // the loss-aware stopping rule serves the plain variant's CV and prediction tasks
+        // whose prediction points cost no more than a residual pass
+        const bool loss_rule = !EXT && a.refine_loss_tol > 0.0 && m <= k;
+        bool have_pred = false;       // the predictions of the final solution are done
         if (ok) {
             // iterative refinement: x += L^-T L^-1 r
             ok = false;
@@ -1496,24 +1659,48 @@ __device__ void run_task(SmemM& sm, SmemKeep& keep, SmemSimt* simt, TcCtx* tc, c
                     if (a.phase_cycles && tid == 0) atomicAdd(a.phase_cycles + kPhFailNaN, 1ull);
                     break;
                 }
-                if (it >= 1) {
-                    if (dmax > 0.5f * dprev) {                             // not contracting
-                        if (a.phase_cycles && tid == 0) atomicAdd(a.phase_cycles + kPhFailStall, 1ull);
-                        break;
-                    }
-                    // error left after this correction ~ |d_i| * (|d_i| / |d_i-1|)
-                    const float est = dmax * (dmax / fmaxf(dprev, 1e-30f));
-                    if (est <= (float)a.refine_tol * xmax) { ok = true; break; }
-                }
-                dprev = dmax;
-                if (it == a.refine_max_iter) break;
                 for (int q = tid; q < k; q += NT) {
                     const df v = dfm::from_double(R.xs[q]);
                     R.qh[q] = v.h;
                     R.ql[q] = v.l;
                 }
                 __syncthreads();
-                residual_df<LAT>(sm, keep.tbl, R, k, lam, W);
+                if (it >= 1) {
+                    if (dmax > 0.5f * dprev) {                             // not contracting
+                        if (a.phase_cycles && tid == 0) atomicAdd(a.phase_cycles + kPhFailStall, 1ull);
+                        break;
+                    }
+                    // error left after this correction ~ c |d_i|, c = |d_i| / |d_i-1| the
+                    // observed contraction; the solution rule stops when that is small
+                    // against |x|
+                    const float c = dmax / fmaxf(dprev, 1e-30f);
+                    if (c * dmax <= (float)a.refine_tol * xmax) { ok = true; break; }
+                    if (loss_rule) {
+                        // loss-aware rule: the predictions of x_i and the change u = K d_i the
+                        // last correction made to them; the error left in the predictions is
+                        // estimated as g |u|, g = c / (1 - c) (the corrections still to come
+                        // shrink geometrically).  Stop when it moves the local SSPE (Eq. 4)
+                        // by at most refine_loss_tol relative -- |dz| <= 2 |yhat - y| |dyhat|
+                        // -- and every prediction by at most 10 refine_loss_tol of their RMS.
+                        const PredStats ps = predict_points<LAT>(sm, keep, a, R, k, m, p0, ox, oy, sc, W,
+                                                                 (int64_t)b, R.w);
+                        tm.lap(kPhPredict);
+                        const double g = (double)c / (1.0 - (double)c);
+                        const double lt = a.refine_loss_tol;
+                        const bool loss_ok = !a.Pv || 2.0 * g * sqrt(ps.usq) <= lt * sqrt(ps.sse);
+                        const bool pred_ok = g * (double)ps.umax <= 10.0 * lt * sqrt(ps.ysq / (double)max(m, 1));
+                        if (loss_ok && pred_ok) {
+                            ok = true;
+                            have_pred = true;
+                            if (a.Pv && tid == 0) a.z[zoff] = ps.sse;
+                            break;
+                        }
+                    }
+                }
+                dprev = dmax;
+                if (it == a.refine_max_iter) break;
+                if constexpr (LAT) residual_lat<4>(R, k, lam, W);
+                else residual_df<LAT>(sm, keep.tbl, R, k, lam, W);
                 tm.lap(kPhResidual);
                 if (a.phase_cycles && tid == 0) atomicAdd(a.phase_cycles + kPhResidualPasses, 1ull);
             }
@@ -1524,7 +1711,7 @@ __device__ void run_task(SmemM& sm, SmemKeep& keep, SmemSimt* simt, TcCtx* tc, c
             if (tid == 0) {
                 a.tstatus[zoff] = PCV_REFINE_FALLBACK;
                 const unsigned pos = atomicAdd(a.fb_count, 1u);
-                a.fb_list[pos] = t;
+                a.fb_list[pos] = i * a.B + b;   // (subset, configuration), whatever launch order ran it
             }
             __syncthreads();
             return;
@@ -1558,61 +1745,12 @@ __device__ void run_task(SmemM& sm, SmemKeep& keep, SmemSimt* simt, TcCtx* tc, c
             __syncthreads();
         }
 
-        // predict (Eq. 3) in double-float, squared errors in FP64 (Eq. 4)
-        for (int q = tid; q < k; q += NT) {
-            const df v = dfm::from_double(R.xs[q]);
-            R.qh[q] = v.h;
-            R.ql[q] = v.l;
-        }
-        __syncthreads();
-        for (int j0 = 2 * warp; j0 < m; j0 += 2 * (NT / 32)) {   // two prediction points per warp
-            const int j1 = min(j0 + 1, m - 1);
-            Pt P0, P1;
-            if constexpr (LAT) {
-                P0 = Pt{__int_as_float(a.PLX[p0 + j0]), 0.0f, __int_as_float(a.PLY[p0 + j0]), 0.0f};
-                P1 = Pt{__int_as_float(a.PLX[p0 + j1]), 0.0f, __int_as_float(a.PLY[p0 + j1]), 0.0f};
-            } else {
-                const df px0 = dfm::from_double((a.Px[p0 + j0] - ox) * sc), py0 = dfm::from_double((a.Py[p0 + j0] - oy) * sc);
-                const df px1 = dfm::from_double((a.Px[p0 + j1] - ox) * sc), py1 = dfm::from_double((a.Py[p0 + j1] - oy) * sc);
-                P0 = Pt{px0.h, px0.l, py0.h, py0.l};
-                P1 = Pt{px1.h, px1.l, py1.h, py1.l};
-            }
-            dfm::acc s0, s1;
-            for (int q = lane; q < k; q += 32) {
-                const Pt Q{R.xh[q], LAT ? 0.0f : R.xl[q], R.yh[q], LAT ? 0.0f : R.yl[q]};
-                const df xq{R.qh[q], R.ql[q]};
-                if constexpr (LAT) {
-                    s0.add_prod(lat_cov(R.tab, W, P0, Q), xq);
-                    s1.add_prod(lat_cov(R.tab, W, P1, Q), xq);
-                } else {
-                    s0.add_prod(exp_neg_sm(keep.tbl, t_any(P0, Q)), xq);
-                    s1.add_prod(exp_neg_sm(keep.tbl, t_any(P1, Q)), xq);
-                }
-            }
-            const double v0 = warp_sum_d((double)s0.h + (double)s0.l);
-            const double v1 = warp_sum_d((double)s1.h + (double)s1.l);
-            if (lane < 2 && (lane == 0 || j1 != j0)) {
-                const int j = lane == 0 ? j0 : j1;
-                const double v = lane == 0 ? v0 : v1;
-                if (a.yhat) a.yhat[(int64_t)(EXT && a.rhs ? rh : b) * a.yhat_stride + p0 + j] = v;
-                if (a.Pv) {
-                    const double e = v - a.Pv[p0 + j];
-                    R.ep[j] = e * e;
-                }
-            }
-        }
-        __syncthreads();
-        if (a.Pv) {
-            double s = 0.0;
-            for (int j = tid; j < m; j += NT) s += R.ep[j];
-            s = warp_sum_d(s);
-            if (lane == 0) sm.dred[warp] = s;
-            __syncthreads();
-            if (tid == 0) {
-                double zz = 0.0;
-                for (int w = 0; w < NT / 32; ++w) zz += sm.dred[w];
-                a.z[zoff] = zz;
-            }
+        // predict (Eq. 3) in double-float, squared errors in FP64 (Eq. 4), unless the
+        // stopping rule already did so for the final solution
+        if (!have_pred) {
+            const PredStats ps = predict_points<LAT>(sm, keep, a, R, k, m, p0, ox, oy, sc, W,
+                                                     (int64_t)(EXT && a.rhs ? rh : b), nullptr);
+            if (a.Pv && tid == 0) a.z[zoff] = ps.sse;
         }
     }
     if (tid == 0) a.tstatus[zoff] = PCV_OK;

@@ -42,25 +42,45 @@ struct Layout {
 
 size_t align256(size_t v) { return (v + 255) / 256 * 256; }
 
-// Subsets with validation data, in ascending order (one CTA, block-wide scan).
-__global__ void __launch_bounds__(kOrderThreads) k_active_order(const int64_t* V_off, int32_t N, int32_t* order) {
-    __shared__ int32_t cnt[kOrderThreads];
+// Subsets with validation data, longest training set first, so that the persistent
+// CTAs finish together (the order pcv_cv_loss_device uses): one CTA, a counting sort by
+// training size in shared memory (sizes 0 .. kmax, kmax <= kMaxOrderK; ties in any
+// order, which changes no result: every task is computed on its own and the losses
+// are summed in subset order).
+constexpr int kMaxOrderK = 4096;
+__global__ void __launch_bounds__(kOrderThreads) k_active_order(const int64_t* T_off, const int64_t* V_off, int32_t N,
+                                                              int32_t kmax, int32_t* order) {
+    __shared__ int32_t cnt[kMaxOrderK + 1];
+    __shared__ int32_t part[kOrderThreads];
     const int t = threadIdx.x;
-    const int32_t per = (N + kOrderThreads - 1) / kOrderThreads;
-    const int32_t lo = min(N, t * per), hi = min(N, lo + per);
+    for (int q = t; q <= kmax; q += kOrderThreads) cnt[q] = 0;
+    __syncthreads();
+    for (int32_t i = t; i < N; i += kOrderThreads)
+        if (V_off[i + 1] > V_off[i]) atomicAdd(&cnt[(int)(T_off[i + 1] - T_off[i])], 1);
+    __syncthreads();
+    // exclusive scan from the largest size down: start[q] = active subsets larger than q.
+    // Thread t owns sizes kmax - t*per .. (descending), a chunk of per values.
+    const int per = (kmax + 1 + kOrderThreads - 1) / kOrderThreads;
+    const int hi = kmax - t * per, lo = max(-1, hi - per);   // sizes hi down to lo + 1
     int32_t c = 0;
-    for (int32_t i = lo; i < hi; ++i) c += V_off[i + 1] > V_off[i];
-    cnt[t] = c;
+    for (int q = hi; q > lo; --q) c += cnt[q];
+    part[t] = c;
     __syncthreads();
     for (int off = 1; off < kOrderThreads; off <<= 1) {   // inclusive Hillis-Steele scan
-        int32_t v = t >= off ? cnt[t - off] : 0;
+        const int32_t v = t >= off ? part[t - off] : 0;
         __syncthreads();
-        cnt[t] += v;
+        part[t] += v;
         __syncthreads();
     }
-    int32_t pos = cnt[t] - c;
-    for (int32_t i = lo; i < hi; ++i)
-        if (V_off[i + 1] > V_off[i]) order[pos++] = i;
+    int32_t run = part[t] - c;
+    for (int q = hi; q > lo; --q) {
+        const int32_t n = cnt[q];
+        cnt[q] = run;
+        run += n;
+    }
+    __syncthreads();
+    for (int32_t i = t; i < N; i += kOrderThreads)
+        if (V_off[i + 1] > V_off[i]) order[atomicAdd(&cnt[(int)(T_off[i + 1] - T_off[i])], 1)] = i;
 }
 
 cudaError_t scratch_address(int dev, unsigned char** out) {
@@ -88,6 +108,11 @@ PCV_API pcv_status pcv_cv_loss_fp64_static(const double* d_x, const double* d_y,
     if (N < 1 || B < 0 || !h_T_off || !h_V_off) return PCV_ERR_ARG;
     if (B == 0) return PCV_OK;
     if (!d_x || !d_y || !d_v || !d_T_idx || !d_Vx || !d_Vy || !d_Vv || !d_params || !d_sspe) return PCV_ERR_ARG;
+    // offsets index the caller's arrays from their first entry on
+    if (h_T_off[0] < 0 || h_V_off[0] < 0) return PCV_ERR_ARG;
+    // the per-task results (12 bytes each) alone must fit, checked before any size
+    // arithmetic that could wrap
+    if ((uint64_t)B * (uint64_t)N > (uint64_t)(kScratchBytes / 12)) return PCV_ERR_ARG;
     int32_t kmax = 0, n_active = 0;
     int64_t mmax = 0;
     for (int32_t i = 0; i < N; ++i) {
@@ -111,6 +136,7 @@ PCV_API pcv_status pcv_cv_loss_fp64_static(const double* d_x, const double* d_y,
     L.slots = align256(L.tst + (size_t)B * N * sizeof(int32_t));
     L.slot_bytes = (size_t)slot_bytes_fp64(L.ld, mmax);
     if (L.slots + L.slot_bytes > kScratchBytes) return PCV_ERR_ARG;   // problem exceeds the static scratch
+    static_assert((size_t)8 * kMaxOrderK * kMaxOrderK > kScratchBytes, "a slot bounds the training size");
     int sms = 0, dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return PCV_ERR_CUDA;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return PCV_ERR_CUDA;
@@ -133,7 +159,7 @@ PCV_API pcv_status pcv_cv_loss_fp64_static(const double* d_x, const double* d_y,
         cudaMemsetAsync(z, 0, (size_t)B * N * sizeof(double), s) != cudaSuccess ||
         cudaMemsetAsync(tst, 0, (size_t)B * N * sizeof(int32_t), s) != cudaSuccess)
         return PCV_ERR_CUDA;
-    k_active_order<<<1, kOrderThreads, 0, s>>>(Voff, N, order);
+    k_active_order<<<1, kOrderThreads, 0, s>>>(Toff, Voff, N, kmax, order);
     count_launch();
     if (cudaGetLastError() != cudaSuccess) return PCV_ERR_CUDA;
     if (n_active > 0) {

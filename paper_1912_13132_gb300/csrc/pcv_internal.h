@@ -43,7 +43,7 @@ struct TaskArgs {
     const double* Px;
     const double* Py;
     const double* Pv;       // observed values at the prediction points (NULL: no loss)
-    const int32_t* order;   // subsets to process, longest first
+    const int32_t* order;   // subsets to process, longest first (NULL: task t is subset t / B)
     int32_t n_order;
     const double* params;   // B x 3 (sigma2, rho, tau2), device
     int32_t B;
@@ -65,11 +65,13 @@ struct TaskArgs {
     int32_t ld;             // leading dimension of the slot matrix (multiple of 128)
     int32_t refine_max_iter;
     double refine_tol;
+    double refine_loss_tol;  // loss-aware stopping rule of the refinement (<= 0: solution rule only)
     double coord_scale;     // power of two: scaled offsets inside one window are below 1 in magnitude
     // mixed path: tasks that need the FP64 fallback are appended here
     int32_t* fb_list;
     unsigned int* fb_count;
-    // FP64 path in list mode: run only the tasks task_list[0 .. *task_count)
+    // FP64 path in list mode: run only the tasks task_list[0 .. *task_count) (entries
+    // subset * B + configuration, the mixed kernels' fallback list, with order NULL)
     const int32_t* task_list;
     const unsigned int* task_count;
     int32_t list_status;    // status written for a task finished in list mode

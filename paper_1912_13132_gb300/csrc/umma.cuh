@@ -175,6 +175,18 @@ __device__ __forceinline__ void mma_f16kind(uint32_t d_tmem, uint64_t a_desc, ui
         "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
         : "memory");
 }
+// kind::tf32: A and B are FP32 words of which the tensor core uses the TF32 part (8-bit
+// exponent, 10 explicit mantissa bits); one instruction covers K = 8 (32 bytes per row,
+// the same byte footprint as K = 16 of a 16-bit kind::f16 operand).  Format code 2.
+constexpr uint32_t kFmtTF32 = 2;
+__device__ __forceinline__ void mma_tf32kind(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                             uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                  : "memory");

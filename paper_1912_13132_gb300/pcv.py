@@ -36,7 +36,8 @@ class pcv_layout(ctypes.Structure):
 class pcv_options(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_int32), ("max_slots", ctypes.c_int32),
                 ("workspace_fraction", ctypes.c_double), ("refine_max_iter", ctypes.c_int32),
-                ("refine_tol", ctypes.c_double), ("factor_engine", ctypes.c_int32), ("tc_stages", ctypes.c_int32)]
+                ("refine_tol", ctypes.c_double), ("factor_engine", ctypes.c_int32), ("tc_stages", ctypes.c_int32),
+                ("refine_loss_tol", ctypes.c_double), ("bucketing", ctypes.c_int32), ("graph", ctypes.c_int32)]
 
 
 class pcv_server_options(ctypes.Structure):
@@ -86,6 +87,8 @@ _SIGS = {
     "pcv_selftest_umma": (ctypes.c_int, [ctypes.POINTER(ctypes.c_float), ctypes.c_int32,
                                          ctypes.POINTER(ctypes.c_float), ctypes.c_int32,
                                          ctypes.POINTER(ctypes.c_float)]),
+    "pcv_buckets": (ctypes.c_int32, [_vp, ctypes.c_char_p, ctypes.c_int32]),
+    "pcv_measure_peak": (ctypes.c_int, [ctypes.c_int32, ctypes.c_double, _dp, _dp]),
     "pcv_server_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int32, ctypes.POINTER(pcv_server_options),
                                          ctypes.POINTER(_vp)]),
     "pcv_server_submit_cv": (ctypes.c_int, [_vp, ctypes.c_int32, _dp, _i64p]),
@@ -215,13 +218,14 @@ class Context:
 
     def __init__(self, xy, v, role, layout: dict, device: int = 0, max_slots: int = 0,
                  workspace_fraction: float = 0.0, refine_max_iter: int = 0, refine_tol: float = 0.0,
-                 factor_engine: str = "tensor", tc_stages: int = 0):
+                 factor_engine: str = "tensor", tc_stages: int = 0, refine_loss_tol: float = 0.0,
+                 bucketing: int = 0, graph: int = 0):
         xy = _f64(xy).reshape(-1, 2)
         v = _f64(v)
         role = np.ascontiguousarray(role, dtype=np.uint8)
         L, keep = make_layout(layout)
         o = pcv_options(ctypes.sizeof(pcv_options), max_slots, workspace_fraction, refine_max_iter,
-                        refine_tol, ENGINES[factor_engine], tc_stages)
+                        refine_tol, ENGINES[factor_engine], tc_stages, refine_loss_tol, bucketing, graph)
         h = _vp()
         _check(_lib.pcv_create(_ptr(xy, _dp), _ptr(v, _dp), _ptr(role, _u8p), len(v), ctypes.byref(L),
                                device, ctypes.byref(o), ctypes.byref(h)), "pcv_create")
@@ -286,6 +290,13 @@ class Context:
     PHASES = ("gather_assemble", "tc_update", "diag", "panel_solve", "diag_io", "factor_simt", "solves",
               "residual", "predict_loss", "task", "residual_passes", "tasks", "fail_factor", "fail_nan",
               "fail_stall")
+
+    def buckets(self) -> str:
+        """The mixed CV launch's size buckets (pcv_buckets), '' before the first mixed call."""
+        n = _lib.pcv_buckets(self._h, None, 0)
+        buf = ctypes.create_string_buffer(n + 1)
+        _lib.pcv_buckets(self._h, buf, n + 1)
+        return buf.value.decode()
 
     def lattice(self):
         """(hx, hy) when every point lies on one regular lattice, else None (pcv_lattice)."""
@@ -476,6 +487,18 @@ def pcv_selftest_umma(A, B):
     st = _lib.pcv_selftest_umma(A.ctypes.data_as(fp), A.shape[0], B.ctypes.data_as(fp), A.shape[1],
                                 C.ctypes.data_as(fp))
     return int(st), C
+
+
+PEAK_KINDS = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16": 3, "fp16": 4}
+
+
+def pcv_measure_peak(kind: str, seconds: float = 2.0) -> dict:
+    """Device throughput probe (dense FMA or tcgen05 MMA) on the current device:
+    {'tflops': achieved TFLOP/s, 'seconds': timed duration}."""
+    t, e = ctypes.c_double(), ctypes.c_double()
+    _check(_lib.pcv_measure_peak(PEAK_KINDS[kind], float(seconds), ctypes.byref(t), ctypes.byref(e)),
+           "pcv_measure_peak")
+    return dict(tflops=t.value, seconds=e.value)
 
 
 def pcv_lattice_detect(xy):

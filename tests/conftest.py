@@ -1,6 +1,11 @@
 import os
 import sys
 
+# The oracle's LAPACK-backed kriging runs many subsets on a thread pool; one BLAS thread
+# per call keeps the pool from oversubscribing the host cores.  Set before numpy loads.
+for _v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))

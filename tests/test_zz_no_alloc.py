@@ -59,6 +59,60 @@ def test_static_scratch_matches_regular_entry(gpu_lib):
             assert np.all(np.abs(za - zr) <= TOL * np.abs(zr) + 1e-300)
 
 
+def test_static_scratch_bad_row_optional_outputs_and_no_validation(gpu_lib):
+    """An invalid configuration row gives its own PCV_ERR_ARG status and a NaN loss while
+    the others evaluate; the optional outputs may be NULL; a layout whose cores hold no
+    validation data runs no task and returns zero losses -- each as the regular entry
+    point does."""
+    import torch
+
+    pcv = gpu_lib
+    w = datagen.make_uniform(900, 400, 3, 0.06, seed=4243, name="noalloc-bad")
+    P = np.array([[1.0, 0.1, 0.05], [1.0, -0.1, 0.05], [0.7, 0.08, 0.02]])
+    d_p = torch.tensor(P, dtype=torch.float64, device="cuda")
+    with pcv.Context(w.xy, w.v, w.role, w.layout) as ctx:
+        inp = _device_inputs(ctx, w, torch)
+        ref = torch.empty(3, dtype=torch.float64, device="cuda")
+        ref_st = torch.empty(3, dtype=torch.int32, device="cuda")
+        ctx.cv_loss_device(d_p, ref, precision="fp64", d_status=ref_st)
+        out = torch.full((3,), -1.0, dtype=torch.float64, device="cuda")
+        st = torch.full((3,), -1, dtype=torch.int32, device="cuda")
+        rc = pcv.pcv_cv_loss_fp64_static(inp["d_x"], inp["d_y"], inp["d_v"], ctx.T_off, inp["d_T_idx"],
+                                         ctx.V_off, inp["d_Vx"], inp["d_Vy"], inp["d_Vv"], d_p, out,
+                                         d_status=st)
+        assert rc == pcv.PCV_OK
+        out2 = torch.full((3,), -1.0, dtype=torch.float64, device="cuda")
+        rc = pcv.pcv_cv_loss_fp64_static(inp["d_x"], inp["d_y"], inp["d_v"], ctx.T_off, inp["d_T_idx"],
+                                         ctx.V_off, inp["d_Vx"], inp["d_Vy"], inp["d_Vv"], d_p, out2)
+        assert rc == pcv.PCV_OK
+        torch.cuda.synchronize()
+        a, a2, r = out.cpu().numpy(), out2.cpu().numpy(), ref.cpu().numpy()
+        assert st.cpu().numpy().tolist() == ref_st.cpu().numpy().tolist() == [0, pcv.PCV_ERR_ARG, 0]
+        assert np.isnan(a[1]) and np.isnan(a2[1]) and np.isnan(r[1])
+        for x in (a, a2):
+            assert np.all(np.abs(x[[0, 2]] - r[[0, 2]]) <= TOL * np.abs(r[[0, 2]])), (x, r)
+    # no validation data anywhere: every subset is skipped (Sec. 4.3.1)
+    role = np.zeros_like(w.role)
+    with pcv.Context(w.xy, w.v, role, w.layout) as ctx:
+        inp = _device_inputs(ctx, w, torch)
+        assert ctx.V_off[-1] == 0
+        for key in ("d_Vx", "d_Vy", "d_Vv"):      # no validation points: a placeholder, never read
+            inp[key] = torch.zeros(1, dtype=torch.float64, device="cuda")
+        ref = torch.empty(3, dtype=torch.float64, device="cuda")
+        ref_st = torch.empty(3, dtype=torch.int32, device="cuda")
+        ctx.cv_loss_device(d_p, ref, precision="fp64", d_status=ref_st)
+        out = torch.full((3,), -1.0, dtype=torch.float64, device="cuda")
+        st = torch.full((3,), -1, dtype=torch.int32, device="cuda")
+        rc = pcv.pcv_cv_loss_fp64_static(inp["d_x"], inp["d_y"], inp["d_v"], ctx.T_off, inp["d_T_idx"],
+                                         ctx.V_off, inp["d_Vx"], inp["d_Vy"], inp["d_Vv"], d_p, out,
+                                         d_status=st)
+        assert rc == pcv.PCV_OK
+        torch.cuda.synchronize()
+        a, r = out.cpu().numpy(), ref.cpu().numpy()
+        assert st.cpu().numpy().tolist() == ref_st.cpu().numpy().tolist()
+        assert a[0] == r[0] == 0.0 and a[2] == r[2] == 0.0 and np.isnan(a[1]) == np.isnan(r[1])
+
+
 def test_static_scratch_rejects_oversized(gpu_lib):
     import torch
 
@@ -71,4 +125,10 @@ def test_static_scratch_rejects_oversized(gpu_lib):
     P = torch.tensor([[1.0, 0.1, 0.05]], dtype=torch.float64, device="cuda")
     out = torch.empty(1, dtype=torch.float64, device="cuda")
     rc = pcv.pcv_cv_loss_fp64_static(d, d, d, T_off, idx, V_off, d, d, d, P, out)
+    assert rc == pcv.PCV_ERR_ARG
+    # offsets that would index before the caller's arrays
+    rc = pcv.pcv_cv_loss_fp64_static(d, d, d, np.array([-5, 10], dtype=np.int64), idx, V_off, d, d, d, P, out)
+    assert rc == pcv.PCV_ERR_ARG
+    rc = pcv.pcv_cv_loss_fp64_static(d, d, d, np.array([0, 10], dtype=np.int64), idx,
+                                     np.array([-1, 5], dtype=np.int64), d, d, d, P, out)
     assert rc == pcv.PCV_ERR_ARG
