@@ -139,9 +139,10 @@ typedef struct {
     int32_t tc_stages;         /* tensor engines: depth of the TMA operand ring, 2 to 4 (0 =
                                   default: 3 for engine 0, 2 for engine 2); rings above
                                   96 KB leave one CTA per SM */
-    double refine_loss_tol;    /* mixed path, loss-aware stopping rule (default 1e-7; < 0
+    double refine_loss_tol;    /* mixed path, loss-aware stopping rule (default 2e-8; < 0
                                   turns it off): a CV-loss or prediction task whose solution
-                                  rule (refine_tol) is not met yet also stops once the error
+                                  rule (refine_tol) is not met yet, but whose error bound is
+                                  within 50 times it, also stops once the error
                                   left in its predictions, estimated as g |K d_i| (K the
                                   cross-covariances to the prediction points, d_i the last
                                   correction, g = c / (1 - c) with c the observed
@@ -176,6 +177,15 @@ typedef struct {
                                   and results pass through context buffers by
                                   device-to-device copies on the caller's stream); 1 = every
                                   call launches its kernels directly */
+    int32_t alpha_cache;       /* kriging weights kept per context (default 32 configurations,
+                                  < 0 = none): pcv_cv_loss (host buffers) and pcv_predict
+                                  store the refined weights alpha = (Sigma + lambda I)^-1 y_T
+                                  of every subset they solve, keyed by (rho, lambda =
+                                  tau2 / sigma2, precision), least recently used replaced
+                                  first, in T_off[N] doubles of device memory per
+                                  configuration; pcv_predict with a configuration whose
+                                  weights are kept for every subset it needs computes the
+                                  predictions (Eq. 3) from them without any factorisation */
 } pcv_options;
 
 /* ---------------------------------------------------------------- host-only */
@@ -294,6 +304,11 @@ pcv_status pcv_gls(pcv_ctx* ctx, const double* X, int32_t p, const double* param
  * the full description. */
 int32_t pcv_buckets(const pcv_ctx* ctx, char* buf, int32_t cap);
 
+/* Use of the kriging-weight cache (pcv_options.alpha_cache): pcv_predict calls served
+ * from kept weights (hits) and calls that solved (misses), and the configurations held.
+ * Any output may be NULL. */
+pcv_status pcv_alpha_cache_stats(const pcv_ctx* ctx, int64_t* hits, int64_t* misses, int32_t* rows_held);
+
 /* Kernel timing for benchmarks.  When enabled, pcv_cv_loss* records CUDA events
  * on the launching stream around the task kernel and around the combine kernel;
  * pcv_kernel_time waits for the most recent call's end events and returns the
@@ -322,27 +337,36 @@ void pcv_destroy(pcv_ctx* ctx);
  * A request loop over several device-resident datasets (contexts) for outer
  * optimisers that submit CV-loss evaluations one configuration at a time (the
  * paper evaluates its grid of configurations sequentially, Sec. 4.4) and for
- * prediction requests.  Continuous batching: each dataset has a worker thread and
- * stream; a worker takes all CV requests queued for its dataset (up to max_batch)
- * as one pcv_cv_loss batch, so requests arriving meanwhile join the next batch;
- * workers of different datasets run concurrently and their kernels overlap on the
- * device.  Admission by device memory: a batch starts only when its dataset's
- * work memory fits hbm_budget_bytes; idle datasets' work memory is released
- * (least recently used first) to make room.  Streams get priorities by work per
- * configuration (sum of k^3 over subsets), the smallest dataset highest, so that
- * waiting launches of short jobs are scheduled first.  Results do not depend on
- * batching (every subset task is computed on its own; the sums have a fixed order).
+ * prediction requests.  Continuous batching: every dataset has `lanes` lanes (the
+ * caller's context and clones over the same data, each with a worker thread and a
+ * stream); an idle lane takes the CV requests queued for its dataset (up to
+ * max_batch) as one pcv_cv_loss batch, or all queued predictions with one
+ * configuration as one pcv_predict call.  A request arriving while a batch runs
+ * starts on an idle lane at once: its persistent launch takes the SMs the running
+ * launch leaves free or frees as its last tasks finish, so the two overlap on the
+ * device.  Predictions use the kriging weights CV evaluations kept (the lanes share
+ * that cache, pcv_options.alpha_cache), so a prediction at a recently evaluated
+ * configuration factors nothing.  Admission by device memory: a batch starts only
+ * when its lane's work memory fits hbm_budget_bytes; idle lanes' work memory is
+ * released (least recently used first) to make room.  Streams get priorities by work
+ * per configuration (sum of k^3 over subsets), the smallest dataset highest, so that
+ * waiting launches of short jobs are scheduled first.  CV results do not depend on
+ * batching or lane (every subset task is computed on its own, lanes are identical,
+ * the sums have a fixed order); predictions agree within the precision's tolerance
+ * whether they come from kept weights or a fresh solve.
  *
  * The server takes the contexts over: while it exists, no other thread may use
- * them.  Contexts should be created with max_slots set so that their work memory
- * is predictable.  Thread-safe: any thread may submit and wait. */
+ * them (their clones' device copies of the data are the server's and are freed with
+ * it).  Contexts should be created with max_slots set so that their work memory is
+ * predictable.  Thread-safe: any thread may submit and wait. */
 typedef struct pcv_server pcv_server;
 
 typedef struct {
     int32_t struct_size;      /* sizeof(pcv_server_options) */
     int32_t max_batch;        /* CV requests per batch (default 16) */
     int32_t precision;        /* PCV_PREC_MIXED (default) or PCV_PREC_FP64 */
-    double hbm_budget_bytes;  /* work-memory budget over all datasets; 0 = unlimited */
+    double hbm_budget_bytes;  /* work-memory budget over all lanes; 0 = unlimited */
+    int32_t lanes;            /* lanes per dataset, 1 to 4 (default 2) */
 } pcv_server_options;
 
 pcv_status pcv_server_create(pcv_ctx* const* ctxs, int32_t n_ctx, const pcv_server_options* opts,

@@ -12,6 +12,7 @@
 #include <cmath>
 #include <cstring>
 #include <cstdio>
+#include <functional>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -90,6 +91,26 @@ struct Bucket {
     }
 };
 
+// Kriging weights of recent configurations: a pool of `cap` rows of T_off[N] doubles,
+// one row per (rho, lambda, precision), least recently used replaced first; a row in
+// use by a running call is pinned and never replaced.  Guarded by mu (serving lanes of
+// one dataset share it from their worker threads).
+struct AlphaEntry {
+    double rho = 0.0, lam = 0.0;
+    int32_t prec = -1;
+    std::vector<uint8_t> have;   // subsets whose weights the row holds
+    uint64_t used = 0;
+    int pins = 0;
+};
+struct AlphaCache {
+    std::mutex mu;
+    int cap = 0;
+    DevBuf<double> pool;
+    std::vector<AlphaEntry> rows;
+    uint64_t clock = 0;
+    int64_t hits = 0, misses = 0;
+};
+
 }  // namespace
 
 struct pcv_plan {
@@ -145,6 +166,13 @@ struct pcv_ctx {
     // CUDA graph of the mixed CV call (the buckets' launches, the FP64 fallback and the
     // combine), captured at the second call of a shape and replayed while the buffers it
     // names stay in place; parameters and results pass through the context's buffers
+    // kriging weights of recent configurations (pcv_cv_loss and pcv_predict keep them),
+    // so that predictions at new locations need no factorisation; shared with the
+    // context's serving lanes (ctx_clone)
+    std::shared_ptr<AlphaCache> alpha;
+    DevBuf<int32_t> alpha_slot;             // the current call's row per configuration
+    bool alpha_call = false;                // this call stores weights (alpha_slot is set)
+    bool alpha_in_call = false;             // this call predicts from stored weights
     cudaGraphExec_t gexec = nullptr;
     int64_t gkey = -1, gseen = -1;
     std::vector<const void*> gprint;
@@ -175,9 +203,10 @@ pcv_options default_options(const pcv_options* o) {
     d.refine_tol = 2e-8;
     d.factor_engine = pcv::kMixedEngineTensor;
     d.tc_stages = 0;
-    d.refine_loss_tol = 1e-7;
+    d.refine_loss_tol = 2e-8;
     d.bucketing = 0;
     d.graph = 0;
+    d.alpha_cache = 32;
     if (o) {
         if (o->struct_size != 0 && o->struct_size != (int32_t)sizeof(pcv_options)) return d;
         if (o->max_slots > 0) d.max_slots = o->max_slots;
@@ -189,6 +218,8 @@ pcv_options default_options(const pcv_options* o) {
         if (o->tc_stages >= 2 && o->tc_stages <= 4) d.tc_stages = o->tc_stages;
         if (o->bucketing == 1) d.bucketing = 1;
         if (o->graph == 1) d.graph = 1;
+        if (o->alpha_cache > 0) d.alpha_cache = std::min(o->alpha_cache, 4096);
+        else if (o->alpha_cache < 0) d.alpha_cache = 0;
         if (o->refine_loss_tol > 0) d.refine_loss_tol = o->refine_loss_tol;
         else if (o->refine_loss_tol < 0) d.refine_loss_tol = 0.0;   // solution rule only
     }
@@ -338,6 +369,55 @@ void ctx_release_workspace(pcv_ctx* c) {
 
 int ctx_device(const pcv_ctx* c) { return c->device; }
 
+// A second context over the same data on the same device (a serving lane): the plan,
+// options and device arrays are copied, the kriging-weight cache is shared, work memory
+// and per-call buffers are its own.  nullptr on failure.
+template <class T>
+static bool copy_buf(DevBuf<T>& dst, const DevBuf<T>& src) {
+    if (!src.p) return true;
+    if (dst.reserve(src.n) != cudaSuccess) return false;
+    return cudaMemcpy(dst.p, src.p, src.n * sizeof(T), cudaMemcpyDeviceToDevice) == cudaSuccess;
+}
+
+pcv_ctx* ctx_clone(const pcv_ctx* c) {
+    if (cudaSetDevice(c->device) != cudaSuccess) return nullptr;
+    std::unique_ptr<pcv_ctx> d(new (std::nothrow) pcv_ctx);
+    if (!d) return nullptr;
+    try {
+        d->device = c->device;
+        d->sms = c->sms;
+        d->plan = c->plan;
+        d->opts = c->opts;
+        d->hxy = c->hxy;
+        d->hv = c->hv;
+    } catch (const std::bad_alloc&) {
+        return nullptr;
+    }
+    d->lattice = c->lattice;
+    d->lat_hx = c->lat_hx;
+    d->lat_hy = c->lat_hy;
+    d->lat_cap = c->lat_cap;
+    d->n_active = c->n_active;
+    d->kmax = c->kmax;
+    d->mmax = c->mmax;
+    d->nV = c->nV;
+    d->coord_scale = c->coord_scale;
+    d->alpha = c->alpha;
+    const bool ok = copy_buf(d->X, c->X) && copy_buf(d->Y, c->Y) && copy_buf(d->V, c->V) &&
+                    copy_buf(d->Toff, c->Toff) && copy_buf(d->Voff, c->Voff) && copy_buf(d->Tidx, c->Tidx) &&
+                    copy_buf(d->Vx, c->Vx) && copy_buf(d->Vy, c->Vy) && copy_buf(d->Vv, c->Vv) &&
+                    copy_buf(d->LX, c->LX) && copy_buf(d->LY, c->LY) && copy_buf(d->VLX, c->VLX) &&
+                    copy_buf(d->VLY, c->VLY) && copy_buf(d->order, c->order) &&
+                    d->counter.reserve(1) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return d.release();
+}
+
+void ctx_free(pcv_ctx* c) { pcv_destroy(c); }
+
 double ctx_work_estimate(const pcv_ctx* c) {
     const Plan& P = c->plan;
     double w = 0.0;
@@ -419,6 +499,8 @@ PCV_API pcv_status pcv_create(const double* xy, const double* v, const uint8_t* 
     c->device = device;
     CUDA_TRY(cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device));
     c->opts = default_options(opts);
+    c->alpha = std::make_shared<AlphaCache>();
+    c->alpha->cap = c->opts.alpha_cache;
     const pcv::Plan& P = c->plan;
     const int32_t N = P.N;
 
@@ -578,7 +660,59 @@ static pcv::TaskArgs base_args(pcv_ctx* c, const double* d_params, int32_t B, co
     a.fb_count = c->fb_count.p;
     a.phase_cycles = c->timing ? c->phase.p : nullptr;
     a.tc_stages = c->opts.tc_stages;
+    if (c->alpha_call || c->alpha_in_call) {
+        if (c->alpha_in_call) a.alpha_in = c->alpha->pool.p;
+        else a.alpha_out = c->alpha->pool.p;
+        a.alpha_slot = c->alpha_slot.p;
+        a.alpha_stride = c->plan.T_off[c->plan.N];
+    }
     return a;
+}
+
+// ---------------------------------------------------------------- kriging-weight cache
+
+// The row of (rho, lambda, precision), or -1 (cache lock held).
+static int alpha_find(const AlphaCache& A, double rho, double lam, int32_t prec) {
+    for (size_t q = 0; q < A.rows.size(); ++q) {
+        const auto& e = A.rows[q];
+        if (e.prec == prec && e.rho == rho && e.lam == lam) return (int)q;
+    }
+    return -1;
+}
+
+// A pinned row for (rho, lambda, precision): its own if cached, else a free or the
+// least recently used unpinned one (its weights forgotten); -1 when the cache is off or
+// every row is pinned (cache lock held).
+static int alpha_take(pcv_ctx* c, AlphaCache& A, double rho, double lam, int32_t prec) {
+    if (A.cap <= 0) return -1;
+    const int64_t T = c->plan.T_off[c->plan.N];
+    if (T <= 0) return -1;
+    if (!A.pool.p) {
+        if (A.pool.reserve((size_t)A.cap * T) != cudaSuccess) {
+            cudaGetLastError();
+            A.cap = 0;   // no room: run without the cache
+            return -1;
+        }
+        A.rows.assign(A.cap, {});
+    }
+    int q = alpha_find(A, rho, lam, prec);
+    if (q < 0) {
+        uint64_t oldest = UINT64_MAX;
+        for (int r = 0; r < A.cap; ++r)
+            if (A.rows[r].pins == 0 && A.rows[r].used < oldest) {
+                oldest = A.rows[r].used;
+                q = r;
+            }
+        if (q < 0) return -1;
+        auto& e = A.rows[q];
+        e.rho = rho;
+        e.lam = lam;
+        e.prec = prec;
+        e.have.assign(c->plan.N, 0);
+    }
+    A.rows[q].used = ++A.clock;
+    ++A.rows[q].pins;
+    return q;
 }
 
 static void with_workspace(pcv::TaskArgs& a, const Workspace& w) {
@@ -866,7 +1000,8 @@ static pcv_status run_tasks(pcv_ctx* c, const double* d_params, int32_t B, int32
 // they are all where they were at capture time.
 static std::vector<const void*> graph_fingerprint(const pcv_ctx* c) {
     std::vector<const void*> f = {c->z.p, c->tst.p, c->fb_list.p, c->fb_count.p, c->ws[kFallbackWs].mem.p,
-                                  c->phase.p, c->gparams.p, c->gsspe.p, c->gstatus.p, c->gyhat.p};
+                                  c->phase.p, c->gparams.p, c->gsspe.p, c->gstatus.p, c->gyhat.p,
+                                  c->alpha->pool.p, c->alpha_slot.p};
     for (const auto& b : c->buckets) {
         f.push_back(b->ws.mem.p);
         f.push_back(b->ws.planes.p);
@@ -942,7 +1077,7 @@ PCV_API pcv_status pcv_cv_loss_device(pcv_ctx* c, const double* d_params, int32_
     const int32_t N = c->plan.N;
     // repeated mixed calls of one shape replay a captured graph of the whole call
     const bool graphable = prec == PCV_PREC_MIXED && c->opts.graph == 0 && c->n_active > 0;
-    const int64_t key = (int64_t)B * 4 + (d_yhat_valid ? 2 : 0) + (c->timing ? 1 : 0);
+    const int64_t key = (int64_t)B * 8 + (c->alpha_call ? 4 : 0) + (d_yhat_valid ? 2 : 0) + (c->timing ? 1 : 0);
     bool replay = false;
     if (graphable) {
         if (c->gexec && c->gkey == key && graph_fingerprint(c) == c->gprint) {
@@ -998,16 +1133,65 @@ PCV_API pcv_status pcv_cv_loss(pcv_ctx* c, const double* params, int32_t B, int3
     DevBuf<double> yv;
     if (yhat_valid) CUDA_TRY(yv.reserve((size_t)B * c->nV));
     CUDA_TRY(cudaMemcpyAsync(c->params.p, params, (size_t)3 * B * sizeof(double), cudaMemcpyHostToDevice, s));
+    // rows of the kriging-weight cache for the valid configurations of the batch
+    std::vector<int32_t> rows(B, -1);
+    AlphaCache& A = *c->alpha;
+    bool store = false;
+    if (c->n_active > 0) {
+        std::lock_guard<std::mutex> lk(A.mu);
+        for (int32_t b = 0; b < B; ++b) {
+            const double s2 = params[3 * b], rho = params[3 * b + 1], t2 = params[3 * b + 2];
+            if (!(s2 > 0 && rho > 0 && t2 >= 0 && std::isfinite(s2) && std::isfinite(rho) && std::isfinite(t2)))
+                continue;
+            rows[b] = alpha_take(c, A, rho, t2 / s2, prec);
+            store = store || rows[b] >= 0;
+        }
+    }
+    bool unpinned = false;
+    auto unpin = [&](bool good_call, const int32_t* st) {
+        if (unpinned) return;
+        unpinned = true;
+        std::lock_guard<std::mutex> lk(A.mu);
+        for (int32_t b = 0; b < B; ++b) {
+            if (rows[b] < 0) continue;
+            auto& e = A.rows[rows[b]];
+            // the row now holds the weights of every subset with validation data, unless
+            // a task of this configuration failed
+            const bool good = good_call && (st[b] == PCV_OK || st[b] == PCV_REFINE_FALLBACK);
+            for (int32_t i = 0; i < N; ++i)
+                if (c->plan.V_off[i + 1] > c->plan.V_off[i]) e.have[i] = good ? 1 : 0;
+            --e.pins;
+        }
+    };
+    std::vector<int32_t> hst(B, PCV_ERR_CUDA);
+    struct Guard {   // an early return leaves no row pinned (after the stream's work ends)
+        std::function<void()> f;
+        ~Guard() { if (f) f(); }
+    } guard{[&] {
+        if (!unpinned) {
+            cudaStreamSynchronize(s);
+            unpin(false, hst.data());
+        }
+    }};
+    if (store) {
+        CUDA_TRY(c->alpha_slot.reserve(B));
+        CUDA_TRY(cudaMemcpyAsync(c->alpha_slot.p, rows.data(), B * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    }
+    c->alpha_call = store;
     pcv_status st = pcv_cv_loss_device(c, c->params.p, B, prec, c->sspe.p, nullptr, yhat_valid ? yv.p : nullptr,
                                        c->status.p, stream);
+    c->alpha_call = false;
     if (st != PCV_OK) return st;
     CUDA_TRY(cudaMemcpyAsync(sspe, c->sspe.p, B * sizeof(double), cudaMemcpyDeviceToHost, s));
-    if (status) CUDA_TRY(cudaMemcpyAsync(status, c->status.p, B * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(hst.data(), c->status.p, B * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     if (sspe_per_subset)
         CUDA_TRY(cudaMemcpyAsync(sspe_per_subset, c->z.p, (size_t)B * N * sizeof(double), cudaMemcpyDeviceToHost, s));
     if (yhat_valid && c->nV)
         CUDA_TRY(cudaMemcpyAsync(yhat_valid, yv.p, (size_t)B * c->nV * sizeof(double), cudaMemcpyDeviceToHost, s));
-    CUDA_TRY(cudaStreamSynchronize(s));
+    const cudaError_t se = cudaStreamSynchronize(s);
+    unpin(se == cudaSuccess, hst.data());
+    if (se != cudaSuccess) return cuda_fail(se, "cudaStreamSynchronize");
+    if (status) std::copy(hst.begin(), hst.end(), status);
     return PCV_OK;
 }
 
@@ -1118,9 +1302,43 @@ static pcv_status predict_impl(pcv_ctx* c, const double* params, int32_t nrows,
         CUDA_TRY(cudaMemcpyAsync(c->prow.p, row_of_subset.data(), N * sizeof(int32_t), cudaMemcpyHostToDevice, s));
         d_rows = c->prow.p;
     }
+    // one configuration for every subset: its kriging weights may be kept (alpha_cache);
+    // when they are, for every subset the locations need, no matrix is factored
+    int row = -1;
+    bool from_cache = false;
+    AlphaCache& A = *c->alpha;
+    if (row_of_subset.empty()) {
+        const double rho = params[1], lam = params[2] / params[0];
+        if (params[0] > 0 && rho > 0 && params[2] >= 0 && std::isfinite(rho) && std::isfinite(lam)) {
+            std::lock_guard<std::mutex> lk(A.mu);
+            const int q = alpha_find(A, rho, lam, prec);
+            if (q >= 0) {
+                from_cache = true;
+                for (int32_t i : ord) from_cache = from_cache && A.rows[q].have[i];
+            }
+            row = alpha_take(c, A, rho, lam, prec);
+            if (row < 0) from_cache = false;
+            if (row >= 0) ++(from_cache ? A.hits : A.misses);
+        }
+    }
+    struct Guard {   // the row is released (after the stream's work ends) on every return
+        std::function<void()> f;
+        ~Guard() { if (f) f(); }
+    } guard{[&] {
+        if (row < 0) return;
+        cudaStreamSynchronize(s);
+        std::lock_guard<std::mutex> lk(A.mu);
+        --A.rows[row].pins;
+    }};
+    if (row >= 0) {
+        CUDA_TRY(c->alpha_slot.reserve(1));
+        CUDA_TRY(cudaMemcpyAsync(c->alpha_slot.p, &row, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+        (from_cache ? c->alpha_in_call : c->alpha_call) = true;
+    }
     // predictions need the slot for matrices as large as the largest training set
     pcv_status st = run_tasks(c, c->params.p, 1, prec, c->Poff.p, c->Px.p, c->Py.p, nullptr, c->Porder.p,
                               (int32_t)ord.size(), c->Pyhat.p, 0, stream, false, d_rows);
+    c->alpha_call = c->alpha_in_call = false;
     if (st != PCV_OK) return st;
     std::vector<double> out(m);
     std::vector<int32_t> tst(N);
@@ -1131,6 +1349,10 @@ static pcv_status predict_impl(pcv_ctx* c, const double* params, int32_t nrows,
     pcv_status worst = PCV_OK;
     for (int32_t i : ord)
         if (tst[i] != PCV_OK && tst[i] != PCV_REFINE_FALLBACK) worst = (pcv_status)tst[i];
+    if (row >= 0 && !from_cache) {   // the weights just computed for these subsets are kept
+        std::lock_guard<std::mutex> lk(A.mu);
+        for (int32_t i : ord) A.rows[row].have[i] = (tst[i] == PCV_OK || tst[i] == PCV_REFINE_FALLBACK);
+    }
     if (worst != PCV_OK) return fail(worst, "prediction failed for at least one subset");
     return PCV_OK;
 }
@@ -1350,6 +1572,20 @@ PCV_API const char* pcv_status_str(int32_t s) {
 PCV_API const char* pcv_last_error(void) { return g_err.c_str(); }
 
 PCV_API int32_t pcv_version(void) { return 1; }
+
+PCV_API pcv_status pcv_alpha_cache_stats(const pcv_ctx* c, int64_t* hits, int64_t* misses, int32_t* rows_held) {
+    if (!c) return fail(PCV_ERR_ARG, "NULL ctx");
+    AlphaCache& A = *c->alpha;
+    std::lock_guard<std::mutex> lk(A.mu);
+    if (hits) *hits = A.hits;
+    if (misses) *misses = A.misses;
+    if (rows_held) {
+        int32_t n = 0;
+        for (const auto& e : A.rows) n += e.prec >= 0;
+        *rows_held = n;
+    }
+    return PCV_OK;
+}
 
 PCV_API int32_t pcv_buckets(const pcv_ctx* c, char* buf, int32_t cap) {
     if (!c) return 0;

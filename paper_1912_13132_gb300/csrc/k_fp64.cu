@@ -144,8 +144,10 @@ __device__ int run_task(Smem64& sm, const TaskArgs& a, int i, int b) {
     }
     __syncthreads();
 
+    // predictions from kriging weights computed earlier (alpha_in): no matrix, no solve
+    const bool pred_only = a.alpha_in != nullptr;
     // assemble the lower triangle of Sigma + lambda I (column-major)
-    const int nb = (k + NB - 1) / NB;
+    const int nb = pred_only ? 0 : (k + NB - 1) / NB;
     for (int bj = 0; bj < nb; ++bj)
         for (int bi = bj; bi < nb; ++bi)
             for (int e = tid; e < NB * NB; e += NT) {
@@ -255,6 +257,15 @@ __device__ int run_task(Smem64& sm, const TaskArgs& a, int i, int b) {
             __syncthreads();
         }
 
+        if (pred_only) {
+            const double* al = a.alpha_in + (int64_t)(a.alpha_slot ? a.alpha_slot[b] : 0) * a.alpha_stride + t0;
+            for (int t = tid; t < k; t += NT) S.al[t] = al[t];
+            __syncthreads();
+        } else if (a.alpha_out && a.alpha_slot && a.alpha_slot[b] >= 0 && !a.rhs) {
+            // keep the kriging weights for later predictions at new locations
+            double* al = a.alpha_out + (int64_t)a.alpha_slot[b] * a.alpha_stride + t0;
+            for (int t = tid; t < k; t += NT) al[t] = S.al[t];
+        }
         // local -2 log-likelihood (Eq. 2) of the training data from the same factor:
         // log det(sigma2 A) = k log sigma2 + 2 sum log L_jj, y^T (sigma2 A)^-1 y = y^T alpha / sigma2
         if (a.lik && rh == 0) {

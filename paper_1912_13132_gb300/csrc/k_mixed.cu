@@ -41,6 +41,9 @@ using dfm::df;
 constexpr int NB = 64;   // block-column width of the factorisation and of the residual tiles
 constexpr int NT = 256;  // threads per CTA
 constexpr int KC = 16;   // K chunk of the trailing update
+// the loss-aware stopping rule applies once the solution rule's error bound is within
+// this factor of refine_tol
+constexpr float kLossGuard = 50.0f;
 
 __constant__ dfm::ExpConsts c_exp;
 
@@ -1355,6 +1358,9 @@ __device__ void run_task(SmemM& sm, SmemKeep& keep, SmemSimt* simt, TcCtx* tc, c
     const int k = (int)(a.T_off[i + 1] - t0);
     const int64_t ld = a.ld;
     const SlotM S = slot_of(a);
+    // predictions from kriging weights computed earlier (alpha_in): gather the training
+    // points, skip the matrix, its factorisation and the refinement
+    const bool pred_only = a.alpha_in != nullptr;
     PhaseTimer tm(a.phase_cycles);
     const long long t_task = a.phase_cycles ? now_cycles() : 0;
     // coordinates become offsets from the subset's first training point in units of
@@ -1431,7 +1437,7 @@ __device__ void run_task(SmemM& sm, SmemKeep& keep, SmemSimt* simt, TcCtx* tc, c
         const int nb = (k + NB - 1) / NB;
         const float2* __restrict__ tab = S.tab;
         constexpr int CPT = NB / (NT / NB);     // columns per thread in a 64 x 64 tile
-        if (lat_ok)
+        if (lat_ok && !pred_only)
             for (int bj = 0; bj < nb; ++bj)
                 for (int bi = bj; bi < (TC ? min(nb, (bj & ~1) + 2) : nb); ++bi) {
                     const int r = bi * NB + (tid & (NB - 1));
@@ -1498,7 +1504,7 @@ __device__ void run_task(SmemM& sm, SmemKeep& keep, SmemSimt* simt, TcCtx* tc, c
             }
         }
         const float lam32 = (float)lam;
-        const int nb = (k + NB - 1) / NB;
+        const int nb = pred_only ? 0 : (k + NB - 1) / NB;
         for (int bj = 0; bj < nb; ++bj)
             for (int bi = bj; bi < nb; ++bi) {
                 const int r = bi * NB + (tid & (NB - 1));     // fixed row per thread within a tile
@@ -1527,7 +1533,9 @@ __device__ void run_task(SmemM& sm, SmemKeep& keep, SmemSimt* simt, TcCtx* tc, c
     // the tensor-core factorisation also makes the first forward solve of the data
     // (not of the extended variant's right-hand-side columns)
     const bool fuse_fw = TC && !(EXT && a.rhs);
-    if (lat_ok) {
+    if (pred_only) {
+        ok = true;
+    } else if (lat_ok) {
         if constexpr (TC) {
             if (fuse_fw)
                 for (int q = tid; q < k; q += NT) S.w[q] = (float)S.rr[q];
@@ -1621,11 +1629,12 @@ __device__ void run_task(SmemM& sm, SmemKeep& keep, SmemSimt* simt, TcCtx* tc, c
             }
             __syncthreads();
         }
-        // the loss-aware stopping rule serves the plain variant's CV and prediction tasks
-        // whose prediction points cost no more than a residual pass
-        const bool loss_rule = !EXT && a.refine_loss_tol > 0.0 && m <= k;
+        // the loss-aware stopping rule serves CV and prediction tasks (not the local
+        // log-likelihood's or GLS's, whose results need the solution itself) whose
+        // prediction points cost no more than a residual pass
+        const bool loss_rule = !a.lik && !a.rhs && a.refine_loss_tol > 0.0 && m <= k;
         bool have_pred = false;       // the predictions of the final solution are done
-        if (ok) {
+        if (ok && !pred_only) {
             // iterative refinement: x += L^-T L^-1 r
             ok = false;
             float dprev = 0.0f;
@@ -1675,13 +1684,16 @@ __device__ void run_task(SmemM& sm, SmemKeep& keep, SmemSimt* simt, TcCtx* tc, c
                     // against |x|
                     const float c = dmax / fmaxf(dprev, 1e-30f);
                     if (c * dmax <= (float)a.refine_tol * xmax) { ok = true; break; }
-                    if (loss_rule) {
-                        // loss-aware rule: the predictions of x_i and the change u = K d_i the
-                        // last correction made to them; the error left in the predictions is
-                        // estimated as g |u|, g = c / (1 - c) (the corrections still to come
-                        // shrink geometrically).  Stop when it moves the local SSPE (Eq. 4)
-                        // by at most refine_loss_tol relative -- |dz| <= 2 |yhat - y| |dyhat|
-                        // -- and every prediction by at most 10 refine_loss_tol of their RMS.
+                    // loss-aware rule, for a solution already within kLossGuard times the
+                    // solution rule's bound: the predictions of x_i and the change u = K d_i
+                    // the last correction made to them; the error left in the predictions is
+                    // estimated as g |u|, g = c / (1 - c) (the corrections still to come
+                    // shrink geometrically).  Stop when it moves the local SSPE (Eq. 4) by at
+                    // most refine_loss_tol relative -- |dz| <= 2 |yhat - y| |dyhat| -- and
+                    // every prediction by at most 10 refine_loss_tol of their RMS.  The guard
+                    // covers a remaining error whose smooth part K damps less than it damps
+                    // the last correction (the estimate alone can then be optimistic).
+                    if (loss_rule && c * dmax <= kLossGuard * (float)a.refine_tol * xmax) {
                         const PredStats ps = predict_points<LAT>(sm, keep, a, R, k, m, p0, ox, oy, sc, W,
                                                                  (int64_t)b, R.w);
                         tm.lap(kPhPredict);
@@ -1715,6 +1727,22 @@ __device__ void run_task(SmemM& sm, SmemKeep& keep, SmemSimt* simt, TcCtx* tc, c
             }
             __syncthreads();
             return;
+        }
+        if (pred_only) {
+            // the stored kriging weights of this subset and configuration
+            const double* al = a.alpha_in + (int64_t)(a.alpha_slot ? a.alpha_slot[b] : 0) * a.alpha_stride + t0;
+            for (int q = tid; q < k; q += NT) {
+                const double x = al[q];
+                R.xs[q] = x;
+                const df v = dfm::from_double(x);
+                R.qh[q] = v.h;
+                R.ql[q] = v.l;
+            }
+            __syncthreads();
+        } else if (a.alpha_out && a.alpha_slot && a.alpha_slot[b] >= 0 && !(EXT && a.rhs)) {
+            // keep the refined kriging weights for later predictions at new locations
+            double* al = a.alpha_out + (int64_t)a.alpha_slot[b] * a.alpha_stride + t0;
+            for (int q = tid; q < k; q += NT) al[q] = R.xs[q];
         }
 
         // local -2 log-likelihood (Eq. 2) of the training data: the quadratic form from

@@ -88,6 +88,15 @@ struct TaskArgs {
     const int32_t* PLY;
     double lat_hx, lat_hy;
     int64_t lat_cap;
+    // kriging weights (the refined solution alpha = A^-1 y_T of each task), indexed like the
+    // training membership: configuration b of the launch uses row alpha_slot[b] (of
+    // alpha_stride = T_off[N] entries; -1: not stored).  alpha_out: store them after the
+    // solve; alpha_in: take them from there instead of assembling, factoring and solving
+    // (predictions only)
+    double* alpha_out;
+    const double* alpha_in;
+    const int32_t* alpha_slot;
+    int64_t alpha_stride;
     // optional per-phase cycle counters (kPhaseCount entries, summed over CTAs), or NULL
     unsigned long long* phase_cycles;
     int32_t tc_stages;      // TMA ring depth of the tensor-core kernel (2 or 3)
@@ -125,6 +134,8 @@ int64_t ctx_workspace_estimate(pcv_ctx* c, int32_t prec);   // bytes still to al
 int64_t ctx_workspace_resident(pcv_ctx* c);                  // bytes held now
 void ctx_release_workspace(pcv_ctx* c);                      // free all (context must be idle)
 int ctx_device(const pcv_ctx* c);
+pcv_ctx* ctx_clone(const pcv_ctx* c);                        // a serving lane over the same data
+void ctx_free(pcv_ctx* c);
 double ctx_work_estimate(const pcv_ctx* c);                  // sum of k^3 over subsets with validation data
 
 }  // namespace pcv

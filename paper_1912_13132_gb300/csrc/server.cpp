@@ -3,16 +3,24 @@
 // The paper's Algorithm 1 evaluates one parameter configuration after another for
 // an outer optimiser (Sec. 4.4: a grid of configurations evaluated sequentially).
 // Here many clients submit CV-loss evaluations and prediction requests at any time:
-//   * every dataset (a pcv_ctx) has a worker thread with its own stream; a worker
-//     takes *all* CV requests queued for its dataset (up to max_batch) as one batch,
-//     so requests that arrive while a batch runs join the next one;
-//   * workers of different datasets run concurrently, so their kernels overlap on
-//     the device;
-//   * a batch is admitted only when its dataset's work memory fits the server's HBM
-//     budget; idle datasets' work memory is released, least recently used first, to
-//     make room, otherwise the worker waits for running batches to finish;
-//   * results do not depend on the batching: every (subset, configuration) task is
-//     computed on its own and the per-configuration sum has a fixed order.
+//   * every dataset has `lanes` lanes (default two): its own context and a clone over
+//     the same device-resident data (ctx_clone), each with a worker thread and a
+//     stream.  An idle lane takes the CV requests queued for its dataset (up to
+//     max_batch) as one batch, or every queued prediction with the same parameters as
+//     one call; so a request that arrives while a batch runs starts on the other lane
+//     at once, and its persistent launch takes over the SMs that the running launch
+//     frees as its last tasks finish (or the SMs it never used) -- admission as slots
+//     free up, with the two launches overlapping on the device;
+//   * lanes of different datasets run concurrently as well;
+//   * predictions use the kriging weights that CV evaluations of the same
+//     configuration kept (the lanes of a dataset share that cache), so a prediction at
+//     a recently evaluated configuration factors nothing;
+//   * a batch is admitted only when its lane's work memory fits the server's HBM
+//     budget; idle lanes' work memory is released, least recently used first, to make
+//     room, otherwise the worker waits for running batches to finish;
+//   * results do not depend on the batching or the lane: every (subset,
+//     configuration) task is computed on its own, lanes are identical clones, and the
+//     per-configuration sum has a fixed order.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -49,15 +57,20 @@ struct Request {
     std::vector<double> yhat;
 };
 
-struct Dataset {
-    pcv_ctx* ctx;
-    std::deque<std::shared_ptr<Request>> queue;
+struct Lane {
+    pcv_ctx* ctx = nullptr;
+    bool owned = false;             // a clone the server made (freed with the server)
     bool busy = false;
     bool evicting = false;
-    int64_t resident = 0;           // work-memory bytes accounted to this dataset
+    int64_t resident = 0;           // work-memory bytes accounted to this lane
     Clock::time_point last_used;
     std::thread worker;
     cudaStream_t stream = nullptr;
+};
+
+struct Dataset {
+    std::deque<std::shared_ptr<Request>> queue;
+    std::vector<std::unique_ptr<Lane>> lanes;
 };
 
 }  // namespace
@@ -69,39 +82,40 @@ struct pcv_server {
     std::unordered_map<int64_t, std::shared_ptr<Request>> reqs;
     int64_t next_id = 1;
     int32_t max_batch = 16;
+    int32_t lanes = 2;
     int32_t precision = PCV_PREC_MIXED;
     double budget = 0.0;            // 0: unlimited
     int64_t used = 0;
     bool stop = false;
     // statistics
     std::vector<double> lat_ms;
-    int64_t cv_done = 0, pred_done = 0, batches = 0, evictions = 0;
+    int64_t cv_done = 0, pred_done = 0, batches = 0, evictions = 0, pred_calls = 0;
     Clock::time_point t_first, t_last;
     bool any = false;
 };
 
 namespace {
 
-// Admission: make room for dataset d's work memory (called with the lock held).
-bool admit(pcv_server* s, size_t d, std::unique_lock<std::mutex>& lk) {
-    Dataset& D = *s->ds[d];
+// Admission: make room for lane L's work memory (called with the lock held).
+bool admit(pcv_server* s, Lane& L, std::unique_lock<std::mutex>& lk) {
     for (;;) {
         if (s->stop) return false;
-        const int64_t need = pcv::ctx_workspace_estimate(D.ctx, s->precision);
+        const int64_t need = pcv::ctx_workspace_estimate(L.ctx, s->precision);
         if (s->budget <= 0.0 || (double)(s->used + need) <= s->budget) {
             s->used += need;
-            D.resident += need;
+            L.resident += need;
             return true;
         }
-        // evict the least recently used idle dataset that holds memory
-        int victim = -1;
-        for (size_t j = 0; j < s->ds.size(); ++j) {
-            Dataset& V = *s->ds[j];
-            if (j == d || V.busy || V.evicting || V.resident == 0) continue;
-            if (victim < 0 || V.last_used < s->ds[victim]->last_used) victim = (int)j;
-        }
-        if (victim >= 0) {
-            Dataset& V = *s->ds[victim];
+        // evict the least recently used idle lane that holds memory
+        Lane* victim = nullptr;
+        for (auto& d : s->ds)
+            for (auto& lp : d->lanes) {
+                Lane& V = *lp;
+                if (&V == &L || V.busy || V.evicting || V.resident == 0) continue;
+                if (!victim || V.last_used < victim->last_used) victim = &V;
+            }
+        if (victim) {
+            Lane& V = *victim;
             V.evicting = true;
             lk.unlock();
             pcv::ctx_release_workspace(V.ctx);
@@ -118,65 +132,89 @@ bool admit(pcv_server* s, size_t d, std::unique_lock<std::mutex>& lk) {
     }
 }
 
-void worker(pcv_server* s, size_t d) {
+// The next batch of dataset D for an idle lane (lock held): every queued prediction with
+// the front prediction's parameters (one call), or up to max_batch CV requests.
+void take_batch(pcv_server* s, Dataset& D, std::vector<std::shared_ptr<Request>>& batch) {
+    batch.clear();
+    const Kind kind = D.queue.front()->kind;
+    const double* p = D.queue.front()->params;
+    for (auto it = D.queue.begin(); it != D.queue.end();) {
+        const Request& r = **it;
+        const bool take = r.kind == kind &&
+                          (kind == Kind::Cv ? (int)batch.size() < s->max_batch
+                                            : std::memcmp(r.params, p, sizeof r.params) == 0);
+        if (take) {
+            batch.push_back(*it);
+            it = D.queue.erase(it);
+        } else {
+            ++it;
+        }
+    }
+}
+
+void worker(pcv_server* s, size_t d, size_t l) {
     Dataset& D = *s->ds[d];
-    cudaSetDevice(pcv::ctx_device(D.ctx));
+    Lane& L = *D.lanes[l];
+    cudaSetDevice(pcv::ctx_device(L.ctx));
     std::vector<std::shared_ptr<Request>> batch;
-    std::vector<double> params, sspe;
+    std::vector<double> params, sspe, xy, yhat;
     std::vector<int32_t> status;
     for (;;) {
         std::unique_lock<std::mutex> lk(s->mu);
-        s->cv.wait(lk, [&] { return s->stop || (!D.queue.empty() && !D.evicting); });
+        s->cv.wait(lk, [&] { return s->stop || (!D.queue.empty() && !L.evicting); });
         if (s->stop) return;
-        batch.clear();
-        if (D.queue.front()->kind == Kind::Predict) {
-            batch.push_back(D.queue.front());
-            D.queue.pop_front();
-        } else {
-            while (!D.queue.empty() && D.queue.front()->kind == Kind::Cv && (int)batch.size() < s->max_batch) {
-                batch.push_back(D.queue.front());
-                D.queue.pop_front();
-            }
-        }
-        D.busy = true;
-        if (!admit(s, d, lk)) {
-            D.busy = false;
+        take_batch(s, D, batch);
+        L.busy = true;
+        if (!admit(s, L, lk)) {
+            L.busy = false;
             return;
         }
         ++s->batches;
         lk.unlock();
+        s->cv.notify_all();   // the other lane may take what is still queued
 
-        // run the batch (synchronous on this dataset's stream; other datasets proceed)
+        // run the batch (synchronous on this lane's stream; other lanes proceed)
         if (batch[0]->kind == Kind::Cv) {
             const int32_t B = (int32_t)batch.size();
             params.resize(3 * B);
             sspe.assign(B, 0.0);
             status.assign(B, 0);
             for (int32_t b = 0; b < B; ++b) std::memcpy(&params[3 * b], batch[b]->params, sizeof(double) * 3);
-            pcv_status st = pcv_cv_loss(D.ctx, params.data(), B, s->precision, sspe.data(), nullptr, nullptr, nullptr,
-                                        status.data(), D.stream);
+            pcv_status st = pcv_cv_loss(L.ctx, params.data(), B, s->precision, sspe.data(), nullptr, nullptr, nullptr,
+                                        status.data(), L.stream);
             for (int32_t b = 0; b < B; ++b) {
                 batch[b]->sspe = st == PCV_OK ? sspe[b] : NAN;
                 batch[b]->status = st == PCV_OK ? status[b] : (int32_t)st;
             }
         } else {
-            Request& R = *batch[0];
-            const int64_t m = (int64_t)R.xy.size() / 2;
-            R.yhat.assign(m, 0.0);
-            R.status = pcv_predict(D.ctx, R.params, R.xy.data(), m, s->precision, R.yhat.data(), D.stream);
+            // predictions with one configuration: one call over all their locations
+            xy.clear();
+            for (auto& r : batch) xy.insert(xy.end(), r->xy.begin(), r->xy.end());
+            const int64_t m = (int64_t)xy.size() / 2;
+            yhat.assign(m, 0.0);
+            const pcv_status st = pcv_predict(L.ctx, batch[0]->params, xy.data(), m, s->precision, yhat.data(),
+                                              L.stream);
+            int64_t off = 0;
+            for (auto& r : batch) {
+                const int64_t mr = (int64_t)r->xy.size() / 2;
+                r->yhat.assign(yhat.begin() + off, yhat.begin() + off + mr);
+                r->status = st;
+                off += mr;
+            }
         }
 
         lk.lock();
         const auto now = Clock::now();
         s->t_last = now;
+        if (batch[0]->kind == Kind::Predict) ++s->pred_calls;
         for (auto& r : batch) {
             r->t_done = now;
             r->done = true;
             s->lat_ms.push_back(std::chrono::duration<double, std::milli>(now - r->t_submit).count());
             if (r->kind == Kind::Cv) ++s->cv_done; else ++s->pred_done;
         }
-        D.busy = false;
-        D.last_used = now;
+        L.busy = false;
+        L.last_used = now;
         // the workspace estimate is now zero; keep the accounted bytes as resident
         lk.unlock();
         s->cv.notify_all();
@@ -215,6 +253,7 @@ PCV_API pcv_status pcv_server_create(pcv_ctx* const* ctxs, int32_t n_ctx, const 
     if (opts) {
         if (opts->struct_size != 0 && opts->struct_size != (int32_t)sizeof(pcv_server_options)) return PCV_ERR_ARG;
         if (opts->max_batch > 0) s->max_batch = opts->max_batch;
+        if (opts->lanes > 0) s->lanes = std::min(opts->lanes, 4);
         if (opts->precision == PCV_PREC_FP64 || opts->precision == PCV_PREC_MIXED) s->precision = opts->precision;
         if (opts->hbm_budget_bytes > 0) s->budget = opts->hbm_budget_bytes;
     }
@@ -224,12 +263,15 @@ PCV_API pcv_status pcv_server_create(pcv_ctx* const* ctxs, int32_t n_ctx, const 
     // a running launch is never pre-empted, so long jobs are delayed, not starved).
     std::vector<double> work(n_ctx);
     for (int32_t i = 0; i < n_ctx; ++i) work[i] = pcv::ctx_work_estimate(ctxs[i]);
+    auto cleanup = [&]() {
+        for (auto& e : s->ds)
+            for (auto& l : e->lanes) {
+                if (l->stream) cudaStreamDestroy(l->stream);
+                if (l->owned) pcv::ctx_free(l->ctx);
+            }
+    };
     for (int32_t i = 0; i < n_ctx; ++i) {
         auto d = std::make_unique<Dataset>();
-        d->ctx = ctxs[i];
-        d->last_used = Clock::now();
-        d->resident = pcv::ctx_workspace_resident(ctxs[i]);
-        s->used += d->resident;
         cudaSetDevice(pcv::ctx_device(ctxs[i]));
         int least = 0, greatest = 0;
         if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) least = greatest = 0;
@@ -237,14 +279,29 @@ PCV_API pcv_status pcv_server_create(pcv_ctx* const* ctxs, int32_t n_ctx, const 
         for (int32_t j = 0; j < n_ctx; ++j) rank += work[j] < work[i];
         const int levels = least - greatest + 1;   // greatest is numerically smallest
         const int prio = n_ctx > 1 ? greatest + (int)((int64_t)rank * (levels - 1) / (n_ctx - 1)) : least;
-        if (cudaStreamCreateWithPriority(&d->stream, cudaStreamNonBlocking, prio) != cudaSuccess) {
-            for (auto& e : s->ds) cudaStreamDestroy(e->stream);
-            return PCV_ERR_CUDA;
+        for (int32_t l = 0; l < s->lanes; ++l) {
+            auto L = std::make_unique<Lane>();
+            L->ctx = l == 0 ? ctxs[i] : pcv::ctx_clone(ctxs[i]);
+            L->owned = l > 0;
+            L->last_used = Clock::now();
+            const bool ok = L->ctx && cudaStreamCreateWithPriority(&L->stream, cudaStreamNonBlocking, prio) == cudaSuccess;
+            if (L->ctx) {
+                L->resident = pcv::ctx_workspace_resident(L->ctx);
+                s->used += L->resident;
+            }
+            d->lanes.push_back(std::move(L));
+            if (!ok) {
+                s->ds.push_back(std::move(d));
+                cleanup();
+                return PCV_ERR_CUDA;
+            }
         }
         s->ds.push_back(std::move(d));
     }
     pcv_server* raw = s.get();
-    for (size_t i = 0; i < raw->ds.size(); ++i) raw->ds[i]->worker = std::thread(worker, raw, i);
+    for (size_t i = 0; i < raw->ds.size(); ++i)
+        for (size_t l = 0; l < raw->ds[i]->lanes.size(); ++l)
+            raw->ds[i]->lanes[l]->worker = std::thread(worker, raw, i, l);
     *out = s.release();
     return PCV_OK;
 }
@@ -317,9 +374,11 @@ PCV_API void pcv_server_destroy(pcv_server* s) {
         s->stop = true;
     }
     s->cv.notify_all();
-    for (auto& d : s->ds) {
-        if (d->worker.joinable()) d->worker.join();
-        if (d->stream) cudaStreamDestroy(d->stream);
-    }
+    for (auto& d : s->ds)
+        for (auto& l : d->lanes) {
+            if (l->worker.joinable()) l->worker.join();
+            if (l->stream) cudaStreamDestroy(l->stream);
+            if (l->owned) pcv::ctx_free(l->ctx);
+        }
     delete s;
 }

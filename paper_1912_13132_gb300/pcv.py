@@ -37,12 +37,13 @@ class pcv_options(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_int32), ("max_slots", ctypes.c_int32),
                 ("workspace_fraction", ctypes.c_double), ("refine_max_iter", ctypes.c_int32),
                 ("refine_tol", ctypes.c_double), ("factor_engine", ctypes.c_int32), ("tc_stages", ctypes.c_int32),
-                ("refine_loss_tol", ctypes.c_double), ("bucketing", ctypes.c_int32), ("graph", ctypes.c_int32)]
+                ("refine_loss_tol", ctypes.c_double), ("bucketing", ctypes.c_int32), ("graph", ctypes.c_int32),
+                ("alpha_cache", ctypes.c_int32)]
 
 
 class pcv_server_options(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_int32), ("max_batch", ctypes.c_int32), ("precision", ctypes.c_int32),
-                ("hbm_budget_bytes", ctypes.c_double)]
+                ("hbm_budget_bytes", ctypes.c_double), ("lanes", ctypes.c_int32)]
 
 
 class PcvError(RuntimeError):
@@ -88,6 +89,7 @@ _SIGS = {
                                          ctypes.POINTER(ctypes.c_float), ctypes.c_int32,
                                          ctypes.POINTER(ctypes.c_float)]),
     "pcv_buckets": (ctypes.c_int32, [_vp, ctypes.c_char_p, ctypes.c_int32]),
+    "pcv_alpha_cache_stats": (ctypes.c_int, [_vp, _i64p, _i64p, _i32p]),
     "pcv_measure_peak": (ctypes.c_int, [ctypes.c_int32, ctypes.c_double, _dp, _dp]),
     "pcv_server_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int32, ctypes.POINTER(pcv_server_options),
                                          ctypes.POINTER(_vp)]),
@@ -219,13 +221,14 @@ class Context:
     def __init__(self, xy, v, role, layout: dict, device: int = 0, max_slots: int = 0,
                  workspace_fraction: float = 0.0, refine_max_iter: int = 0, refine_tol: float = 0.0,
                  factor_engine: str = "tensor", tc_stages: int = 0, refine_loss_tol: float = 0.0,
-                 bucketing: int = 0, graph: int = 0):
+                 bucketing: int = 0, graph: int = 0, alpha_cache: int = 0):
         xy = _f64(xy).reshape(-1, 2)
         v = _f64(v)
         role = np.ascontiguousarray(role, dtype=np.uint8)
         L, keep = make_layout(layout)
         o = pcv_options(ctypes.sizeof(pcv_options), max_slots, workspace_fraction, refine_max_iter,
-                        refine_tol, ENGINES[factor_engine], tc_stages, refine_loss_tol, bucketing, graph)
+                        refine_tol, ENGINES[factor_engine], tc_stages, refine_loss_tol, bucketing, graph,
+                        alpha_cache)
         h = _vp()
         _check(_lib.pcv_create(_ptr(xy, _dp), _ptr(v, _dp), _ptr(role, _u8p), len(v), ctypes.byref(L),
                                device, ctypes.byref(o), ctypes.byref(h)), "pcv_create")
@@ -290,6 +293,13 @@ class Context:
     PHASES = ("gather_assemble", "tc_update", "diag", "panel_solve", "diag_io", "factor_simt", "solves",
               "residual", "predict_loss", "task", "residual_passes", "tasks", "fail_factor", "fail_nan",
               "fail_stall")
+
+    def alpha_cache_stats(self) -> dict:
+        """pcv_alpha_cache_stats: predictions served from kept kriging weights, and not."""
+        h, m, r = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
+        _check(_lib.pcv_alpha_cache_stats(self._h, ctypes.byref(h), ctypes.byref(m), ctypes.byref(r)),
+               "pcv_alpha_cache_stats")
+        return dict(hits=h.value, misses=m.value, rows=r.value)
 
     def buckets(self) -> str:
         """The mixed CV launch's size buckets (pcv_buckets), '' before the first mixed call."""
@@ -363,11 +373,12 @@ class Context:
 class Server:
     """Continuous-batching request loop over device-resident datasets (pcv_server_*)."""
 
-    def __init__(self, contexts, max_batch: int = 16, precision: str = "mixed", hbm_budget_bytes: float = 0.0):
+    def __init__(self, contexts, max_batch: int = 16, precision: str = "mixed", hbm_budget_bytes: float = 0.0,
+                 lanes: int = 0):
         self.contexts = list(contexts)
         arr = (_vp * len(self.contexts))(*[c._h for c in self.contexts])
         o = pcv_server_options(ctypes.sizeof(pcv_server_options), max_batch, PRECISIONS[precision],
-                               float(hbm_budget_bytes))
+                               float(hbm_budget_bytes), lanes)
         h = _vp()
         _check(_lib.pcv_server_create(arr, len(self.contexts), ctypes.byref(o), ctypes.byref(h)), "pcv_server_create")
         self._h = h

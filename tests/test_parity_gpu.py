@@ -140,7 +140,8 @@ def test_forced_fp64_fallback(gpu_lib):
     FP64 bar; the same data at the default options need no fallback."""
     w = datagen.make_uniform(800, 400, 3, 0.05, seed=41, name="fallback")
     P = np.array([[1.0, 0.1, 0.05], [1.0, 0.05, 0.01], [0.5, 0.2, 0.002]])
-    with gpu_lib.Context(w.xy, w.v, w.role, w.layout, refine_max_iter=1, refine_tol=1e-300) as ctx:
+    with gpu_lib.Context(w.xy, w.v, w.role, w.layout, refine_max_iter=1, refine_tol=1e-300,
+                         refine_loss_tol=-1.0) as ctx:
         out = ctx.cv_loss(P, precision="mixed", per_subset=True, predictions=True)
         V_off = ctx.V_off.copy()
     assert np.all(out["status"] == gpu_lib.PCV_REFINE_FALLBACK), out["status"]
@@ -463,3 +464,58 @@ def test_size_buckets_autotuned(gpu_lib, cluster):
         assert ctx2.buckets() == desc                       # the cached choice
     assert np.array_equal(again["sspe"], out["sspe"])       # same engines, same arithmetic
     print("buckets", lines, worst)
+
+
+@pytest.mark.parametrize("engine", ["tensor", "simt"])
+def test_loss_aware_refinement_stop(gpu_lib, cluster, engine):
+    """The loss-aware stopping rule (refine_loss_tol, the default) against the solution
+    rule alone (refine_loss_tol < 0) on every subset of the cluster workload: both meet
+    the mixed bars against the oracle, and the loss-aware rule spends no more residual
+    passes.  The rule stops a task once the estimated error left in its predictions
+    moves the local SSPE by at most 2e-8 relative; the SSPE amplifies prediction errors
+    by about |yhat| / |yhat - y|, which varies from subset to subset."""
+    w, P, act, ref = cluster
+    passes = {}
+    for label, lt in (("loss-aware", 0.0), ("solution", -1.0)):
+        with gpu_lib.Context(w.xy, w.v, w.role, w.layout, factor_engine=engine, refine_loss_tol=lt,
+                             bucketing=1) as ctx:
+            ctx.set_timing(True)
+            out = ctx.cv_loss(P, precision="mixed", per_subset=True, predictions=True)
+            ph = ctx.phase_cycles()
+            V_off = ctx.V_off.copy()
+        assert np.all(out["status"] == 0), out["status"]
+        worst = compare(out, ref, V_off, act, len(P), "mixed", check_total=False)
+        passes[label] = ph["residual_passes"] / max(ph["tasks"], 1)
+        print(engine, label, worst, "passes per task", passes[label])
+    assert passes["loss-aware"] <= passes["solution"] + 1e-9
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_predict_from_kept_weights(gpu_lib, prec):
+    """Predictions at new locations from the kriging weights a CV evaluation kept
+    (alpha_cache): after pcv_cv_loss of a batch, pcv_predict with one of its
+    configurations factors nothing (a cache hit) and matches the oracle's kriging (Eq. 3)
+    at the precision's bar; a configuration not evaluated before is solved (a miss) and
+    kept, so asking again hits; with the cache off every call solves."""
+    w = datagen.make_uniform(1500, 700, 3, 0.06, seed=57, name="alpha")
+    P = np.array([[1.0, 0.1, 0.05], [2.0, 0.05, 0.02], [0.8, 0.15, 0.01]])
+    pts = np.random.default_rng(3).random((900, 2)) * 1.1 - 0.05
+    with gpu_lib.Context(w.xy, w.v, w.role, w.layout) as ctx:
+        ctx.cv_loss(P, precision=prec)
+        got = [ctx.predict(p, pts, precision=prec) for p in P]
+        st1 = ctx.alpha_cache_stats()
+        p_new = (1.3, 0.08, 0.03)
+        y_new = ctx.predict(p_new, pts, precision=prec)
+        y_new2 = ctx.predict(p_new, pts, precision=prec)
+        st2 = ctx.alpha_cache_stats()
+    assert st1["hits"] == len(P) and st1["misses"] == 0, st1
+    assert st2["hits"] == len(P) + 1 and st2["misses"] == 1, st2
+    for p, yh in zip(list(P) + [p_new], got + [y_new]):
+        ref = oracle.predict(w.xy, w.v, w.role, w.layout, tuple(p), pts)
+        assert pred_err(yh, ref) <= TOL[prec]["pred"], (p, pred_err(yh, ref))
+    assert pred_err(y_new2, y_new) <= TOL[prec]["pred"]
+    with gpu_lib.Context(w.xy, w.v, w.role, w.layout, alpha_cache=-1) as ctx0:
+        ctx0.cv_loss(P, precision=prec)
+        y0 = ctx0.predict(P[0], pts, precision=prec)
+        assert ctx0.alpha_cache_stats() == dict(hits=0, misses=0, rows=0)
+    assert pred_err(got[0], y0) <= TOL[prec]["pred"]
