@@ -72,8 +72,30 @@ enum { PCV_ROLE_TRAIN = 0, PCV_ROLE_VALID = 1, PCV_ROLE_IGNORE = 2 };
  *   PCV_PREC_FP64:  every step in FP64 (reference GPU path).
  *   PCV_PREC_MIXED: matrix factorised in a lower precision, solution refined
  *                   against double-float residuals; same results to the stated
- *                   tolerance (1e-6 relative on losses, 1e-5 on predictions). */
-enum { PCV_PREC_FP64 = 0, PCV_PREC_MIXED = 1 };
+ *                   tolerance (1e-6 relative on losses, 1e-5 on predictions), with
+ *                   the context's factorisation engine (pcv_options.factor_engine;
+ *                   for the CV loss, size buckets with autotuned engines).
+ *   The other modes are the mixed path with one operand scheme for the tensor-core
+ *   factorisation, for every subset of the call (trailing updates and panels on
+ *   tcgen05 with FP32 accumulation):
+ *   PCV_PREC_MIXED_TF32:   values rounded to TF32 (11 significant bits), one product;
+ *                          refinement converges only for well-conditioned matrices,
+ *                          other tasks are recomputed in FP64 (status
+ *                          PCV_REFINE_FALLBACK) -- results meet the tolerance either way;
+ *   PCV_PREC_MIXED_TF32X3: two TF32 terms (22 bits), three products;
+ *   PCV_PREC_MIXED_BF16X3: three BF16 terms (24 bits), six products;
+ *   PCV_PREC_MIXED_F16X2:  two FP16 terms (22 bits), three products (the default
+ *                          engine's scheme).
+ *   pcv_neg2loglik and pcv_gls in mixed precision need the FP16 scheme (or, for
+ *   pcv_neg2loglik, the SIMT engine). */
+enum {
+    PCV_PREC_FP64 = 0,
+    PCV_PREC_MIXED = 1,
+    PCV_PREC_MIXED_TF32 = 2,
+    PCV_PREC_MIXED_TF32X3 = 3,
+    PCV_PREC_MIXED_BF16X3 = 4,
+    PCV_PREC_MIXED_F16X2 = 5
+};
 
 enum { PCV_LAYOUT_RECTS = 0, PCV_LAYOUT_GRID = 1, PCV_LAYOUT_RECURSIVE = 2 };
 
@@ -135,14 +157,16 @@ typedef struct {
                                   whose values leave FP16 range, which needs tau2 / sigma2
                                   above ~6e4, is recomputed in FP64); 1 = FP32 SIMT;
                                   2 = tensor cores with three BF16 terms, six products
-                                  (FP32 range, half again the operand bytes, twice the MMAs) */
+                                  (FP32 range, half again the operand bytes, twice the MMAs);
+                                  3 = tensor cores with TF32 values, one product; 4 = two
+                                  TF32 terms, three products */
     int32_t tc_stages;         /* tensor engines: depth of the TMA operand ring, 2 to 4 (0 =
-                                  default: 3 for engine 0, 2 for engine 2); rings above
-                                  96 KB leave one CTA per SM */
+                                  each engine's default: 3 for engines 0 and 4, 2 for engine
+                                  2, 4 for engine 3); rings above 96 KB leave one CTA per SM */
     double refine_loss_tol;    /* mixed path, loss-aware stopping rule (default 2e-8; < 0
                                   turns it off): a CV-loss or prediction task whose solution
                                   rule (refine_tol) is not met yet, but whose error bound is
-                                  within 50 times it, also stops once the error
+                                  within 1000 times it, also stops once the error
                                   left in its predictions, estimated as g |K d_i| (K the
                                   cross-covariances to the prediction points, d_i the last
                                   correction, g = c / (1 - c) with c the observed

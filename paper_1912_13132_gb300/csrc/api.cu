@@ -144,7 +144,9 @@ struct pcv_ctx {
     DevBuf<double> lik, lik_total;          // local -2 log-likelihoods and their sums
     DevBuf<int32_t> tst, status;
     DevBuf<unsigned int> counter;
-    Workspace ws[3];                        // FP64, mixed, FP64 fallback of the mixed path
+    // work memory: [0] FP64, [2] FP64 fallback of the mixed path, [3 + e] mixed engine e
+    Workspace ws[3 + pcv::kMixedEngines];
+    int32_t tc_stages_set = 0;              // ring depth the caller asked for (0: each engine's default)
     // prediction buffers
     DevBuf<double> Px, Py, Pyhat;
     DevBuf<int64_t> Poff;
@@ -179,6 +181,7 @@ struct pcv_ctx {
     cudaStream_t gcap = nullptr;
     bool capturing = false;
     int64_t graph_launches = 0;             // replays so far
+    uint64_t mem_gen = 0;                   // bumped whenever work memory is released or buckets rebuilt
     int64_t graph_kernels = 0;              // kernel launches inside the captured graph
     DevBuf<double> gparams, gsspe, gyhat;
     DevBuf<int32_t> gstatus;
@@ -213,8 +216,7 @@ pcv_options default_options(const pcv_options* o) {
         if (o->workspace_fraction > 0 && o->workspace_fraction <= 0.95) d.workspace_fraction = o->workspace_fraction;
         if (o->refine_max_iter > 0) d.refine_max_iter = o->refine_max_iter;
         if (o->refine_tol > 0) d.refine_tol = o->refine_tol;
-        if (o->factor_engine == pcv::kMixedEngineSimt || o->factor_engine == pcv::kMixedEngineTensorBF16)
-            d.factor_engine = o->factor_engine;
+        if (o->factor_engine > 0 && o->factor_engine < pcv::kMixedEngines) d.factor_engine = o->factor_engine;
         if (o->tc_stages >= 2 && o->tc_stages <= 4) d.tc_stages = o->tc_stages;
         if (o->bucketing == 1) d.bucketing = 1;
         if (o->graph == 1) d.graph = 1;
@@ -224,6 +226,7 @@ pcv_options default_options(const pcv_options* o) {
         else if (o->refine_loss_tol < 0) d.refine_loss_tol = 0.0;   // solution rule only
     }
     if (d.tc_stages == 0) d.tc_stages = pcv::mixed_default_stages(d.factor_engine);
+    // (the explicit engine modes take their own default depth unless the caller set one)
     return d;
 }
 
@@ -231,19 +234,44 @@ int32_t round_up(int64_t v, int64_t m) { return (int32_t)(((std::max<int64_t>(v,
 
 // Allocate the per-CTA workspace slots of one precision (once per context).
 constexpr int kFallbackWs = 2;          // index of the fallback workspace
+constexpr int kMixedWs0 = 3;            // workspace of mixed engine e: kMixedWs0 + e
+
+bool is_mixed(int32_t prec) { return prec != PCV_PREC_FP64; }
+
+// The factorisation engine of a mixed precision mode (-1 for FP64).
+int engine_of(const pcv_ctx* c, int32_t prec) {
+    switch (prec) {
+        case PCV_PREC_MIXED: return c->opts.factor_engine;
+        case PCV_PREC_MIXED_TF32: return pcv::kMixedEngineTensorTF32;
+        case PCV_PREC_MIXED_TF32X3: return pcv::kMixedEngineTensorTF32x3;
+        case PCV_PREC_MIXED_BF16X3: return pcv::kMixedEngineTensorBF16;
+        case PCV_PREC_MIXED_F16X2: return pcv::kMixedEngineTensor;
+        default: return -1;
+    }
+}
+
+// Workspace index of a precision mode.
+int ws_of(const pcv_ctx* c, int32_t prec) { return is_mixed(prec) ? kMixedWs0 + engine_of(c, prec) : 0; }
+
+// TMA ring depth of an engine: the caller's choice, else the engine's default.
+int32_t stages_for(const pcv_ctx* c, int engine) {
+    return c->tc_stages_set ? c->tc_stages_set : pcv::mixed_default_stages(engine);
+}
 constexpr int kFallbackSlots = 32;      // tasks needing the FP64 fallback are rare
 
 // Slot count (before the free-memory clamp) and bytes per slot of workspace `wi`
-// (PCV_PREC_FP64, PCV_PREC_MIXED or kFallbackWs).
+// (0 FP64, kFallbackWs, or kMixedWs0 + engine).
 void workspace_shape(const pcv_ctx* c, int wi, int64_t& g, int64_t& sb, int64_t& pb, int32_t& ld) {
     const bool fallback = wi == kFallbackWs;
-    const int prec = fallback ? PCV_PREC_FP64 : wi;
+    const bool mixed = wi >= kMixedWs0;
+    const int prec = mixed ? PCV_PREC_MIXED : PCV_PREC_FP64;
+    const int engine = mixed ? wi - kMixedWs0 : -1;
     ld = round_up(c->kmax, 128);
-    const int planes = prec == PCV_PREC_MIXED ? pcv::mixed_planes(c->opts.factor_engine) : 0;
+    const int planes = mixed ? pcv::mixed_planes(engine) : 0;
     const bool tensor = planes > 0;
     sb = prec == PCV_PREC_FP64 ? pcv::slot_bytes_fp64(ld, c->mmax)
                                : pcv::slot_bytes_mixed(ld, c->mmax, c->lattice ? c->lat_cap : 0);
-    pb = (int64_t)planes * ld * ld * 2;   // 16-bit planes per slot
+    pb = (int64_t)planes * ld * ld * (tensor ? pcv::mixed_term_bytes(engine) : 0);   // planes per slot
     // CTAs per SM: two for both mixed engines (the tensor engine holds half of an
     // SM's tensor memory per CTA), one for the FP64 kernel
     const int per_sm = prec == PCV_PREC_MIXED ? 2 : 1;
@@ -255,7 +283,8 @@ void workspace_shape(const pcv_ctx* c, int wi, int64_t& g, int64_t& sb, int64_t&
 // Allocate `g` slots of sb bytes plus pb bytes of planes each (at most the context's
 // share of free device memory) for slots of leading dimension ld, with the tensor maps
 // of a tensor engine's `np` planes.
-pcv_status alloc_workspace(pcv_ctx* c, Workspace& w, int64_t g, int64_t sb, int64_t pb, int32_t ld, int np) {
+pcv_status alloc_workspace(pcv_ctx* c, Workspace& w, int64_t g, int64_t sb, int64_t pb, int32_t ld, int np,
+                           int term_bytes = 2) {
     size_t free_b = 0, total_b = 0;
     CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
     const double budget = c->opts.workspace_fraction * (double)free_b;
@@ -264,10 +293,10 @@ pcv_status alloc_workspace(pcv_ctx* c, Workspace& w, int64_t g, int64_t sb, int6
     cudaError_t e = w.mem.reserve((size_t)(g * sb));
     if (e != cudaSuccess) return cuda_fail(e, "workspace allocation");
     if (pb > 0) {
-        w.plane_elems = g * (int64_t)ld * ld;
+        w.plane_elems = g * (int64_t)ld * ld * (term_bytes / 2);   // 16-bit units per plane
         e = w.planes.reserve((size_t)(np * w.plane_elems * 2));
         if (e != cudaSuccess) return cuda_fail(e, "plane allocation");
-        if (!pcv::mixed_make_maps(w.planes.p, w.plane_elems, ld, (int)g, np, w.maps))
+        if (!pcv::mixed_make_maps(w.planes.p, w.plane_elems, ld, (int)g, np, term_bytes, w.maps))
             return fail(PCV_ERR_CUDA, "tensor map encoding failed");
     }
     w.grid = (int)g;
@@ -282,19 +311,21 @@ pcv_status ensure_workspace(pcv_ctx* c, int wi) {
     int64_t g, sb, pb;
     int32_t ld;
     workspace_shape(c, wi, g, sb, pb, ld);
-    return alloc_workspace(c, w, g, sb, pb, ld, pb > 0 ? pcv::mixed_planes(c->opts.factor_engine) : 0);
+    const int engine = wi >= kMixedWs0 ? wi - kMixedWs0 : -1;
+    return alloc_workspace(c, w, g, sb, pb, ld, pb > 0 ? pcv::mixed_planes(engine) : 0,
+                           pb > 0 ? pcv::mixed_term_bytes(engine) : 2);
 }
 
 // Mixed-path slot shape of a given slot size and engine (two CTAs per SM).
 void mixed_shape(const pcv_ctx* c, int32_t ld, int engine, int64_t& g, int64_t& sb, int64_t& pb) {
     const int planes = pcv::mixed_planes(engine);
     sb = pcv::slot_bytes_mixed(ld, c->mmax, c->lattice ? c->lat_cap : 0);
-    pb = (int64_t)planes * ld * ld * 2;
+    pb = (int64_t)planes * ld * ld * pcv::mixed_term_bytes(engine);
     g = c->opts.max_slots > 0 ? c->opts.max_slots : 2 * (int64_t)c->sms;
     if (planes > 0) g = std::min<int64_t>(g, 2 * (int64_t)c->sms);
 }
 
-bool bad_precision(int32_t p) { return p != PCV_PREC_FP64 && p != PCV_PREC_MIXED; }
+bool bad_precision(int32_t p) { return p < PCV_PREC_FP64 || p > PCV_PREC_MIXED_F16X2; }
 
 // Whether the values v all lie on v0 + i h for integers 0 <= i < 2^31, h the smallest
 // gap between distinct values refined over the whole range.  The slack is a few FP64
@@ -337,10 +368,10 @@ namespace pcv {
 
 int64_t ctx_workspace_estimate(pcv_ctx* c, int32_t prec) {
     int64_t total = 0;
-    const int list[2] = {prec, prec == PCV_PREC_MIXED ? kFallbackWs : -1};
+    const int list[2] = {ws_of(c, prec), is_mixed(prec) ? kFallbackWs : -1};
     for (int wi : list) {
         if (wi < 0 || c->ws[wi].grid > 0) continue;
-        if (wi == PCV_PREC_MIXED && !c->buckets.empty()) continue;   // the CV launch's buckets are held
+        if (prec == PCV_PREC_MIXED && wi == ws_of(c, prec) && !c->buckets.empty()) continue;   // buckets are held
         int64_t g, sb, pb;
         int32_t ld;
         workspace_shape(c, wi, g, sb, pb, ld);
@@ -365,6 +396,7 @@ void ctx_release_workspace(pcv_ctx* c) {
         w.plane_elems = 0;
     }
     c->buckets.clear();   // rebuilt at the next mixed CV call (the tuner's choice is cached)
+    ++c->mem_gen;         // a captured graph of the CV call names freed memory now
 }
 
 int ctx_device(const pcv_ctx* c) { return c->device; }
@@ -499,6 +531,8 @@ PCV_API pcv_status pcv_create(const double* xy, const double* v, const uint8_t* 
     c->device = device;
     CUDA_TRY(cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device));
     c->opts = default_options(opts);
+    c->tc_stages_set = opts && (opts->struct_size == 0 || opts->struct_size == (int32_t)sizeof(pcv_options)) &&
+                               opts->tc_stages >= 2 && opts->tc_stages <= 4 ? opts->tc_stages : 0;
     c->alpha = std::make_shared<AlphaCache>();
     c->alpha->cap = c->opts.alpha_cache;
     const pcv::Plan& P = c->plan;
@@ -749,7 +783,7 @@ static pcv_status time_engine(pcv_ctx* c, const std::vector<int32_t>& sample, in
     int64_t g, sb, pb;
     mixed_shape(c, ld, engine, g, sb, pb);
     g = std::min<int64_t>(g, (int64_t)sample.size() * Bt);
-    pcv_status st = alloc_workspace(c, w, g, sb, pb, ld, pcv::mixed_planes(engine));
+    pcv_status st = alloc_workspace(c, w, g, sb, pb, ld, pcv::mixed_planes(engine), pcv::mixed_term_bytes(engine));
     if (st != PCV_OK) return st;
     DevBuf<int32_t> ord;
     DevBuf<unsigned int> cnt;
@@ -791,8 +825,20 @@ static pcv_status time_engine(pcv_ctx* c, const std::vector<int32_t>& sample, in
 // and the default engine, every training-size class present gets the engine that ran
 // its sample fastest (cached per process by the class histogram); adjacent classes with
 // the same engine merge.  Otherwise one bucket takes every subset with factor_engine.
+static pcv_status build_buckets(pcv_ctx* c, const double* d_params, int32_t B, cudaStream_t s);
+
 static pcv_status ensure_buckets(pcv_ctx* c, const double* d_params, int32_t B, cudaStream_t s) {
     if (!c->buckets.empty()) return PCV_OK;
+    ++c->mem_gen;
+    const pcv_status st = build_buckets(c, d_params, B, s);
+    if (st != PCV_OK) {
+        c->buckets.clear();   // no half-built list: the next call starts over
+        c->bucket_desc.clear();
+    }
+    return st;
+}
+
+static pcv_status build_buckets(pcv_ctx* c, const double* d_params, int32_t B, cudaStream_t s) {
     const pcv::Plan& P = c->plan;
     std::vector<int32_t> act;
     for (int32_t i = 0; i < P.N; ++i)
@@ -884,7 +930,8 @@ static pcv_status ensure_buckets(pcv_ctx* c, const double* d_params, int32_t B, 
         int64_t g, sb, pb;
         mixed_shape(c, ld, bk.engine, g, sb, pb);
         g = std::min<int64_t>(g, (int64_t)bk.subsets.size() * std::max(B, 1));
-        pcv_status st = alloc_workspace(c, bk.ws, g, sb, pb, ld, pcv::mixed_planes(bk.engine));
+        pcv_status st = alloc_workspace(c, bk.ws, g, sb, pb, ld, pcv::mixed_planes(bk.engine),
+                                        pcv::mixed_term_bytes(bk.engine));
         if (st != PCV_OK) return st;
         CUDA_TRY(bk.order.reserve(bk.subsets.size()));
         CUDA_TRY(cudaMemcpy(bk.order.p, bk.subsets.data(), bk.subsets.size() * sizeof(int32_t),
@@ -892,7 +939,7 @@ static pcv_status ensure_buckets(pcv_ctx* c, const double* d_params, int32_t B, 
         CUDA_TRY(bk.counter.reserve(1));
         CUDA_TRY(cudaStreamCreateWithFlags(&bk.stream, cudaStreamNonBlocking));
         CUDA_TRY(cudaEventCreateWithFlags(&bk.done, cudaEventDisableTiming));
-        static const char* names[] = {"tensor-f16x2", "simt-f32", "tensor-bf16x3"};
+        static const char* names[] = {"tensor-f16x2", "simt-f32", "tensor-bf16x3", "tensor-tf32", "tensor-tf32x3"};
         char line[256];
         std::snprintf(line, sizeof line, "k %d-%d: %zu subsets, engine %s, ld %d, %d slots%s\n", bk.klo, bk.khi,
                       bk.subsets.size(), names[bk.engine], ld, bk.ws.grid, c->buckets_tuned ? " (tuned)" : "");
@@ -914,7 +961,10 @@ static pcv_status run_tasks(pcv_ctx* c, const double* d_params, int32_t B, int32
     CUDA_TRY(c->z.reserve((size_t)B * N));
     CUDA_TRY(c->tst.reserve((size_t)B * N));
     cudaStream_t s = (cudaStream_t)stream;
-    if ((int64_t)n_order * B > 0 && prec == PCV_PREC_MIXED) {
+    // the size buckets serve the context's own mixed mode (PCV_PREC_MIXED); the explicit
+    // engine modes run one launch with their engine
+    bucketed = bucketed && prec == PCV_PREC_MIXED;
+    if ((int64_t)n_order * B > 0 && is_mixed(prec)) {
         int e = pcv::mixed_prepare(c->device);
         if (e) return cuda_fail((cudaError_t)e, "mixed-path set-up");
         if (bucketed) {
@@ -932,11 +982,11 @@ static pcv_status run_tasks(pcv_ctx* c, const double* d_params, int32_t B, int32
     }
     if ((int64_t)n_order * B == 0) return PCV_OK;
     pcv_status st = PCV_OK;
-    if (!(prec == PCV_PREC_MIXED && bucketed)) {
-        st = ensure_workspace(c, prec);
+    if (!bucketed) {
+        st = ensure_workspace(c, ws_of(c, prec));
         if (st != PCV_OK) return st;
     }
-    if (prec == PCV_PREC_MIXED) {
+    if (is_mixed(prec)) {
         st = ensure_workspace(c, kFallbackWs);   // fallback tasks run in FP64
         if (st != PCV_OK) return st;
         CUDA_TRY(c->fb_list.reserve((size_t)n_order * B));
@@ -947,7 +997,7 @@ static pcv_status run_tasks(pcv_ctx* c, const double* d_params, int32_t B, int32
                                 d_param_row, d_rhs, nrhs, lattice);
     const bool timing = c->timing && !c->capturing;   // a captured record would not time the replay
     if (timing) CUDA_TRY(cudaEventRecord(c->ev[0], s));
-    if (prec == PCV_PREC_MIXED && bucketed) {
+    if (bucketed) {
         // the buckets' persistent launches side by side, forked from and joined to `s`
         CUDA_TRY(cudaEventRecord(c->fork, s));
         for (auto& bp : c->buckets) {
@@ -966,19 +1016,20 @@ static pcv_status run_tasks(pcv_ctx* c, const double* d_params, int32_t B, int32
             CUDA_TRY(cudaStreamWaitEvent(s, bk.done, 0));
         }
     } else {
-        Workspace& w = c->ws[prec];
+        Workspace& w = c->ws[ws_of(c, prec)];
+        a.tc_stages = is_mixed(prec) ? stages_for(c, engine_of(c, prec)) : a.tc_stages;
         CUDA_TRY(cudaMemsetAsync(c->counter.p, 0, sizeof(unsigned int), s));
         with_workspace(a, w);
         const int grid = (int)std::min<int64_t>(w.grid, (int64_t)n_order * B);
         int e = prec == PCV_PREC_FP64 ? pcv::launch_task_fp64(a, grid, stream)
-                                      : pcv::launch_task_mixed(a, w.maps, c->opts.factor_engine, grid, stream);
+                                      : pcv::launch_task_mixed(a, w.maps, engine_of(c, prec), grid, stream);
         if (e) return cuda_fail((cudaError_t)e, "task kernel launch");
     }
     if (timing) {
         CUDA_TRY(cudaEventRecord(c->ev[1], s));
         c->timed_task = true;
     }
-    if (prec == PCV_PREC_MIXED) {
+    if (is_mixed(prec)) {
         // tasks the mixed kernel could not finish run again in FP64 (the list and
         // its length stay on the device; CTAs beyond the list exit at once)
         Workspace& w64 = c->ws[kFallbackWs];
@@ -1001,7 +1052,7 @@ static pcv_status run_tasks(pcv_ctx* c, const double* d_params, int32_t B, int32
 static std::vector<const void*> graph_fingerprint(const pcv_ctx* c) {
     std::vector<const void*> f = {c->z.p, c->tst.p, c->fb_list.p, c->fb_count.p, c->ws[kFallbackWs].mem.p,
                                   c->phase.p, c->gparams.p, c->gsspe.p, c->gstatus.p, c->gyhat.p,
-                                  c->alpha->pool.p, c->alpha_slot.p};
+                                  c->alpha->pool.p, c->alpha_slot.p, (const void*)(uintptr_t)c->mem_gen};
     for (const auto& b : c->buckets) {
         f.push_back(b->ws.mem.p);
         f.push_back(b->ws.planes.p);
@@ -1032,13 +1083,23 @@ static pcv_status cv_work(pcv_ctx* c, const double* d_params, int32_t B, int32_t
 // Capture cv_work for B configurations into c->gexec (on the context's own capture
 // stream, so that any caller stream can replay it).  False if the capture did not work
 // out (the call then runs eagerly and this shape is not captured again).
-static bool capture_cv_graph(pcv_ctx* c, int32_t B, bool want_yhat) {
+static bool capture_cv_graph(pcv_ctx* c, const double* d_params, int32_t B, bool want_yhat, cudaStream_t s) {
     if (c->gexec) {
         cudaGraphExecDestroy(c->gexec);
         c->gexec = nullptr;
     }
     if (c->gparams.reserve((size_t)3 * B) != cudaSuccess || c->gsspe.reserve(B) != cudaSuccess ||
         c->gstatus.reserve(B) != cudaSuccess || (want_yhat && c->gyhat.reserve((size_t)B * c->nV) != cudaSuccess))
+        return false;
+    // everything the call allocates is allocated before the capture (a released work
+    // memory, say, is rebuilt here): nothing inside may allocate or synchronise
+    if (pcv::mixed_prepare(c->device) != 0 || ensure_buckets(c, d_params, B, s) != PCV_OK ||
+        ensure_workspace(c, kFallbackWs) != PCV_OK)
+        return false;
+    const int32_t N = c->plan.N;
+    if (c->z.reserve((size_t)B * N) != cudaSuccess || c->tst.reserve((size_t)B * N) != cudaSuccess ||
+        c->fb_list.reserve((size_t)c->n_active * B) != cudaSuccess || c->fb_count.reserve(2) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
         return false;
     if (!c->gcap && cudaStreamCreateWithFlags(&c->gcap, cudaStreamNonBlocking) != cudaSuccess) return false;
     if (cudaStreamBeginCapture(c->gcap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return false;
@@ -1083,7 +1144,7 @@ PCV_API pcv_status pcv_cv_loss_device(pcv_ctx* c, const double* d_params, int32_
         if (c->gexec && c->gkey == key && graph_fingerprint(c) == c->gprint) {
             replay = true;
         } else if (c->gseen == key) {
-            replay = capture_cv_graph(c, B, d_yhat_valid != nullptr);
+            replay = capture_cv_graph(c, d_params, B, d_yhat_valid != nullptr, s);
             c->gkey = replay ? key : -1;
             if (!replay) c->gseen = -2;
         } else if (c->gseen != -2) {
@@ -1205,6 +1266,8 @@ PCV_API pcv_status pcv_neg2loglik(pcv_ctx* c, const double* params, int32_t B, i
     CUDA_TRY(cudaSetDevice(c->device));
     cudaStream_t s = (cudaStream_t)stream;
     const int32_t N = c->plan.N;
+    if (is_mixed(prec) && engine_of(c, prec) != pcv::kMixedEngineTensor && engine_of(c, prec) != pcv::kMixedEngineSimt)
+        return fail(PCV_ERR_ARG, "the local log-likelihood in mixed precision needs the FP16 tensor or the SIMT engine");
     CUDA_TRY(c->params.reserve((size_t)3 * B));
     CUDA_TRY(c->lik_total.reserve(B));
     CUDA_TRY(c->status.reserve(B));
@@ -1409,7 +1472,7 @@ PCV_API pcv_status pcv_gls(pcv_ctx* c, const double* X, int32_t p, const double*
     if (!(s2 > 0.0) || !(rho > 0.0) || !(tau2 > 0.0) || !std::isfinite(s2) || !std::isfinite(rho) ||
         !std::isfinite(tau2))
         return fail(PCV_ERR_ARG, "GLS needs sigma2 > 0, rho > 0 and a nugget tau2 > 0");
-    if (prec == PCV_PREC_MIXED && c->opts.factor_engine != pcv::kMixedEngineTensor)
+    if (is_mixed(prec) && engine_of(c, prec) != pcv::kMixedEngineTensor)
         return fail(PCV_ERR_ARG, "GLS in mixed precision needs the default tensor engine");
     const pcv::Plan& P = c->plan;
     const int32_t N = P.N;

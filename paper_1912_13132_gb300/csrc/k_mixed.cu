@@ -28,6 +28,7 @@
 #include <cstddef>
 #include <cmath>
 #include <mutex>
+#include <type_traits>
 
 #include "df.cuh"
 #include "pcv_internal.h"
@@ -43,7 +44,7 @@ constexpr int NT = 256;  // threads per CTA
 constexpr int KC = 16;   // K chunk of the trailing update
 // the loss-aware stopping rule applies once the solution rule's error bound is within
 // this factor of refine_tol
-constexpr float kLossGuard = 50.0f;
+constexpr float kLossGuard = 1000.0f;
 
 __constant__ dfm::ExpConsts c_exp;
 
@@ -282,8 +283,15 @@ constexpr uint32_t kTcTmemCols = 2 * kTcTilesPerPass * umma::kTileN;
 // the phases between trailing updates, which need kTcRingMin bytes: 2 stages of the
 // three-plane scheme, 3 of the two-plane one.
 constexpr int kTcRingMin = 96 * 1024;
+// (at least kTcRingMin: schemes with small stages get a ring larger than their stages use)
 template <class Sch>
-__host__ __device__ constexpr int tc_ring_bytes(int nst) { return nst * umma::stage_bytes<Sch>(kTcTilesPerPass); }
+__host__ __device__ constexpr int tc_ring_bytes(int nst) {
+    return nst * umma::stage_bytes<Sch>(kTcTilesPerPass) > kTcRingMin ? nst * umma::stage_bytes<Sch>(kTcTilesPerPass)
+                                                                       : kTcRingMin;
+}
+// 16-bit units per term of a scheme (the planes, tensor maps and K chunks count in them)
+template <class Sch>
+__host__ __device__ constexpr int kw() { return Sch::kElem / 2; }
 constexpr int DP = TB + 4;                // row pitch of the diagonal block (rows 16-byte aligned)
 static_assert(TB == 2 * NB, "the tensor-core solves use 2 * NB-wide blocks");
 
@@ -301,26 +309,46 @@ struct TcCtx {
     int row_base;                         // this slot's first row in the tensor maps
 };
 
-// Element (r, c) of a slot's planes: 128 x 32 tiles, tile (r / 128, c / 32),
-// row-major inside a tile (the layout the 3-D tensor maps address).
+// Term (r, c) of a slot's planes, in 16-bit units: 128 x 32-unit tiles (64-byte rows),
+// tile (r / 128, u / 32) for u = c * kw (the unit where the term starts), row-major inside
+// a tile (the layout the 3-D tensor maps address).
+template <class Sch>
 __device__ __forceinline__ int64_t plane_off(int r, int c, int64_t ld) {
-    return ((int64_t)(r >> 7) * (ld >> 5) + (c >> 5)) * 4096 + (r & 127) * 32 + (c & 31);
+    const int u = c * kw<Sch>();
+    return ((int64_t)(r >> 7) * ((ld * kw<Sch>()) >> 5) + (u >> 5)) * 4096 + (r & 127) * 32 + (u & 31);
 }
 
 // Eight consecutive FP32 values (c multiple of 8) split into the scheme's planes.
 template <class Sch>
 __device__ __forceinline__ void store_planes8(const TcCtx& tc, int64_t off, const float* x) {
-    __align__(16) uint16_t t[Sch::kPlanes][8];
+    if constexpr (Sch::kElem == 2) {
+        __align__(16) uint16_t t[Sch::kPlanes][8];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        uint16_t u[Sch::kPlanes];
-        umma::split_terms(Sch{}, x[q], u);
+        for (int q = 0; q < 8; ++q) {
+            uint16_t u[Sch::kPlanes];
+            umma::split_terms(Sch{}, x[q], u);
 #pragma unroll
-        for (int pl = 0; pl < Sch::kPlanes; ++pl) t[pl][q] = u[pl];
+            for (int pl = 0; pl < Sch::kPlanes; ++pl) t[pl][q] = u[pl];
+        }
+#pragma unroll
+        for (int pl = 0; pl < Sch::kPlanes; ++pl)
+            *reinterpret_cast<uint4*>(tc.p[pl] + off) = *reinterpret_cast<const uint4*>(t[pl]);
+    } else {
+        __align__(16) uint32_t t[Sch::kPlanes][8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            uint32_t u[Sch::kPlanes];
+            umma::split_terms(Sch{}, x[q], u);
+#pragma unroll
+            for (int pl = 0; pl < Sch::kPlanes; ++pl) t[pl][q] = u[pl];
+        }
+#pragma unroll
+        for (int pl = 0; pl < Sch::kPlanes; ++pl) {
+            uint4* d = reinterpret_cast<uint4*>(tc.p[pl] + off);
+            d[0] = *reinterpret_cast<const uint4*>(t[pl]);
+            d[1] = *reinterpret_cast<const uint4*>(t[pl] + 4);
+        }
     }
-#pragma unroll
-    for (int pl = 0; pl < Sch::kPlanes; ++pl)
-        *reinterpret_cast<uint4*>(tc.p[pl] + off) = *reinterpret_cast<const uint4*>(t[pl]);
 }
 
 // Cholesky of the nb x nb (nb <= 32) sub-block of D at (c0, c0) by one warp: lane i
@@ -587,7 +615,7 @@ __device__ bool factor_tc(TcCtx& tc, const SlotM& S, int k, int64_t ld, unsigned
 #pragma unroll
                                 for (int j = 0; j < 32; ++j) v[j] = Lr[(int64_t)j * ld] - v[j];
                             }
-                            const int64_t off = plane_off(r, j0 + c0, ld);
+                            const int64_t off = plane_off<Sch>(r, j0 + c0, ld);
 #pragma unroll
                             for (int g = 0; g < 4; ++g) store_planes8<Sch>(tc, off + 8 * g, v + 8 * g);
                         }
@@ -596,7 +624,8 @@ __device__ bool factor_tc(TcCtx& tc, const SlotM& S, int k, int64_t ld, unsigned
             };
             const bool ok = tc.sh->dead == 0 &&
                             umma::block_column<true, kTcTilesPerPass, Sch>(tc.sh->pipe, tc.ph, tc.stages, tc.m0, tc.m1, tc.m2,
-                                                     tc.row_base, j0, k - j0, j0, j0, epi, (int)(ld / 32));
+                                                     tc.row_base, j0, k - j0, j0, j0 * kw<Sch>(), epi,
+                                                     (int)(ld * kw<Sch>() / 32));
             if (!ok) atomicExch(&tc.sh->dead, 1);
             __syncthreads();
             if (tc.sh->dead) return false;
@@ -614,7 +643,7 @@ __device__ bool factor_tc(TcCtx& tc, const SlotM& S, int k, int64_t ld, unsigned
 #pragma unroll
                     for (int q = 0; q < 8; ++q) x[q] = L[r + (int64_t)(g * 8 + q) * ld];
                 }
-                store_planes8<Sch>(tc, plane_off(r, g * 8, ld), x);
+                store_planes8<Sch>(tc, plane_off<Sch>(r, g * 8, ld), x);
             }
             tm.lap(kPhDiagIO);
         }
@@ -720,7 +749,7 @@ __device__ bool factor_tc(TcCtx& tc, const SlotM& S, int k, int64_t ld, unsigned
                 const int c = g * 8 + q;
                 x[q] = c <= r ? D[r][c] * down : 0.0f;
             }
-            store_planes8<Sch>(tc, plane_off(j0 + r, j0 + g * 8, ld), x);
+            store_planes8<Sch>(tc, plane_off<Sch>(j0 + r, j0 + g * 8, ld), x);
         }
         // the planes are read next by TMA (async proxy), which also overwrites the
         // diagonal-block buffer
@@ -747,7 +776,7 @@ __device__ bool factor_tc(TcCtx& tc, const SlotM& S, int k, int64_t ld, unsigned
 #pragma unroll
                             for (int j = 0; j < 32; ++j) acc = fmaf(v[j], fwj[c0 + j], acc);
                         }
-                        const int64_t off = plane_off(r, j0 + c0, ld);
+                        const int64_t off = plane_off<Sch>(r, j0 + c0, ld);
 #pragma unroll
                         for (int g = 0; g < 4; ++g) store_planes8<Sch>(tc, off + 8 * g, v + 8 * g);
                     }
@@ -756,8 +785,8 @@ __device__ bool factor_tc(TcCtx& tc, const SlotM& S, int k, int64_t ld, unsigned
             };
             const bool ok = tc.sh->dead == 0 &&
                             umma::block_column<true, kTcTilesPerPass, Sch>(tc.sh->pipe, tc.ph, tc.stages, tc.m0, tc.m1, tc.m2,
-                                                     tc.row_base, j0 + TB, k - j0 - TB, j0, TB, epi,
-                                                     (int)(ld / 32), j0 / 32);
+                                                     tc.row_base, j0 + TB, k - j0 - TB, j0, TB * kw<Sch>(), epi,
+                                                     (int)(ld * kw<Sch>() / 32), j0 * kw<Sch>() / 32);
             if (!ok) atomicExch(&tc.sh->dead, 1);
             // the panel's planes are read by the next update's TMA loads
             asm volatile("fence.proxy.async.global;" ::: "memory");
@@ -1847,7 +1876,7 @@ __global__ void __launch_bounds__(NT, 2) k_cv_mixed_tc(TaskArgs a, const __grid_
     tc.m0 = &m0;
     tc.m1 = &m1;
     tc.m2 = &m2;
-    const int64_t slot_elems = (int64_t)a.ld * a.ld;
+    const int64_t slot_elems = (int64_t)a.ld * a.ld * kw<Sch>();   // 16-bit units per slot and plane
     uint16_t* P = reinterpret_cast<uint16_t*>(a.planes);
 #pragma unroll
     for (int pl = 0; pl < 3; ++pl)
@@ -1899,58 +1928,82 @@ int mixed_prepare(int device) {
     cudaError_t e = cudaMemcpyToSymbol(c_exp, &k, sizeof(k));
     if (e != cudaSuccess) return (int)e;
     e = cudaFuncSetAttribute(k_cv_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, kSimtSmem);
-    if (e != cudaSuccess) return (int)e;
-    e = cudaFuncSetAttribute(k_cv_mixed_tc<umma::SplitBF16x3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
-    if (e != cudaSuccess) return (int)e;
-    e = cudaFuncSetAttribute(k_cv_mixed_tc<umma::SplitF16x2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
-    if (e != cudaSuccess) return (int)e;
-    e = cudaFuncSetAttribute(k_cv_mixed_tc<umma::SplitF16x2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             kTcSmem);
-    if (e != cudaSuccess) return (int)e;
-    e = cudaFuncSetAttribute(k_cv_mixed_tc<umma::SplitF16x2, false, true>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+    const void* tc_kernels[] = {
+        (const void*)k_cv_mixed_tc<umma::SplitBF16x3>,        (const void*)k_cv_mixed_tc<umma::SplitF16x2>,
+        (const void*)k_cv_mixed_tc<umma::SplitF16x2, true>,   (const void*)k_cv_mixed_tc<umma::SplitF16x2, false, true>,
+        (const void*)k_cv_mixed_tc<umma::SplitTF32x1>,        (const void*)k_cv_mixed_tc<umma::SplitTF32x1, false, true>,
+        (const void*)k_cv_mixed_tc<umma::SplitTF32x3>,        (const void*)k_cv_mixed_tc<umma::SplitTF32x3, false, true>};
+    for (const void* f : tc_kernels)
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
     if (e != cudaSuccess) return (int)e;
     g_prepared[device] = true;
     return 0;
 }
 
 int mixed_planes(int engine) {
-    return engine == kMixedEngineTensor ? umma::SplitF16x2::kPlanes
-           : engine == kMixedEngineTensorBF16 ? umma::SplitBF16x3::kPlanes : 0;
+    switch (engine) {
+        case kMixedEngineTensor: return umma::SplitF16x2::kPlanes;
+        case kMixedEngineTensorBF16: return umma::SplitBF16x3::kPlanes;
+        case kMixedEngineTensorTF32: return umma::SplitTF32x1::kPlanes;
+        case kMixedEngineTensorTF32x3: return umma::SplitTF32x3::kPlanes;
+        default: return 0;
+    }
 }
 
-int mixed_default_stages(int engine) { return engine == kMixedEngineTensorBF16 ? 2 : 3; }
+int mixed_term_bytes(int engine) {
+    return engine == kMixedEngineTensorTF32 || engine == kMixedEngineTensorTF32x3 ? 4 : 2;
+}
+
+int mixed_default_stages(int engine) {
+    switch (engine) {
+        case kMixedEngineTensorBF16: return 2;    // 48 KB stages
+        case kMixedEngineTensorTF32: return 4;    // 16 KB stages
+        default: return 3;                        // 32 KB stages
+    }
+}
+
+namespace {
+template <class Sch>
+int launch_tc(const TaskArgs& a, const CUtensorMap* m, int grid, cudaStream_t st) {
+    const int ring = tc_ring_bytes<Sch>(a.tc_stages);
+    if (a.tc_stages < 2 || a.tc_stages > umma::kStages || ring < kTcRingMin || ring > kTcRingMax)
+        return (int)cudaErrorInvalidValue;
+    if (a.rhs || a.lik) {   // the extended variant exists for the default FP16 scheme only
+        if constexpr (std::is_same<Sch, umma::SplitF16x2>::value)
+            k_cv_mixed_tc<Sch, true><<<grid, NT, tc_smem(ring), st>>>(a, m[0], m[1], m[2]);
+        else
+            return (int)cudaErrorInvalidValue;
+    } else if (a.LX && !std::is_same<Sch, umma::SplitBF16x3>::value) {
+        if constexpr (!std::is_same<Sch, umma::SplitBF16x3>::value)
+            k_cv_mixed_tc<Sch, false, true><<<grid, NT, tc_smem(ring), st>>>(a, m[0], m[1], m[2]);
+    } else {
+        k_cv_mixed_tc<Sch><<<grid, NT, tc_smem(ring), st>>>(a, m[0], m[1], m[2]);
+    }
+    return 0;
+}
+}  // namespace
 
 int launch_task_mixed(const TaskArgs& a, const void* maps, int engine, int grid, void* stream) {
-    if (engine == kMixedEngineTensor || engine == kMixedEngineTensorBF16) {
-        const CUtensorMap* m = reinterpret_cast<const CUtensorMap*>(maps);
-        const bool bf16 = engine == kMixedEngineTensorBF16;
-        const int ring = bf16 ? tc_ring_bytes<umma::SplitBF16x3>(a.tc_stages)
-                              : tc_ring_bytes<umma::SplitF16x2>(a.tc_stages);
-        if (a.tc_stages < 2 || a.tc_stages > umma::kStages || ring < kTcRingMin || ring > kTcRingMax)
-            return (int)cudaErrorInvalidValue;
-        const bool ext = a.rhs || a.lik;
-        if (ext && bf16) return (int)cudaErrorInvalidValue;   // the extended variant: FP16 engine only
-        if (ext)
-            k_cv_mixed_tc<umma::SplitF16x2, true><<<grid, NT, tc_smem(ring), (cudaStream_t)stream>>>(a, m[0], m[1], m[2]);
-        else if (a.LX && !bf16)
-            k_cv_mixed_tc<umma::SplitF16x2, false, true>
-                <<<grid, NT, tc_smem(ring), (cudaStream_t)stream>>>(a, m[0], m[1], m[2]);
-        else if (bf16)
-            k_cv_mixed_tc<umma::SplitBF16x3><<<grid, NT, tc_smem(ring), (cudaStream_t)stream>>>(a, m[0], m[1], m[2]);
-        else
-            k_cv_mixed_tc<umma::SplitF16x2><<<grid, NT, tc_smem(ring), (cudaStream_t)stream>>>(a, m[0], m[1], m[2]);
-    } else {
-        k_cv_mixed<<<grid, NT, kSimtSmem, (cudaStream_t)stream>>>(a);
+    const CUtensorMap* m = reinterpret_cast<const CUtensorMap*>(maps);
+    const cudaStream_t st = (cudaStream_t)stream;
+    int e = 0;
+    switch (engine) {
+        case kMixedEngineTensor: e = launch_tc<umma::SplitF16x2>(a, m, grid, st); break;
+        case kMixedEngineTensorBF16: e = launch_tc<umma::SplitBF16x3>(a, m, grid, st); break;
+        case kMixedEngineTensorTF32: e = launch_tc<umma::SplitTF32x1>(a, m, grid, st); break;
+        case kMixedEngineTensorTF32x3: e = launch_tc<umma::SplitTF32x3>(a, m, grid, st); break;
+        default: k_cv_mixed<<<grid, NT, kSimtSmem, st>>>(a); break;
     }
+    if (e) return e;
     count_launch();
     return (int)cudaGetLastError();
 }
 
-bool mixed_make_maps(void* planes, int64_t plane_elems, int32_t ld, int grid, int nplanes, void* maps_out) {
+bool mixed_make_maps(void* planes, int64_t plane_elems, int32_t ld, int grid, int nplanes, int term_bytes,
+                     void* maps_out) {
     CUtensorMap* m = reinterpret_cast<CUtensorMap*>(maps_out);
     uint16_t* P = reinterpret_cast<uint16_t*>(planes);
-    const uint64_t tiles = (uint64_t)grid * (ld / umma::kTileM) * (ld / umma::kChunkK);
+    const uint64_t tiles = (uint64_t)grid * (ld / umma::kTileM) * (ld * (term_bytes / 2) / umma::kChunkK);
     for (int p = 0; p < 3; ++p)   // maps past the scheme's planes repeat the last one (never used)
         if (!umma::make_tiled_map(&m[p], P + std::min(p, nplanes - 1) * plane_elems, tiles)) return false;
     return true;

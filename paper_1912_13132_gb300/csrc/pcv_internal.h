@@ -114,11 +114,16 @@ int64_t slot_bytes_fp64(int32_t ld, int64_t mmax);
 // cores (three BF16 terms).  maps: three CUtensorMap (128 bytes each) over the
 // planes (tensor engines only; the FP16 scheme uses the first two).
 int launch_task_mixed(const TaskArgs& a, const void* maps, int engine, int grid, void* stream);
-bool mixed_make_maps(void* planes, int64_t plane_elems, int32_t ld, int grid, int nplanes, void* maps_out);
+bool mixed_make_maps(void* planes, int64_t plane_elems, int32_t ld, int grid, int nplanes, int term_bytes,
+                     void* maps_out);
 // mixed-path engines: tensor cores with two-term FP16 operands (default), FP32 SIMT,
-// tensor cores with three-term BF16 operands
-constexpr int kMixedEngineTensor = 0, kMixedEngineSimt = 1, kMixedEngineTensorBF16 = 2;
-int mixed_planes(int engine);           // 16-bit planes of the engine's operand scheme (0: none)
+// tensor cores with three-term BF16 operands, with TF32 operands (one term), with
+// two-term TF32 operands (three products)
+constexpr int kMixedEngineTensor = 0, kMixedEngineSimt = 1, kMixedEngineTensorBF16 = 2,
+              kMixedEngineTensorTF32 = 3, kMixedEngineTensorTF32x3 = 4;
+constexpr int kMixedEngines = 5;
+int mixed_planes(int engine);           // planes of the engine's operand scheme (0: none)
+int mixed_term_bytes(int engine);       // bytes per term of those planes (2 or 4)
 int mixed_default_stages(int engine);   // default operand-ring depth of a tensor engine
 int64_t slot_bytes_mixed(int32_t ld, int64_t mmax, int64_t lat_cap = 0);
 int mixed_prepare(int device);   // one-time per-device set-up of the mixed path

@@ -42,15 +42,39 @@ constexpr int kTileBytes = kTileM * kChunkK * 2;                    // 8 KB
 // <= 2^-22 |x| for |x| >= 2^-14, an absolute 2^-25 below that), three products
 // h*h + h*l + l*h (the dropped l*l is <= 2^-22 |a||b|): a third fewer bytes per
 // element and half the MMAs, for values of magnitude well below 65504.
+// kElem: bytes per term; the planes of 4-byte terms are stored as planes of 16-bit
+// units twice as wide (a 64-byte TMA box row holds 16 of them), so the tiles, tensor
+// maps and K chunks keep their byte layout.  kTF32: the terms are TF32 words, multiplied
+// by tcgen05.mma kind::tf32 (K = 8 per instruction: 32 bytes, as K = 16 of kind::f16).
 struct SplitBF16x3 {
-    static constexpr int kPlanes = 3, kProducts = 6;
+    static constexpr int kPlanes = 3, kProducts = 6, kElem = 2;
+    static constexpr bool kTF32 = false;
     static constexpr uint32_t kFmt = 1;   // instruction-descriptor code of BF16
     __host__ __device__ static constexpr int a(int q) { return q == 2 ? 1 : q == 4 ? 2 : q == 5 ? 1 : 0; }
     __host__ __device__ static constexpr int b(int q) { return q == 1 ? 1 : q == 3 ? 2 : q == 5 ? 1 : 0; }
 };
 struct SplitF16x2 {
-    static constexpr int kPlanes = 2, kProducts = 3;
+    static constexpr int kPlanes = 2, kProducts = 3, kElem = 2;
+    static constexpr bool kTF32 = false;
     static constexpr uint32_t kFmt = 0;   // instruction-descriptor code of FP16
+    __host__ __device__ static constexpr int a(int q) { return q == 2 ? 1 : 0; }
+    __host__ __device__ static constexpr int b(int q) { return q == 1 ? 1 : 0; }
+};
+// TF32x1: x rounded to TF32 (11 significant bits), one product: the plain TF32 tensor-core
+// factorisation, fast but accurate only for well-conditioned matrices.  TF32x3: x = h + l,
+// h = tf32(x), l = tf32(x - h) (22 significant bits), three products h*h + h*l + l*h (the
+// split of Ootomo and Yokota, 2022).
+struct SplitTF32x1 {
+    static constexpr int kPlanes = 1, kProducts = 1, kElem = 4;
+    static constexpr bool kTF32 = true;
+    static constexpr uint32_t kFmt = 2;   // instruction-descriptor code of TF32
+    __host__ __device__ static constexpr int a(int) { return 0; }
+    __host__ __device__ static constexpr int b(int) { return 0; }
+};
+struct SplitTF32x3 {
+    static constexpr int kPlanes = 2, kProducts = 3, kElem = 4;
+    static constexpr bool kTF32 = true;
+    static constexpr uint32_t kFmt = 2;
     __host__ __device__ static constexpr int a(int q) { return q == 2 ? 1 : 0; }
     __host__ __device__ static constexpr int b(int q) { return q == 1 ? 1 : 0; }
 };
@@ -238,6 +262,19 @@ __device__ __forceinline__ void split_terms(SplitF16x2, float x, uint16_t* t) {
     t[1] = __half_as_ushort(l);
 }
 
+// x rounded to TF32 (round to nearest, ties away from zero), as an FP32 word whose low
+// 13 mantissa bits are zero
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ void split_terms(SplitTF32x1, float x, uint32_t* t) { t[0] = to_tf32(x); }
+__device__ __forceinline__ void split_terms(SplitTF32x3, float x, uint32_t* t) {
+    t[0] = to_tf32(x);
+    t[1] = to_tf32(x - __uint_as_float(t[0]));
+}
+
 // ---------------------------------------------------------------- pipeline state
 
 struct Pipe {
@@ -340,8 +377,9 @@ __device__ bool block_column(Pipe& P, Phases& ph, uint8_t* stages, const CUtenso
                             const uint32_t a =
                                 st + (Sch::kPlanes + t * Sch::kPlanes + Sch::a(q)) * kTileBytes + kk * 32;
                             const uint32_t b = st + Sch::b(q) * kTileBytes + kk * 32;
-                            mma_f16kind(d, smem_desc_sw64(a), smem_desc_sw64(b), idesc,
-                                        (kc > 0 || kk > 0 || q > 0) ? 1u : 0u);
+                            const uint32_t acc = (kc > 0 || kk > 0 || q > 0) ? 1u : 0u;
+                            if constexpr (Sch::kTF32) mma_tf32kind(d, smem_desc_sw64(a), smem_desc_sw64(b), idesc, acc);
+                            else mma_f16kind(d, smem_desc_sw64(a), smem_desc_sw64(b), idesc, acc);
                         }
                 }
                 mma_commit(&P.empty[s]);

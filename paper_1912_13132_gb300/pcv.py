@@ -18,7 +18,8 @@ PCV_OK, PCV_ERR_ARG, PCV_ERR_OOM, PCV_ERR_CUDA, PCV_ERR_TIMEOUT = 0, 1, 2, 3, 4
 PCV_ERR_BUSY, PCV_NOT_SPD, PCV_REFINE_FALLBACK, PCV_ERR_UNSUPPORTED = 5, 6, 7, 8
 PCV_PREC_FP64, PCV_PREC_MIXED = 0, 1
 PCV_LAYOUT_RECTS, PCV_LAYOUT_GRID, PCV_LAYOUT_RECURSIVE = 0, 1, 2
-PRECISIONS = {"fp64": PCV_PREC_FP64, "mixed": PCV_PREC_MIXED}
+PRECISIONS = {"fp64": PCV_PREC_FP64, "mixed": PCV_PREC_MIXED, "mixed-tf32": 2, "mixed-tf32x3": 3,
+              "mixed-bf16x3": 4, "mixed-f16x2": 5}
 
 
 class pcv_rect(ctypes.Structure):
@@ -212,7 +213,7 @@ def _stream_ptr(stream) -> int | None:
 
 
 # mixed-path factorisation engines (pcv_options.factor_engine)
-ENGINES = {"tensor": 0, "simt": 1, "tensor-bf16": 2}
+ENGINES = {"tensor": 0, "simt": 1, "tensor-bf16": 2, "tensor-tf32": 3, "tensor-tf32x3": 4}
 
 
 class Context:

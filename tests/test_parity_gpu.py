@@ -195,7 +195,7 @@ def test_paper_scale_sampled(gpu_lib, paper5m, prec, B):
         print("paper-scale", prec, b, worst)
 
 
-@pytest.mark.parametrize("engine", ["tensor", "simt", "tensor-bf16"])
+@pytest.mark.parametrize("engine", ["tensor", "simt", "tensor-bf16", "tensor-tf32", "tensor-tf32x3"])
 def test_mixed_engines(gpu_lib, engine):
     """Every factorisation engine of the mixed path (tcgen05 with two-term FP16 or
     three-term BF16 operands, FP32 SIMT) meets the mixed tolerance on subsets spanning
@@ -208,19 +208,27 @@ def test_mixed_engines(gpu_lib, engine):
         V_off = ctx.V_off.copy()
     members = oracle.all_members(w.xy, w.role, w.layout)
     ref = oracle.cv_loss(w.xy, w.v, w.role, w.layout, P, members=members)
-    assert np.all(out["status"] == 0), out["status"]
+    if engine == "tensor-tf32":   # 11-bit operands: ill-conditioned tasks fall back to FP64
+        assert np.all(np.isin(out["status"], (0, 7))), out["status"]
+    else:
+        assert np.all(out["status"] == 0), out["status"]
     worst = compare(out, ref, V_off, range(16), len(P), "mixed")
-    print("mixed", engine, worst)
+    print("mixed", engine, out["status"].tolist(), worst)
 
 
 @pytest.mark.parametrize("rho,tau2", [(0.02, 0.001), (0.02, 0.1), (0.2, 0.001), (0.2, 0.01), (0.2, 0.1)])
-@pytest.mark.parametrize("prec,engine", [("mixed", "tensor"), ("mixed", "tensor-bf16"), ("fp64", "tensor")])
+@pytest.mark.parametrize("prec,engine", [("mixed", "tensor"), ("mixed", "tensor-bf16"), ("fp64", "tensor"),
+                                         ("mixed-tf32", "tensor"), ("mixed-tf32x3", "tensor")])
 def test_grid_precision_stress(gpu_lib, prec, engine, rho, tau2):
     """Gridded 1024^2 training set (fine 2048^2 grid, 131 072 validation nodes), 32-cell
     cores with 8-cell shells (k = 1600 / 1920 / 2304): the conditioning sweep of the
     precision-stress workload (rho in {0.02, 0.2}, tau2 in {0.001, 0.01, 0.1}, the
-    largest condition numbers near 1e6).  The field's own parameters are evaluated;
-    sampled subsets (corner, edge, interior) are compared with the oracle."""
+    largest condition numbers near 1e6), for every operand scheme of the tensor-core
+    factorisation (FP16 x2, BF16 x3, TF32 x1, TF32 x3) and FP64.  The field's own
+    parameters are evaluated; sampled subsets (corner, edge, interior) are compared
+    with the oracle.  Plain TF32 (11 significant bits) is expected to fail its
+    refinement on the ill-conditioned cases: those tasks are recomputed in FP64
+    (status PCV_REFINE_FALLBACK) and still meet the bar; the counts are printed."""
     w = datagen.config_grid_1m(rho=rho, tau2=tau2)
     P = w.params
     nx = w.layout["nx"]
@@ -235,6 +243,8 @@ def test_grid_precision_stress(gpu_lib, prec, engine, rho, tau2):
     members = {i: oracle.subset_members(w.xy, w.role, w.layout, i, cores) for i in pick}
     ref = oracle.cv_loss(w.xy, w.v, w.role, w.layout, P, members=members, subsets=pick)
     worst = compare(out, ref, V_off, pick, 1, prec, check_total=False)
+    if prec == "mixed-tf32x3" or (prec == "mixed" and engine != "simt"):
+        assert out["status"][0] == 0, out["status"]       # the 22-24-bit schemes refine every task
     counts = {k: ph.get(k) for k in ("tasks", "residual_passes", "fail_factor", "fail_nan", "fail_stall")}
     print("grid stress", prec, engine, rho, tau2, out["status"].tolist(), worst, counts)
 
