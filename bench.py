@@ -495,6 +495,7 @@ def run_cluster(pcv, device: int, steps: int = 3) -> dict:
         k = np.diff(ctx.T_off)[np.diff(ctx.V_off) > 0]
         out[label] = dict(value=B * steps / (sum(ms) / 1e3), unit=UNIT, ms_per_step=sum(ms) / steps, steps=steps,
                           status=st, setup_s=round(first_s, 2), buckets=ctx.buckets().strip().splitlines())
+        # (the bucket lines, then the autotuner's per-class timings when this context tuned)
         out.update(active_subsets=int(len(k)), k_min=int(k.min()), k_max=int(k.max()))
         ctx.close()
     out["bucketed_over_one_launch"] = out["bucketed"]["value"] / out["one_launch"]["value"]

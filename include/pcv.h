@@ -481,6 +481,12 @@ pcv_status pcv_selftest_df_device(int32_t op, const double* d_a, const double* d
  * PCV_ERR_TIMEOUT if one of the kernel's bounded waits ran out. */
 pcv_status pcv_selftest_umma(const float* A, int32_t M, const float* B, int32_t K, float* C);
 
+/* The same product with the operand scheme of each tensor engine: scheme 0 = three BF16
+ * terms (six products), 1 = two FP16 terms (three products), 2 = TF32 (one product,
+ * tcgen05.mma kind::tf32), 3 = two TF32 terms (three products).  Same arguments, limits
+ * and errors as pcv_selftest_umma (PCV_ERR_ARG for an unknown scheme). */
+pcv_status pcv_selftest_umma_scheme(int32_t scheme, const float* A, int32_t M, const float* B, int32_t K, float* C);
+
 /* Throughput probes for roofline denominators (the paper has no counterpart; they
  * measure the device, not the method).  kind: 0 FP64 fused multiply-add, 1 FP32 fused
  * multiply-add (SIMT pipes, every SM), 2 tcgen05 kind::tf32, 3 kind::f16 with BF16

@@ -42,23 +42,39 @@ pcv_status cuda_fail(cudaError_t e, const char* where) {
         if (e_ != cudaSuccess) return cuda_fail(e_, #expr);         \
     } while (0)
 
+// Device buffer that grows on demand.  Growing never frees the old allocation at once:
+// cudaFree waits for the whole device, which would stall a call behind kernels other
+// streams (other serving lanes) are running; the old block is kept until release() (the
+// context idle or destroyed), and growth is geometric so that few such blocks pile up.
 template <class T>
 struct DevBuf {
     T* p = nullptr;
     size_t n = 0;
+    std::vector<T*> retired;
     ~DevBuf() { release(); }
     void release() {
         if (p) cudaFree(p);
+        for (T* q : retired) cudaFree(q);
+        retired.clear();
         p = nullptr;
         n = 0;
     }
     cudaError_t reserve(size_t want) {
+        want = std::max<size_t>(want, 1);
         if (want <= n && p) return cudaSuccess;
-        release();
-        size_t bytes = std::max<size_t>(want, 1) * sizeof(T);
-        cudaError_t e = cudaMalloc(&p, bytes);
-        if (e == cudaSuccess) n = std::max<size_t>(want, 1);
-        return e;
+        size_t cnt = std::max(want, n + n / 2);
+        T* q = nullptr;
+        cudaError_t e = cudaMalloc(&q, cnt * sizeof(T));
+        if (e != cudaSuccess && cnt > want) {   // the geometric size did not fit: the exact one may
+            cudaGetLastError();
+            cnt = want;
+            e = cudaMalloc(&q, cnt * sizeof(T));
+        }
+        if (e != cudaSuccess) return e;
+        if (p) retired.push_back(p);
+        p = q;
+        n = cnt;
+        return cudaSuccess;
     }
 };
 
@@ -149,6 +165,7 @@ struct pcv_ctx {
     int32_t tc_stages_set = 0;              // ring depth the caller asked for (0: each engine's default)
     // prediction buffers
     DevBuf<double> Px, Py, Pyhat;
+    DevBuf<double> yv;                      // validation predictions of the host-buffer CV call
     DevBuf<int64_t> Poff;
     DevBuf<int32_t> Porder;
     DevBuf<int32_t> prow;                   // parameter row of each subset (local predictions)
@@ -772,7 +789,8 @@ static int size_class(int32_t k) {
     return c;
 }
 
-static std::mutex g_tune_mu;
+static std::mutex g_tune_mu;       // guards the cache below
+static std::mutex g_tune_run_mu;   // held from the cache lookup through tuning: contexts with one key tune once
 static std::map<std::string, std::vector<int>> g_tune_cache;   // key -> engine per class
 
 // Time the mixed task kernel with `engine` on a sample of subsets (each evaluated with
@@ -848,6 +866,7 @@ static pcv_status build_buckets(pcv_ctx* c, const double* d_params, int32_t B, c
     });
     auto ksz = [&](int32_t i) { return (int32_t)(P.T_off[i + 1] - P.T_off[i]); };
     std::vector<int> eng(kClasses, c->opts.factor_engine);
+    std::string tune_notes;
     std::vector<std::vector<int32_t>> cls(kClasses);
     for (int32_t i : act) cls[size_class(ksz(i))].push_back(i);
     const bool tune = c->opts.bucketing == 0 && c->opts.factor_engine == pcv::kMixedEngineTensor;
@@ -858,6 +877,7 @@ static pcv_status build_buckets(pcv_ctx* c, const double* d_params, int32_t B, c
         for (int q = 0; q < kClasses; ++q)
             if (!cls[q].empty()) key += std::to_string(q) + ":" + std::to_string(cls[q].size()) + ",";
         bool cached = false;
+        std::lock_guard<std::mutex> run_lk(g_tune_run_mu);
         {
             std::lock_guard<std::mutex> lk(g_tune_mu);
             auto it = g_tune_cache.find(key);
@@ -900,6 +920,10 @@ static pcv_status build_buckets(pcv_ctx* c, const double* d_params, int32_t B, c
                     // the SIMT engine must win clearly (timing noise must not flip the choice)
                     eng[q] = t_simt < 0.9 * t_tc ? pcv::kMixedEngineSimt : pcv::kMixedEngineTensor;
                     timed = true;
+                    char line[200];
+                    std::snprintf(line, sizeof line, "tuned k %d-%d (%lld sampled x %d): tensor %.4f ms/task, simt %.4f ms/task\n",
+                                  ksz(L.back()), ksz(L.front()), (long long)ns, Bt, t_tc, t_simt);
+                    tune_notes += line;
                 }
             }
             c->buckets_tuned = timed;
@@ -945,6 +969,7 @@ static pcv_status build_buckets(pcv_ctx* c, const double* d_params, int32_t B, c
                       bk.subsets.size(), names[bk.engine], ld, bk.ws.grid, c->buckets_tuned ? " (tuned)" : "");
         c->bucket_desc += line;
     }
+    c->bucket_desc += tune_notes;
     std::stable_sort(c->buckets.begin(), c->buckets.end(),
                      [](const std::unique_ptr<Bucket>& x, const std::unique_ptr<Bucket>& y) { return x->work > y->work; });
     if (!c->fork) CUDA_TRY(cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming));
@@ -1191,7 +1216,7 @@ PCV_API pcv_status pcv_cv_loss(pcv_ctx* c, const double* params, int32_t B, int3
     CUDA_TRY(c->params.reserve((size_t)3 * B));
     CUDA_TRY(c->sspe.reserve(B));
     CUDA_TRY(c->status.reserve(B));
-    DevBuf<double> yv;
+    DevBuf<double>& yv = c->yv;   // (a context buffer: no allocation and free per call)
     if (yhat_valid) CUDA_TRY(yv.reserve((size_t)B * c->nV));
     CUDA_TRY(cudaMemcpyAsync(c->params.p, params, (size_t)3 * B * sizeof(double), cudaMemcpyHostToDevice, s));
     // rows of the kriging-weight cache for the valid configurations of the batch

@@ -113,7 +113,124 @@ __global__ void __launch_bounds__(256, 1) k_umma_test(const __grid_constant__ CU
     if (threadIdx.x == 0) *err = sm.err;
 }
 
+// ---- the same product with any operand scheme (16-bit or TF32 terms)
+
+template <class Sch>
+__global__ void k_split_scheme(const float* x, int64_t n, uint16_t* planes, int64_t plane_units) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if constexpr (Sch::kElem == 2) {
+        uint16_t t[Sch::kPlanes];
+        pcv::umma::split_terms(Sch{}, x[i], t);
+        for (int p = 0; p < Sch::kPlanes; ++p) planes[p * plane_units + i] = t[p];
+    } else {
+        uint32_t t[Sch::kPlanes];
+        pcv::umma::split_terms(Sch{}, x[i], t);
+        for (int p = 0; p < Sch::kPlanes; ++p) reinterpret_cast<uint32_t*>(planes + p * plane_units)[i] = t[p];
+    }
+}
+
+template <class Sch>
+__global__ void __launch_bounds__(256, 1) k_umma_test_scheme(const __grid_constant__ CUtensorMap m0,
+                                                             const __grid_constant__ CUtensorMap m1,
+                                                             const __grid_constant__ CUtensorMap m2, int M, int K,
+                                                             float* C, int* err) {
+    using namespace pcv::umma;
+    extern __shared__ __align__(1024) unsigned char raw[];
+    uint8_t* base = (uint8_t*)(((uintptr_t)raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* stages = base;
+    UmmaTestSmem& sm = *reinterpret_cast<UmmaTestSmem*>(base + kTestStages * stage_bytes<Sch>(kTilesPerPass));
+    const int warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) {
+        pipe_init(sm.pipe, kTestStages);
+        sm.err = 0;
+    }
+    if (warp == 1) tmem_alloc(&sm.pipe.tmem_base, kTmemCols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    Phases ph;
+    auto epi = [&](int row0, int quad, uint32_t taddr) {
+        const int r = row0 - kTileM + quad * 32 + (threadIdx.x & 31);
+        for (int c0 = 0; c0 < kTileN; c0 += 32) {
+            float v[32];
+            tmem_ld32(taddr + c0, v);
+            if (r < M)
+                for (int j = 0; j < 32; ++j) C[(int64_t)r * kTileN + c0 + j] = v[j];
+        }
+    };
+    const bool ok = block_column<false, kTilesPerPass, Sch>(sm.pipe, ph, stages, &m0, &m1, &m2, 0, kTileM, M, 0,
+                                                            K * (Sch::kElem / 2), epi);
+    if (!ok) atomicExch(&sm.err, 1);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) tmem_dealloc(sm.pipe.tmem_base, kTmemCols);
+    if (threadIdx.x == 0) *err = sm.err;
+}
+
+template <class Sch>
+pcv_status umma_scheme_test(const float* A, int32_t M, const float* B, int32_t K, float* C) {
+    using namespace pcv::umma;
+    const int Mp = (M + kTileM - 1) / kTileM * kTileM;
+    const int64_t rows = kTileM + Mp;
+    std::vector<float> X((size_t)rows * K, 0.0f);
+    for (int r = 0; r < kTileM; ++r)
+        for (int k = 0; k < K; ++k) X[(size_t)r * K + k] = B[(size_t)r * K + k];
+    for (int r = 0; r < M; ++r)
+        for (int k = 0; k < K; ++k) X[(size_t)(kTileM + r) * K + k] = A[(size_t)r * K + k];
+    const int64_t n = rows * K;
+    const int64_t units = n * (Sch::kElem / 2);   // 16-bit units per plane
+    float *dX = nullptr, *dC = nullptr;
+    uint16_t* dP = nullptr;
+    int* dErr = nullptr;
+    pcv_status st = PCV_OK;
+    if (cudaMalloc(&dX, n * 4) || cudaMalloc(&dP, Sch::kPlanes * units * 2) ||
+        cudaMalloc(&dC, (size_t)M * kTileN * 4) || cudaMalloc(&dErr, 4)) {
+        st = PCV_ERR_OOM;
+    } else {
+        cudaMemcpy(dX, X.data(), n * 4, cudaMemcpyHostToDevice);
+        k_split_scheme<Sch><<<(unsigned)((n + 255) / 256), 256>>>(dX, n, dP, units);
+        CUtensorMap m[3];
+        bool ok = true;
+        for (int p = 0; p < 3; ++p)
+            ok = ok && make_plane_map(&m[p], dP + std::min(p, Sch::kPlanes - 1) * units,
+                                      (uint64_t)K * (Sch::kElem / 2), (uint64_t)rows);
+        if (!ok) {
+            st = PCV_ERR_CUDA;
+        } else {
+            const int smem = kTestStages * stage_bytes<Sch>(kTilesPerPass) + (int)sizeof(UmmaTestSmem) + 1024;
+            cudaFuncSetAttribute(k_umma_test_scheme<Sch>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            k_umma_test_scheme<Sch><<<1, 256, smem>>>(m[0], m[1], m[2], M, K, dC, dErr);
+            pcv::count_launch(2);
+            int herr = 0;
+            if (cudaMemcpy(&herr, dErr, 4, cudaMemcpyDeviceToHost) != cudaSuccess) st = PCV_ERR_CUDA;
+            else if (herr) st = PCV_ERR_TIMEOUT;
+            else if (cudaMemcpy(C, dC, (size_t)M * kTileN * 4, cudaMemcpyDeviceToHost) != cudaSuccess) st = PCV_ERR_CUDA;
+        }
+    }
+    cudaFree(dX);
+    cudaFree(dP);
+    cudaFree(dC);
+    cudaFree(dErr);
+    return st;
+}
+
 }  // namespace
+
+// The block-column product of the mixed path's factorisation with one operand scheme:
+// scheme 0 = three BF16 terms, 1 = two FP16 terms, 2 = TF32, 3 = two TF32 terms.
+PCV_API pcv_status pcv_selftest_umma_scheme(int32_t scheme, const float* A, int32_t M, const float* B, int32_t K,
+                                            float* C) {
+    using namespace pcv::umma;
+    if (!A || !B || !C || M < 1 || K < kChunkK || K % kChunkK) return PCV_ERR_ARG;
+    switch (scheme) {
+        case 0: return umma_scheme_test<SplitBF16x3>(A, M, B, K, C);
+        case 1: return umma_scheme_test<SplitF16x2>(A, M, B, K, C);
+        case 2: return umma_scheme_test<SplitTF32x1>(A, M, B, K, C);
+        case 3: return umma_scheme_test<SplitTF32x3>(A, M, B, K, C);
+        default: return PCV_ERR_ARG;
+    }
+}
 
 // C (M x 128, row-major) = A (M x K) * B (128 x K)^T through the split-BF16 tensor-core
 // pipeline; K a positive multiple of 32.  Host arrays.  Returns PCV_ERR_TIMEOUT if a

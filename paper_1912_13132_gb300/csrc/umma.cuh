@@ -79,8 +79,11 @@ struct SplitTF32x3 {
     __host__ __device__ static constexpr int b(int q) { return q == 1 ? 1 : 0; }
 };
 
+// one stage: per plane, the B operand's bn / 128 boxes and TPP A tiles
 template <class Sch = SplitBF16x3>
-__host__ __device__ constexpr int stage_bytes(int tpp) { return Sch::kPlanes * (tpp + 1) * kTileBytes; }
+__host__ __device__ constexpr int stage_bytes(int tpp, int bn = kTileN) {
+    return Sch::kPlanes * (tpp + bn / kTileM) * kTileBytes;
+}
 constexpr uint32_t kTmemCols = 512;
 constexpr uint64_t kWaitNs = 2000000000ull;  // bound of every mbarrier wait (2 s)
 
@@ -288,8 +291,9 @@ struct Pipe {
 
 // Per-role phase counters; every role walks the same sequence of stages and passes.
 struct Phases {
-    uint32_t stage = 0;   // stage iterations done (ring position and parity)
-    uint32_t pass = 0;    // passes done (accumulator buffer and parity)
+    uint32_t stage = 0;          // stage iterations done (ring position and parity)
+    uint32_t nextbuf = 0;        // accumulator buffer of the next pass of a double-buffered call
+    uint32_t uses[2] = {0, 0};   // passes that have used each accumulator buffer (barrier parities)
 };
 
 __device__ inline void pipe_init(Pipe& p, uint32_t nstages = kStages) {
@@ -306,12 +310,18 @@ __device__ inline void pipe_init(Pipe& p, uint32_t nstages = kStages) {
 }
 
 // One block-column product over all row tiles:
-//   rows [r0, r0 + nrows) of A against rows [b0, b0 + 128) of B over the K columns
-//   [kc0 * kChunkK, kc0 * kChunkK + K), K a multiple of kChunkK.  A and B rows live
-//   in the planes' tensor maps at row offset `row_base` (the task's slot).  For each
-//   finished 128-row tile the epilogue warps call epi(tile_row0, warp_quadrant,
-//   taddr_of_tile) and must read all 128 columns of their 32 lanes.  Returns false
-//   if a bounded wait ran out.
+//   rows [r0, r0 + nrows) of A against rows [b0, b0 + BN) of B over the K columns
+//   [kc0 * kChunkK, kc0 * kChunkK + K), K a multiple of kChunkK (in 16-bit units).  A and
+//   B rows live in the planes' tensor maps at row offset `row_base` (the task's slot).  For
+//   each finished 128-row tile the epilogue warps call epi(tile_row0, warp_quadrant,
+//   taddr_of_tile) and must read all BN columns of their 32 lanes.  BN = 128 or 256 (the B
+//   operand is BN / 128 boxes per plane, one MMA of N = BN per product).  NBUF = 2: the
+//   accumulators of consecutive passes alternate between two TMEM buffers of TPP * BN
+//   columns, so a pass's epilogue overlaps the next pass's MMAs; NBUF = 1: one buffer, the
+//   next pass waits for the epilogue.  Calls of different shapes may follow one another
+//   on one Pipe once the previous call has returned in every thread (a barrier): the
+//   barrier parities follow each buffer's own use count.  Returns false if a bounded wait
+//   ran out.
 // Operand layouts in global memory.  Row-major: a plane is a row-major matrix and a
 // box is 128 rows x 32 columns of it.  Tiled: a plane is stored as contiguous 8 KB
 // tiles of 128 rows x 32 columns (tile (R, kc) at index R * nkc + kc), so that every
@@ -322,10 +332,13 @@ __device__ __forceinline__ void load_box(void* dst, const CUtensorMap* map, int 
     else tma_load_2d(dst, map, kc * kChunkK, row, bar);
 }
 
-template <bool TILED = false, int TPP = kTilesPerPass, class Sch = SplitBF16x3, class Epi>
+template <bool TILED = false, int TPP = kTilesPerPass, class Sch = SplitBF16x3, int BN = kTileN, int NBUF = 2,
+          class Epi>
 __device__ bool block_column(Pipe& P, Phases& ph, uint8_t* stages, const CUtensorMap* mapA0,
                              const CUtensorMap* mapA1, const CUtensorMap* mapA2, int row_base, int r0,
                              int nrows, int b0, int K, Epi&& epi, int nkc = 0, int kc0 = 0) {
+    static_assert(BN % kTileM == 0 && BN <= 256 && (NBUF == 1 || NBUF == 2), "block-column shape");
+    constexpr int BB = BN / kTileM;   // B boxes per plane
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int ntiles = (nrows + kTileM - 1) / kTileM;
     const int npass = (ntiles + TPP - 1) / TPP;
@@ -342,41 +355,42 @@ __device__ bool block_column(Pipe& P, Phases& ph, uint8_t* stages, const CUtenso
                 const int s = it % P.nstages;
                 const uint32_t par = ((it / P.nstages) & 1) ^ 1;
                 if (!mbar_wait(&P.empty[s], par)) { ok = false; break; }
-                uint8_t* st = stages + s * stage_bytes<Sch>(TPP);
-                mbar_expect_tx(&P.full[s], (uint32_t)(Sch::kPlanes * (nt + 1) * kTileBytes));
+                uint8_t* st = stages + s * stage_bytes<Sch>(TPP, BN);
+                mbar_expect_tx(&P.full[s], (uint32_t)(Sch::kPlanes * (nt + BB) * kTileBytes));
                 for (int pl = 0; pl < Sch::kPlanes; ++pl) {
-                    load_box<TILED>(st + pl * kTileBytes, maps[pl], kc0 + kc, row_base + b0, nkc, &P.full[s]);
+                    for (int h = 0; h < BB; ++h)
+                        load_box<TILED>(st + (pl * BB + h) * kTileBytes, maps[pl], kc0 + kc,
+                                        row_base + b0 + h * kTileM, nkc, &P.full[s]);
                     for (int t = 0; t < nt; ++t)
-                        load_box<TILED>(st + (Sch::kPlanes + t * Sch::kPlanes + pl) * kTileBytes, maps[pl], kc0 + kc,
-                                        row_base + r0 + (t0 + t) * kTileM, nkc, &P.full[s]);
+                        load_box<TILED>(st + (Sch::kPlanes * BB + t * Sch::kPlanes + pl) * kTileBytes, maps[pl],
+                                        kc0 + kc, row_base + r0 + (t0 + t) * kTileM, nkc, &P.full[s]);
                 }
             }
         }
     } else if (warp == 1 && lane == 0) {
         // MMA issuer
-        uint32_t it = ph.stage;
-        const uint32_t idesc = idesc_f16kind(kTileM, kTileN, Sch::kFmt);
+        uint32_t it = ph.stage, nb = ph.nextbuf, u[2] = {ph.uses[0], ph.uses[1]};
+        const uint32_t idesc = idesc_f16kind(kTileM, BN, Sch::kFmt);
         for (int p = 0; p < npass && ok; ++p) {
             const int t0 = p * TPP;
             const int nt = min(TPP, ntiles - t0);
-            const uint32_t pp = ph.pass + p;
-            const int buf = pp & 1;
-            if (!mbar_wait(&P.acce[buf], ((pp >> 1) & 1) ^ 1)) { ok = false; break; }
+            const int buf = NBUF == 1 ? 0 : (int)nb;
+            if (!mbar_wait(&P.acce[buf], (u[buf] & 1) ^ 1)) { ok = false; break; }
             tc_fence_after();
             for (int kc = 0; kc < nk; ++kc, ++it) {
                 const int s = it % P.nstages;
                 if (!mbar_wait(&P.full[s], (it / P.nstages) & 1)) { ok = false; break; }
                 tc_fence_after();
-                const uint32_t st = smem_u32(stages + s * stage_bytes<Sch>(TPP));
+                const uint32_t st = smem_u32(stages + s * stage_bytes<Sch>(TPP, BN));
                 for (int t = 0; t < nt; ++t) {
-                    const uint32_t d = P.tmem_base + buf * (TPP * kTileN) + t * kTileN;
+                    const uint32_t d = P.tmem_base + buf * (TPP * BN) + t * BN;
 #pragma unroll
                     for (int kk = 0; kk < kChunkK / 16; ++kk)
 #pragma unroll
                         for (int q = 0; q < Sch::kProducts; ++q) {
                             const uint32_t a =
-                                st + (Sch::kPlanes + t * Sch::kPlanes + Sch::a(q)) * kTileBytes + kk * 32;
-                            const uint32_t b = st + Sch::b(q) * kTileBytes + kk * 32;
+                                st + (Sch::kPlanes * BB + t * Sch::kPlanes + Sch::a(q)) * kTileBytes + kk * 32;
+                            const uint32_t b = st + Sch::b(q) * BB * kTileBytes + kk * 32;
                             const uint32_t acc = (kc > 0 || kk > 0 || q > 0) ? 1u : 0u;
                             if constexpr (Sch::kTF32) mma_tf32kind(d, smem_desc_sw64(a), smem_desc_sw64(b), idesc, acc);
                             else mma_f16kind(d, smem_desc_sw64(a), smem_desc_sw64(b), idesc, acc);
@@ -385,34 +399,43 @@ __device__ bool block_column(Pipe& P, Phases& ph, uint8_t* stages, const CUtenso
                 mma_commit(&P.empty[s]);
             }
             if (ok) mma_commit(&P.accf[buf]);
+            ++u[buf];
+            if (NBUF == 2) nb ^= 1u;
         }
     } else if (warp >= 4) {
         // epilogue: one warp per TMEM lane quadrant
         const int quad = warp & 3;
+        uint32_t nb = ph.nextbuf, u[2] = {ph.uses[0], ph.uses[1]};
         for (int p = 0; p < npass && ok; ++p) {
             const int t0 = p * TPP;
             const int nt = min(TPP, ntiles - t0);
-            const uint32_t pp = ph.pass + p;
-            const int buf = pp & 1;
+            const int buf = NBUF == 1 ? 0 : (int)nb;
             // every lane polls the barrier on its own; agree on the outcome (which also
             // reconverges the warp before the aligned TMEM loads of the epilogue)
-            const bool got = mbar_wait(&P.accf[buf], (pp >> 1) & 1);
+            const bool got = mbar_wait(&P.accf[buf], u[buf] & 1);
             if (!__all_sync(0xffffffffu, got)) { ok = false; break; }
             tc_fence_after();
             for (int t = 0; t < nt; ++t) {
-                const uint32_t taddr = P.tmem_base + ((uint32_t)(quad * 32) << 16) +
-                                       buf * (TPP * kTileN) + t * kTileN;
+                const uint32_t taddr = P.tmem_base + ((uint32_t)(quad * 32) << 16) + buf * (TPP * BN) + t * BN;
                 epi(r0 + (t0 + t) * kTileM, quad, taddr);
             }
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&P.acce[buf]);
+            ++u[buf];
+            if (NBUF == 2) nb ^= 1u;
         }
     }
     // every role advances its counters identically (the producer and MMA counts
     // follow from the shape alone)
     ph.stage += (uint32_t)(npass > 0 ? npass * nk : 0);
-    ph.pass += (uint32_t)npass;
+    if (NBUF == 1) {
+        ph.uses[0] += (uint32_t)npass;
+    } else {
+        ph.uses[ph.nextbuf] += (uint32_t)((npass + 1) / 2);
+        ph.uses[ph.nextbuf ^ 1u] += (uint32_t)(npass / 2);
+        ph.nextbuf ^= (uint32_t)(npass & 1);
+    }
     return ok;
 }
 

@@ -92,6 +92,9 @@ _SIGS = {
     "pcv_buckets": (ctypes.c_int32, [_vp, ctypes.c_char_p, ctypes.c_int32]),
     "pcv_alpha_cache_stats": (ctypes.c_int, [_vp, _i64p, _i64p, _i32p]),
     "pcv_measure_peak": (ctypes.c_int, [ctypes.c_int32, ctypes.c_double, _dp, _dp]),
+    "pcv_selftest_umma_scheme": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(ctypes.c_float), ctypes.c_int32,
+                                                ctypes.POINTER(ctypes.c_float), ctypes.c_int32,
+                                                ctypes.POINTER(ctypes.c_float)]),
     "pcv_server_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int32, ctypes.POINTER(pcv_server_options),
                                          ctypes.POINTER(_vp)]),
     "pcv_server_submit_cv": (ctypes.c_int, [_vp, ctypes.c_int32, _dp, _i64p]),
@@ -511,6 +514,22 @@ def pcv_measure_peak(kind: str, seconds: float = 2.0) -> dict:
     _check(_lib.pcv_measure_peak(PEAK_KINDS[kind], float(seconds), ctypes.byref(t), ctypes.byref(e)),
            "pcv_measure_peak")
     return dict(tflops=t.value, seconds=e.value)
+
+
+UMMA_SCHEMES = {"bf16x3": 0, "f16x2": 1, "tf32": 2, "tf32x3": 3}
+
+
+def pcv_selftest_umma_scheme(scheme: str, A, B):
+    """C = A @ B.T (B has 128 rows) through the tcgen05 pipeline with an operand scheme;
+    returns (status, C)."""
+    A = np.ascontiguousarray(A, dtype=np.float32)
+    B = np.ascontiguousarray(B, dtype=np.float32)
+    assert B.shape[0] == 128 and A.shape[1] == B.shape[1]
+    C = np.zeros((A.shape[0], 128), dtype=np.float32)
+    fp = ctypes.POINTER(ctypes.c_float)
+    st = _lib.pcv_selftest_umma_scheme(UMMA_SCHEMES[scheme], A.ctypes.data_as(fp), A.shape[0], B.ctypes.data_as(fp),
+                                       A.shape[1], C.ctypes.data_as(fp))
+    return int(st), C
 
 
 def pcv_lattice_detect(xy):
