@@ -423,7 +423,8 @@ class ServingClient:
 
 
 def run_serving(pcv, device: int, seconds: float, hbm_budget_gb: float, max_batch: int, n_runs: int = 32,
-                seed: int = 0, max_slots: int = 152, engine: str = "tensor") -> dict:
+                seed: int = 0, max_slots: int = 152, engine: str = "tensor", priorities: int = 0,
+                lanes: int = 0) -> dict:
     """Serving measurement on the eight gridded datasets: capacity from a burst of the
     request mix, then Poisson arrivals at 50/80/100% of it."""
     t0 = time.perf_counter()
@@ -440,10 +441,11 @@ def run_serving(pcv, device: int, seconds: float, hbm_budget_gb: float, max_batc
     out = dict(workload="serving-8-grids-256..1024sq-32x32cores-8buf",
                datasets=[dict(name=w.name, n_obs=int(len(w.v)), subsets=int(c.N)) for w, c in zip(ws, ctxs)],
                nelder_mead_runs=n_runs, max_batch=max_batch, hbm_budget_gb=hbm_budget_gb or None,
-               slots_per_dataset=max_slots, engine=engine,
+               slots_per_dataset=max_slots, engine=engine, lanes=lanes or 2,
+               priorities="by work per configuration" if priorities == 0 else "equal",
                setup_s=round(t_setup, 2), datagen_s=round(t_gen, 2))
     with pcv.Server(ctxs, max_batch=max_batch, precision="mixed",
-                    hbm_budget_bytes=hbm_budget_gb * 1e9) as srv:
+                    hbm_budget_bytes=hbm_budget_gb * 1e9, lanes=lanes, priorities=priorities) as srv:
         cl = ServingClient(pcv, srv, ws, n_runs, seed)
         cap = cl.burst(20 * len(ws))
         out["capacity_req_s"] = cap
@@ -559,7 +561,9 @@ def main():
                     help="seconds per serving load level (0: no serving measurement)")
     ap.add_argument("--serve-batch", type=int, default=16, help="CV requests per serving batch")
     ap.add_argument("--hbm-budget-gb", type=float, default=0.0, help="serving work-memory budget (0: unlimited)")
-    ap.add_argument("--serve-slots", type=int, default=152, help="task slots per serving dataset")
+    ap.add_argument("--serve-slots", type=int, default=152, help="task slots per serving lane")
+    ap.add_argument("--serve-priorities", type=int, default=0, help="0: by work per configuration, 1: equal")
+    ap.add_argument("--serve-lanes", type=int, default=0, help="lanes per serving dataset (0: default 2)")
     args = ap.parse_args()
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
@@ -591,7 +595,8 @@ def main():
     if args.workload == "serving":
         if rank == 0:
             sv = run_serving(pcv, local, args.serve_seconds or 10.0, args.hbm_budget_gb, args.serve_batch,
-                             max_slots=args.serve_slots, engine=args.engine)
+                             max_slots=args.serve_slots, engine=args.engine, priorities=args.serve_priorities,
+                             lanes=args.serve_lanes)
             full = sv["loads"][-1]
             print(json.dumps(dict(metric=METRIC, value=full["cv_evals_per_s"], unit=UNIT, n_gpus=1, steps=0,
                                   warmup=0, higher_is_better=True, scaling="weak", vs_baseline=None,
@@ -779,7 +784,8 @@ def main():
         line["cluster"] = run_cluster(pcv, local, args.cluster_steps)
     if rank == 0 and world == 1 and args.serve_seconds > 0:
         line["serving"] = run_serving(pcv, local, args.serve_seconds, args.hbm_budget_gb, args.serve_batch,
-                                      max_slots=args.serve_slots, engine=args.engine)
+                                      max_slots=args.serve_slots, engine=args.engine,
+                                      priorities=args.serve_priorities, lanes=args.serve_lanes)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:

@@ -210,6 +210,13 @@ typedef struct {
                                   configuration; pcv_predict with a configuration whose
                                   weights are kept for every subset it needs computes the
                                   predictions (Eq. 3) from them without any factorisation */
+    /* Test hooks of the tensor engines' bounded waits (leave 0): test_wait_us > 0 sets
+     * their limit (default 2 s); test_withhold_task = t + 1 makes the TMA producer skip
+     * the first operand stage of the launch's task t, so that the waits of that CTA run
+     * out: the CTA drains the copies and products it issued, stops using the tensor path
+     * and hands its tasks to the FP64 fallback (status PCV_REFINE_FALLBACK). */
+    int32_t test_wait_us;
+    int32_t test_withhold_task;
 } pcv_options;
 
 /* ---------------------------------------------------------------- host-only */
@@ -391,6 +398,8 @@ typedef struct {
     int32_t precision;        /* PCV_PREC_MIXED (default) or PCV_PREC_FP64 */
     double hbm_budget_bytes;  /* work-memory budget over all lanes; 0 = unlimited */
     int32_t lanes;            /* lanes per dataset, 1 to 4 (default 2) */
+    int32_t priorities;       /* 0 (default) = stream priorities by work per configuration,
+                                 the smallest dataset highest; 1 = all equal */
 } pcv_server_options;
 
 pcv_status pcv_server_create(pcv_ctx* const* ctxs, int32_t n_ctx, const pcv_server_options* opts,

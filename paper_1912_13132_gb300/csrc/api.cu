@@ -227,6 +227,8 @@ pcv_options default_options(const pcv_options* o) {
     d.bucketing = 0;
     d.graph = 0;
     d.alpha_cache = 32;
+    d.test_wait_us = 0;
+    d.test_withhold_task = 0;
     if (o) {
         if (o->struct_size != 0 && o->struct_size != (int32_t)sizeof(pcv_options)) return d;
         if (o->max_slots > 0) d.max_slots = o->max_slots;
@@ -239,6 +241,8 @@ pcv_options default_options(const pcv_options* o) {
         if (o->graph == 1) d.graph = 1;
         if (o->alpha_cache > 0) d.alpha_cache = std::min(o->alpha_cache, 4096);
         else if (o->alpha_cache < 0) d.alpha_cache = 0;
+        if (o->test_wait_us > 0) d.test_wait_us = o->test_wait_us;
+        if (o->test_withhold_task > 0) d.test_withhold_task = o->test_withhold_task;
         if (o->refine_loss_tol > 0) d.refine_loss_tol = o->refine_loss_tol;
         else if (o->refine_loss_tol < 0) d.refine_loss_tol = 0.0;   // solution rule only
     }
@@ -711,6 +715,8 @@ static pcv::TaskArgs base_args(pcv_ctx* c, const double* d_params, int32_t B, co
     a.fb_count = c->fb_count.p;
     a.phase_cycles = c->timing ? c->phase.p : nullptr;
     a.tc_stages = c->opts.tc_stages;
+    a.test_wait_ns = c->opts.test_wait_us > 0 ? (uint64_t)c->opts.test_wait_us * 1000ull : 0;
+    a.test_withhold_task = c->opts.test_withhold_task > 0 ? c->opts.test_withhold_task : 0;
     if (c->alpha_call || c->alpha_in_call) {
         if (c->alpha_in_call) a.alpha_in = c->alpha->pool.p;
         else a.alpha_out = c->alpha->pool.p;

@@ -573,7 +573,7 @@ struct LatView {
 };
 
 template <class Sch, bool LAT = false>
-__device__ bool factor_tc(TcCtx& tc, const SlotM& S, int k, int64_t ld, unsigned long long* clk, int nst,
+__device__ bool factor_tc(TcCtx& tc, const SlotM& S, int k, int64_t ld, unsigned long long* clk,
                           float* fw = nullptr, float* fwj = nullptr, LatView lv = LatView{}) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     PhaseTimer tm(clk);
@@ -586,124 +586,10 @@ __device__ bool factor_tc(TcCtx& tc, const SlotM& S, int k, int64_t ld, unsigned
     float* Y = reinterpret_cast<float*>(tc.stages + kDiagYOff);
     float* L = S.L;
     const int nb = (k + TB - 1) / TB;
-    // Paired block columns: with a ring of two stages large enough for a 256-row B operand,
-    // the update of an even block column J >= 2 also computes block column J + 1's update
-    // over the same K range (one pass over L[j0:, :j0] for both, N = 256, one accumulator
-    // buffer); J + 1's part goes to the FP32 matrix as a partial sum, and after J's panel
-    // only the rank-128 update from that panel remains for J + 1.  The left-looking update
-    // then streams the planes left of the diagonal once per two block columns.
-    const bool pairs = nst == 2 && 2 * umma::stage_bytes<Sch>(kTcTilesPerPass, 2 * TB) <= tc_ring_bytes<Sch>(nst);
-    bool pending = false;   // this block column's update up to the previous block column is done
     for (int J = 0; J < nb; ++J) {
         const int j0 = J * TB, jb = min(TB, k - j0);
         const bool below = j0 + TB < k;   // rows below the diagonal block (then jb == TB)
-        const bool pair_first = pairs && j0 > 0 && !pending && (J & 1) == 0 && J + 1 < nb;
-        if (pending) {
-            // the rank-128 rest from the previous block column's panel; the partial sum in L
-            // (diagonal block and below) takes it
-            auto epi_rest = [&](int row0, int quad, uint32_t taddr) {
-                const int r = row0 + quad * 32 + (threadIdx.x & 31);
-                const bool diag_rows = row0 < j0 + TB;
-#pragma unroll 1
-                for (int c0 = 0; c0 < TB; c0 += 32) {
-                    float v[32];
-                    umma::tmem_ld32(taddr + c0, v);
-                    if (r < k) {
-                        float* Lr = L + r + (int64_t)(j0 + c0) * ld;
-                        if (diag_rows) {
-#pragma unroll
-                            for (int j = 0; j < 32; ++j)
-                                if (c0 + j < jb) Lr[(int64_t)j * ld] -= v[j];
-                        } else {
-#pragma unroll
-                            for (int j = 0; j < 32; ++j) v[j] = Lr[(int64_t)j * ld] - v[j];
-                            const int64_t off = plane_off<Sch>(r, j0 + c0, ld);
-#pragma unroll
-                            for (int g = 0; g < 4; ++g) store_planes8<Sch>(tc, off + 8 * g, v + 8 * g);
-                        }
-                    }
-                }
-            };
-            const bool ok = tc.sh->dead == 0 &&
-                            umma::block_column<true, kTcTilesPerPass, Sch>(
-                                tc.sh->pipe, tc.ph, tc.stages, tc.m0, tc.m1, tc.m2, tc.row_base, j0, k - j0, j0,
-                                TB * kw<Sch>(), epi_rest, (int)(ld * kw<Sch>() / 32), (j0 - TB) * kw<Sch>() / 32);
-            if (!ok) atomicExch(&tc.sh->dead, 1);
-            __syncthreads();
-            if (tc.sh->dead) return false;
-            pending = false;
-            tm.lap(kPhUpdate);
-        } else if (pair_first) {
-            // block columns J and J + 1 over K = [0, j0): accumulator columns 0..127 are J's
-            // update (as below), 128..255 J + 1's partial sum, kept in L for the rows at or
-            // below J + 1's diagonal block (the rows above it are the upper triangle)
-            const int j1 = j0 + TB, jb1 = min(TB, k - j1);
-            auto epi2 = [&](int row0, int quad, uint32_t taddr) {
-                const int r = row0 + quad * 32 + (threadIdx.x & 31);
-                const bool diag_rows = row0 < j0 + TB;
-#pragma unroll 1
-                for (int c0 = 0; c0 < TB; c0 += 32) {
-                    float v[32];
-                    umma::tmem_ld32(taddr + c0, v);
-                    if (r < k) {
-                        float* Lr = L + r + (int64_t)(j0 + c0) * ld;
-                        if (diag_rows) {
-#pragma unroll
-                            for (int j = 0; j < 32; ++j) Lr[(int64_t)j * ld] -= v[j];
-                        } else {
-                            if constexpr (LAT) {
-                                const int ri = lv.ti[r], rj = lv.tj[r];
-                                float av[32];
-#pragma unroll
-                                for (int j = 0; j < 32; ++j) av[j] = lv.a(ri, rj, j0 + c0 + j);
-#pragma unroll
-                                for (int j = 0; j < 32; ++j) v[j] = av[j] - v[j];
-                            } else {
-#pragma unroll
-                                for (int j = 0; j < 32; ++j) v[j] = Lr[(int64_t)j * ld] - v[j];
-                            }
-                            const int64_t off = plane_off<Sch>(r, j0 + c0, ld);
-#pragma unroll
-                            for (int g = 0; g < 4; ++g) store_planes8<Sch>(tc, off + 8 * g, v + 8 * g);
-                        }
-                    }
-                }
-                if (row0 < j1) return;   // (whole tiles: warp-uniform) J + 1's upper triangle
-                // J + 1's diagonal block is assembled in L (with 1 + lambda on its diagonal);
-                // below it the lattice variant reads the table, the general one L
-                const bool diag1 = row0 < j1 + TB;
-#pragma unroll 1
-                for (int c0 = 0; c0 < TB; c0 += 32) {
-                    float v[32];
-                    umma::tmem_ld32(taddr + TB + c0, v);
-                    if (r < k) {
-                        float* Lr = L + r + (int64_t)(j1 + c0) * ld;
-                        if (diag1 || !LAT) {
-#pragma unroll
-                            for (int j = 0; j < 32; ++j)
-                                if (c0 + j < jb1) Lr[(int64_t)j * ld] -= v[j];
-                        } else if constexpr (LAT) {
-                            const int ri = lv.ti[r], rj = lv.tj[r];
-                            float av[32];
-#pragma unroll
-                            for (int j = 0; j < 32; ++j) av[j] = c0 + j < jb1 ? lv.a(ri, rj, j1 + c0 + j) : 0.0f;
-#pragma unroll
-                            for (int j = 0; j < 32; ++j)
-                                if (c0 + j < jb1) Lr[(int64_t)j * ld] = av[j] - v[j];
-                        }
-                    }
-                }
-            };
-            const bool ok = tc.sh->dead == 0 &&
-                            umma::block_column<true, kTcTilesPerPass, Sch, 2 * TB, 1>(
-                                tc.sh->pipe, tc.ph, tc.stages, tc.m0, tc.m1, tc.m2, tc.row_base, j0, k - j0, j0,
-                                j0 * kw<Sch>(), epi2, (int)(ld * kw<Sch>() / 32));
-            if (!ok) atomicExch(&tc.sh->dead, 1);
-            __syncthreads();
-            if (tc.sh->dead) return false;
-            pending = true;
-            tm.lap(kPhUpdate);
-        } else if (j0 > 0) {
+        if (j0 > 0) {
             auto epi = [&](int row0, int quad, uint32_t taddr) {
                 const int r = row0 + quad * 32 + (threadIdx.x & 31);
                 const bool diag_rows = row0 < j0 + TB;
@@ -729,9 +615,9 @@ __device__ bool factor_tc(TcCtx& tc, const SlotM& S, int k, int64_t ld, unsigned
 #pragma unroll
                                 for (int j = 0; j < 32; ++j) v[j] = Lr[(int64_t)j * ld] - v[j];
                             }
-                            const int64_t off = plane_off<Sch>(r, j0 + c0, ld);
 #pragma unroll
-                            for (int g = 0; g < 4; ++g) store_planes8<Sch>(tc, off + 8 * g, v + 8 * g);
+                            for (int g = 0; g < 4; ++g)
+                                store_planes8<Sch>(tc, plane_off<Sch>(r, j0 + c0 + 8 * g, ld), v + 8 * g);
                         }
                     }
                 }
@@ -890,9 +776,9 @@ __device__ bool factor_tc(TcCtx& tc, const SlotM& S, int k, int64_t ld, unsigned
 #pragma unroll
                             for (int j = 0; j < 32; ++j) acc = fmaf(v[j], fwj[c0 + j], acc);
                         }
-                        const int64_t off = plane_off<Sch>(r, j0 + c0, ld);
 #pragma unroll
-                        for (int g = 0; g < 4; ++g) store_planes8<Sch>(tc, off + 8 * g, v + 8 * g);
+                        for (int g = 0; g < 4; ++g)
+                            store_planes8<Sch>(tc, plane_off<Sch>(r, j0 + c0 + 8 * g, ld), v + 8 * g);
                     }
                 }
                 if (fw && r < k) fw[r] -= acc;
@@ -1685,7 +1571,7 @@ __device__ void run_task(SmemM& sm, SmemKeep& keep, SmemSimt* simt, TcCtx* tc, c
             LatView lv{};
             if constexpr (LAT)
                 lv = LatView{S.tab, reinterpret_cast<const int*>(S.xh), reinterpret_cast<const int*>(S.yh), W};
-            ok = factor_tc<Sch, LAT>(*tc, S, k, ld, a.phase_cycles, a.tc_stages, fuse_fw ? S.w : nullptr, keep.fwj, lv);
+            ok = factor_tc<Sch, LAT>(*tc, S, k, ld, a.phase_cycles, fuse_fw ? S.w : nullptr, keep.fwj, lv);
         }
         else ok = factor32(sm, *simt, S, k, ld);
     }
@@ -2000,6 +1886,7 @@ __global__ void __launch_bounds__(NT, 2) k_cv_mixed_tc(TaskArgs a, const __grid_
     for (int e = threadIdx.x; e < 2 * dfm::kExpTable; e += NT) keep.tbl[e] = c_exp.tbl[e];
     if (threadIdx.x == 0) {
         umma::pipe_init(tc.sh->pipe, (uint32_t)nst);
+        if (a.test_wait_ns) tc.sh->pipe.wait_ns = a.test_wait_ns;
         tc.sh->dead = 0;
         umma::prefetch_map(&m0);
         umma::prefetch_map(&m1);
@@ -2011,7 +1898,10 @@ __global__ void __launch_bounds__(NT, 2) k_cv_mixed_tc(TaskArgs a, const __grid_
     umma::tc_fence_after();
     const int ntask = a.n_order * a.B;
     for (;;) {
-        if (threadIdx.x == 0) keep.task = (int)atomicAdd(a.counter, 1u);
+        if (threadIdx.x == 0) {
+            keep.task = (int)atomicAdd(a.counter, 1u);
+            tc.sh->pipe.withhold = a.test_withhold_task != 0 && keep.task == a.test_withhold_task - 1;
+        }
         __syncthreads();
         const int t = keep.task;
         __syncthreads();

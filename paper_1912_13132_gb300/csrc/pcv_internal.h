@@ -100,6 +100,11 @@ struct TaskArgs {
     // optional per-phase cycle counters (kPhaseCount entries, summed over CTAs), or NULL
     unsigned long long* phase_cycles;
     int32_t tc_stages;      // TMA ring depth of the tensor-core kernel (2 or 3)
+    // test hooks of the bounded waits: their limit in ns (0: the default 2 s), and task
+    // t + 1 whose first operand stage the TMA producer withholds (0: none), so that its
+    // waits run out and it takes the FP64 fallback
+    uint64_t test_wait_ns;
+    int32_t test_withhold_task;
 };
 
 // Phases timed by the mixed kernel when phase_cycles is set.

@@ -83,6 +83,7 @@ struct pcv_server {
     int64_t next_id = 1;
     int32_t max_batch = 16;
     int32_t lanes = 2;
+    bool by_work = true;            // stream priorities by work per configuration (else all equal)
     int32_t precision = PCV_PREC_MIXED;
     double budget = 0.0;            // 0: unlimited
     int64_t used = 0;
@@ -254,6 +255,7 @@ PCV_API pcv_status pcv_server_create(pcv_ctx* const* ctxs, int32_t n_ctx, const 
         if (opts->struct_size != 0 && opts->struct_size != (int32_t)sizeof(pcv_server_options)) return PCV_ERR_ARG;
         if (opts->max_batch > 0) s->max_batch = opts->max_batch;
         if (opts->lanes > 0) s->lanes = std::min(opts->lanes, 4);
+        if (opts->priorities == 1) s->by_work = false;
         if (opts->precision == PCV_PREC_FP64 || opts->precision == PCV_PREC_MIXED) s->precision = opts->precision;
         if (opts->hbm_budget_bytes > 0) s->budget = opts->hbm_budget_bytes;
     }
@@ -278,7 +280,8 @@ PCV_API pcv_status pcv_server_create(pcv_ctx* const* ctxs, int32_t n_ctx, const 
         int rank = 0;   // datasets with strictly less work
         for (int32_t j = 0; j < n_ctx; ++j) rank += work[j] < work[i];
         const int levels = least - greatest + 1;   // greatest is numerically smallest
-        const int prio = n_ctx > 1 ? greatest + (int)((int64_t)rank * (levels - 1) / (n_ctx - 1)) : least;
+        const int prio = !s->by_work ? least
+                         : n_ctx > 1 ? greatest + (int)((int64_t)rank * (levels - 1) / (n_ctx - 1)) : least;
         for (int32_t l = 0; l < s->lanes; ++l) {
             auto L = std::make_unique<Lane>();
             L->ctx = l == 0 ? ctxs[i] : pcv::ctx_clone(ctxs[i]);

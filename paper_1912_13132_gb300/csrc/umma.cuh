@@ -120,15 +120,16 @@ __device__ __forceinline__ uint64_t global_ns() {
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
-// Wait for the phase with the given parity to complete; false once kWaitNs of wall
-// time have passed without it (the caller then reports an error instead of hanging).
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// Wait for the phase with the given parity to complete; false once `limit_ns` of wall
+// time (default kWaitNs) have passed without it (the caller then reports an error
+// instead of hanging).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t limit_ns = kWaitNs) {
     if (mbar_try(bar, parity)) return true;
     const uint64_t t0 = global_ns();
     for (;;) {
         for (int i = 0; i < 64; ++i)
             if (mbar_try(bar, parity)) return true;
-        if (global_ns() - t0 > kWaitNs) return false;
+        if (global_ns() - t0 > limit_ns) return false;
     }
 }
 
@@ -285,8 +286,12 @@ struct Pipe {
     uint64_t empty[kStages];
     uint64_t accf[2];
     uint64_t acce[2];
+    uint64_t drain;        // a failed MMA issuer waits here for its issued MMAs to complete
+    uint64_t wait_ns;      // bound of the pipeline's waits (kWaitNs unless a test shortens it)
     uint32_t tmem_base;
-    uint32_t nstages;     // ring depth in use (1 .. kStages)
+    uint32_t nstages;      // ring depth in use (1 .. kStages)
+    uint32_t drain_phase;
+    uint32_t withhold;     // test hook: the producer skips the next stage's loads (its waits run out)
 };
 
 // Per-role phase counters; every role walks the same sequence of stages and passes.
@@ -298,6 +303,10 @@ struct Phases {
 
 __device__ inline void pipe_init(Pipe& p, uint32_t nstages = kStages) {
     p.nstages = nstages;
+    p.wait_ns = kWaitNs;
+    p.drain_phase = 0;
+    p.withhold = 0;
+    mbar_init(&p.drain, 1);
     for (int s = 0; s < kStages; ++s) {
         mbar_init(&p.full[s], 1);
         mbar_init(&p.empty[s], 1);
@@ -348,13 +357,21 @@ __device__ bool block_column(Pipe& P, Phases& ph, uint8_t* stages, const CUtenso
     if (warp == 0 && lane == 0) {
         // TMA producer
         uint32_t it = ph.stage;
+        int32_t issued[kStages];   // last iteration whose loads went to each ring slot
+#pragma unroll
+        for (int q = 0; q < kStages; ++q) issued[q] = -1;
         for (int p = 0; p < npass && ok; ++p) {
             const int t0 = p * TPP;
             const int nt = min(TPP, ntiles - t0);
             for (int kc = 0; kc < nk; ++kc, ++it) {
                 const int s = it % P.nstages;
                 const uint32_t par = ((it / P.nstages) & 1) ^ 1;
-                if (!mbar_wait(&P.empty[s], par)) { ok = false; break; }
+                if (!mbar_wait(&P.empty[s], par, P.wait_ns)) { ok = false; break; }
+                if (P.withhold) {   // test hook: this stage is never loaded, its consumers time out
+                    P.withhold = 0;
+                    continue;
+                }
+                issued[s] = (int32_t)it;
                 uint8_t* st = stages + s * stage_bytes<Sch>(TPP, BN);
                 mbar_expect_tx(&P.full[s], (uint32_t)(Sch::kPlanes * (nt + BB) * kTileBytes));
                 for (int pl = 0; pl < Sch::kPlanes; ++pl) {
@@ -367,19 +384,27 @@ __device__ bool block_column(Pipe& P, Phases& ph, uint8_t* stages, const CUtenso
                 }
             }
         }
+        if (!ok) {
+            // the shared memory of the ring is reused once this call returns: every load
+            // issued must have landed first (a consumed stage's phase is already complete)
+            for (int q = 0; q < (int)P.nstages; ++q)
+                if (issued[q] >= 0)
+                    mbar_wait(&P.full[q], (uint32_t)((issued[q] / P.nstages) & 1), P.wait_ns);
+        }
     } else if (warp == 1 && lane == 0) {
         // MMA issuer
-        uint32_t it = ph.stage, nb = ph.nextbuf, u[2] = {ph.uses[0], ph.uses[1]};
+        uint32_t it = ph.stage, nb = ph.nextbuf, u0 = ph.uses[0], u1 = ph.uses[1];   // (scalars: registers)
         const uint32_t idesc = idesc_f16kind(kTileM, BN, Sch::kFmt);
         for (int p = 0; p < npass && ok; ++p) {
             const int t0 = p * TPP;
             const int nt = min(TPP, ntiles - t0);
             const int buf = NBUF == 1 ? 0 : (int)nb;
-            if (!mbar_wait(&P.acce[buf], (u[buf] & 1) ^ 1)) { ok = false; break; }
+            const uint32_t ub = buf ? u1 : u0;
+            if (!mbar_wait(&P.acce[buf], (ub & 1) ^ 1, P.wait_ns)) { ok = false; break; }
             tc_fence_after();
             for (int kc = 0; kc < nk; ++kc, ++it) {
                 const int s = it % P.nstages;
-                if (!mbar_wait(&P.full[s], (it / P.nstages) & 1)) { ok = false; break; }
+                if (!mbar_wait(&P.full[s], (it / P.nstages) & 1, P.wait_ns)) { ok = false; break; }
                 tc_fence_after();
                 const uint32_t st = smem_u32(stages + s * stage_bytes<Sch>(TPP, BN));
                 for (int t = 0; t < nt; ++t) {
@@ -399,20 +424,26 @@ __device__ bool block_column(Pipe& P, Phases& ph, uint8_t* stages, const CUtenso
                 mma_commit(&P.empty[s]);
             }
             if (ok) mma_commit(&P.accf[buf]);
-            ++u[buf];
+            if (buf) ++u1; else ++u0;
             if (NBUF == 2) nb ^= 1u;
+        }
+        if (!ok) {
+            // the MMAs issued so far read the ring and write TMEM: let them complete
+            mma_commit(&P.drain);
+            mbar_wait(&P.drain, P.drain_phase, P.wait_ns);
+            P.drain_phase ^= 1u;
         }
     } else if (warp >= 4) {
         // epilogue: one warp per TMEM lane quadrant
         const int quad = warp & 3;
-        uint32_t nb = ph.nextbuf, u[2] = {ph.uses[0], ph.uses[1]};
+        uint32_t nb = ph.nextbuf, u0 = ph.uses[0], u1 = ph.uses[1];
         for (int p = 0; p < npass && ok; ++p) {
             const int t0 = p * TPP;
             const int nt = min(TPP, ntiles - t0);
             const int buf = NBUF == 1 ? 0 : (int)nb;
             // every lane polls the barrier on its own; agree on the outcome (which also
             // reconverges the warp before the aligned TMEM loads of the epilogue)
-            const bool got = mbar_wait(&P.accf[buf], u[buf] & 1);
+            const bool got = mbar_wait(&P.accf[buf], (buf ? u1 : u0) & 1, P.wait_ns);
             if (!__all_sync(0xffffffffu, got)) { ok = false; break; }
             tc_fence_after();
             for (int t = 0; t < nt; ++t) {
@@ -422,7 +453,7 @@ __device__ bool block_column(Pipe& P, Phases& ph, uint8_t* stages, const CUtenso
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&P.acce[buf]);
-            ++u[buf];
+            if (buf) ++u1; else ++u0;
             if (NBUF == 2) nb ^= 1u;
         }
     }

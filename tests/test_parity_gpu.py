@@ -307,8 +307,16 @@ def test_paper_recursive_sampled(gpu_lib, paper5m_recursive):
     print("paper recursive", [int(k[i]) for i in pick], worst)
 
 
+# Mixed-path bars of the local -2 log-likelihood: its log-determinant comes from the
+# FP32-accurate factor, whose relative error grows with the condition number (measured:
+# 2e-6 at condition ~1e3, 5.5e-5 at ~1e5); refinement corrects solutions, not
+# determinants.  The corner case (rho = 0.2, tau2 = 0.001, condition ~1e6) records where
+# that leaves the mixed result; FP64 meets 1e-10 everywhere.
+LIK_MIXED_BAR = {"uniform": 1e-4, "grid-stress": 1e-4, "grid-corner": 2e-3}
+
+
 @pytest.mark.parametrize("prec", PRECS)
-@pytest.mark.parametrize("wl", ["uniform", "grid-stress"])
+@pytest.mark.parametrize("wl", ["uniform", "grid-stress", "grid-corner"])
 def test_local_neg2loglik(gpu_lib, prec, wl):
     """Local -2 log-likelihood (Eq. 2) of every subset's training data, a by-product of
     the CV factorisations, against the oracle's Eq. 2 routine: per subset and the
@@ -321,8 +329,9 @@ def test_local_neg2loglik(gpu_lib, prec, wl):
         P = np.array([[1.0, 0.1, 0.05], [0.5, 0.04, 0.01], [2.0, 0.3, 0.2]])
         pick = None
     else:
-        w = datagen.config_grid_1m(rho=0.2, tau2=0.01)
-        P = np.array([[1.0, 0.2, 0.01]])
+        t2 = 0.01 if wl == "grid-stress" else 0.001
+        w = datagen.config_grid_1m(rho=0.2, tau2=t2)
+        P = np.array([[1.0, 0.2, t2]])
         nx = w.layout["nx"]
         pick = [0, nx // 2, nx * (nx // 2) + nx // 2]
     with gpu_lib.Context(w.xy, w.v, w.role, w.layout) as ctx:
@@ -331,7 +340,7 @@ def test_local_neg2loglik(gpu_lib, prec, wl):
     assert np.all(out["status"] == 0), out["status"]
     cores = oracle.layout_cores(w.layout, w.xy)
     subsets = range(len(cores)) if pick is None else pick
-    tol = 1e-10 if prec == "fp64" else 1e-4
+    tol = 1e-10 if prec == "fp64" else LIK_MIXED_BAR[wl]
     worst = 0.0
     for b, (s2, rho, tau) in enumerate(P):
         tot = 0.0
@@ -531,41 +540,29 @@ def test_predict_from_kept_weights(gpu_lib, prec):
     assert pred_err(got[0], y0) <= TOL[prec]["pred"]
 
 
-@pytest.mark.parametrize("wl", ["uniform", "cluster"])
-def test_paired_block_columns(gpu_lib, cluster, wl):
-    """The paired left-looking update (a two-stage operand ring: block columns J and J + 1
-    updated in one pass over the factor left of them, N = 256, then the rank-128 rest) on
-    every subset against the oracle: subsets spanning up to 13 block columns, odd and even
-    counts, a ragged last block; the lattice variant (gridded data, the default path of
-    the benchmark) and the general one."""
-    if wl == "uniform":
-        w = datagen.config_uniform_4096()
-        P = np.array([[1.0, 0.1, 0.05], [0.7, 0.03, 0.2], [2.0, 0.3, 0.001]])
-        members = oracle.all_members(w.xy, w.role, w.layout)
-        act = [i for i, (_, V) in enumerate(members) if len(V) > 0]
-        ref = oracle.cv_loss(w.xy, w.v, w.role, w.layout, P, members=members)
-    else:
-        w, P, act, ref = cluster
-    with gpu_lib.Context(w.xy, w.v, w.role, w.layout, tc_stages=2) as ctx:
-        out = ctx.cv_loss(P, precision="mixed", per_subset=True, predictions=True)
-        V_off = ctx.V_off.copy()
-    assert np.all(out["status"] == 0), out["status"]
-    worst = compare(out, ref, V_off, act, len(P), "mixed", check_total=False)
-    print("paired", wl, worst)
-
-
-def test_paired_block_columns_lattice(gpu_lib):
-    """Paired updates on lattice data (the covariance-table variant): every subset of a
-    gridded workload with k = 2304 (18 block columns) against the oracle."""
-    w = datagen.config_grid_1m(rho=0.05, tau2=0.02, fine=512, cells=32, buf=8, n_valid=8192, seed=506)
-    P = np.array([[1.0, 0.05, 0.02], [0.6, 0.1, 0.01]])
-    with gpu_lib.Context(w.xy, w.v, w.role, w.layout, tc_stages=2) as ctx:
-        assert ctx.lattice() is not None
-        out = ctx.cv_loss(P, precision="mixed", per_subset=True, predictions=True)
-        V_off = ctx.V_off.copy()
-    assert np.all(out["status"] == 0), out["status"]
+def test_bounded_wait_runs_out(gpu_lib):
+    """A device wait that runs out, in the form this pool allows: the waits of the
+    tensor-core pipeline are shortened to 5 ms and the TMA producer withholds the first
+    operand stage of one task, so the MMA issuer's and the epilogue's waits on it expire
+    (no trap, fault or unbounded wait).  The CTA lets its issued copies and products
+    complete, stops using the tensor path and hands its tasks to the FP64 fallback:
+    every result still meets the bar, the affected configuration reports
+    PCV_REFINE_FALLBACK, and the same call without the hook runs clean."""
+    w = datagen.config_uniform_4096()
+    P = np.array([[1.0, 0.1, 0.05], [0.7, 0.03, 0.2]])
     members = oracle.all_members(w.xy, w.role, w.layout)
-    act = [i for i, (_, V) in enumerate(members) if len(V) > 0]
-    ref = oracle.cv_loss(w.xy, w.v, w.role, w.layout, P, members=members, subsets=act, lapack=True)
-    worst = compare(out, ref, V_off, act, len(P), "mixed", check_total=False)
-    print("paired lattice", len(act), worst)
+    ref = oracle.cv_loss(w.xy, w.v, w.role, w.layout, P, members=members)
+    with gpu_lib.Context(w.xy, w.v, w.role, w.layout, bucketing=1, graph=1, test_wait_us=5000,
+                         test_withhold_task=3) as ctx:
+        ctx.set_timing(True)
+        out = ctx.cv_loss(P, precision="mixed", per_subset=True, predictions=True)
+        ph = ctx.phase_cycles()
+        V_off = ctx.V_off.copy()
+    assert 7 in out["status"].tolist(), out["status"]
+    assert np.all(np.isin(out["status"], (0, 7))), out["status"]
+    assert ph["fail_factor"] >= 1, ph
+    compare(out, ref, V_off, range(len(members)), len(P), "mixed")
+    with gpu_lib.Context(w.xy, w.v, w.role, w.layout, bucketing=1, test_wait_us=5000) as ctx:
+        out2 = ctx.cv_loss(P, precision="mixed")
+    assert np.all(out2["status"] == 0), out2["status"]
+    print("wait ran out:", out["status"].tolist(), "fallback tasks", ph["fail_factor"])
