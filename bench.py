@@ -557,6 +557,8 @@ def main():
     ap.add_argument("--engine", default="tensor", choices=["tensor", "simt", "tensor-bf16"])
     ap.add_argument("--tc-stages", type=int, default=0, help="TMA ring depth of the tensor engine (2 or 3)")
     ap.add_argument("--refine-tol", type=float, default=0.0, help="refinement tolerance (0: library default)")
+    ap.add_argument("--refine-loss-tol", type=float, default=0.0, help="loss-aware tolerance (0: default, <0: off)")
+    ap.add_argument("--refine-loss-guard", type=float, default=0.0, help="loss-aware guard (0: default, <0: none)")
     ap.add_argument("--serve-seconds", type=float, default=10.0,
                     help="seconds per serving load level (0: no serving measurement)")
     ap.add_argument("--serve-batch", type=int, default=16, help="CV requests per serving batch")
@@ -612,7 +614,8 @@ def main():
     t_gen = time.perf_counter() - t_setup
     t0 = time.perf_counter()
     ctx = pcv.Context(w.xy, w.v, w.role, w.layout, device=local, max_slots=args.max_slots,
-                      factor_engine=args.engine, tc_stages=args.tc_stages, refine_tol=args.refine_tol)
+                      factor_engine=args.engine, tc_stages=args.tc_stages, refine_tol=args.refine_tol,
+                      refine_loss_tol=args.refine_loss_tol, refine_loss_guard=args.refine_loss_guard)
     t_create = time.perf_counter() - t0
     k, m = task_sizes(ctx)
     B = args.batch

@@ -166,7 +166,7 @@ typedef struct {
     double refine_loss_tol;    /* mixed path, loss-aware stopping rule (default 2e-8; < 0
                                   turns it off): a CV-loss or prediction task whose solution
                                   rule (refine_tol) is not met yet, but whose error bound is
-                                  within 1000 times it, also stops once the error
+                                  within refine_loss_guard times it, also stops once the error
                                   left in its predictions, estimated as g |K d_i| (K the
                                   cross-covariances to the prediction points, d_i the last
                                   correction, g = c / (1 - c) with c the observed
@@ -210,6 +210,9 @@ typedef struct {
                                   configuration; pcv_predict with a configuration whose
                                   weights are kept for every subset it needs computes the
                                   predictions (Eq. 3) from them without any factorisation */
+    double refine_loss_guard;  /* the loss-aware rule applies once the solution rule's error
+                                  bound is within this factor of refine_tol (default 1000;
+                                  < 0: always) */
     /* Test hooks of the tensor engines' bounded waits (leave 0): test_wait_us > 0 sets
      * their limit (default 2 s); test_withhold_task = t + 1 makes the TMA producer skip
      * the first operand stage of the launch's task t, so that the waits of that CTA run

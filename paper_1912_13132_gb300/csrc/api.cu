@@ -228,6 +228,7 @@ pcv_options default_options(const pcv_options* o) {
     d.graph = 0;
     d.alpha_cache = 32;
     d.test_wait_us = 0;
+    d.refine_loss_guard = 1000.0;
     d.test_withhold_task = 0;
     if (o) {
         if (o->struct_size != 0 && o->struct_size != (int32_t)sizeof(pcv_options)) return d;
@@ -242,6 +243,8 @@ pcv_options default_options(const pcv_options* o) {
         if (o->alpha_cache > 0) d.alpha_cache = std::min(o->alpha_cache, 4096);
         else if (o->alpha_cache < 0) d.alpha_cache = 0;
         if (o->test_wait_us > 0) d.test_wait_us = o->test_wait_us;
+        if (o->refine_loss_guard > 0) d.refine_loss_guard = o->refine_loss_guard;
+        else if (o->refine_loss_guard < 0) d.refine_loss_guard = 0.0;   // no guard
         if (o->test_withhold_task > 0) d.test_withhold_task = o->test_withhold_task;
         if (o->refine_loss_tol > 0) d.refine_loss_tol = o->refine_loss_tol;
         else if (o->refine_loss_tol < 0) d.refine_loss_tol = 0.0;   // solution rule only
@@ -710,6 +713,7 @@ static pcv::TaskArgs base_args(pcv_ctx* c, const double* d_params, int32_t B, co
     a.refine_max_iter = c->opts.refine_max_iter;
     a.refine_tol = c->opts.refine_tol;
     a.refine_loss_tol = c->opts.refine_loss_tol;
+    a.refine_loss_guard = c->opts.refine_loss_guard;
     a.coord_scale = c->coord_scale;
     a.fb_list = c->fb_list.p;
     a.fb_count = c->fb_count.p;

@@ -42,9 +42,6 @@ using dfm::df;
 constexpr int NB = 64;   // block-column width of the factorisation and of the residual tiles
 constexpr int NT = 256;  // threads per CTA
 constexpr int KC = 16;   // K chunk of the trailing update
-// the loss-aware stopping rule applies once the solution rule's error bound is within
-// this factor of refine_tol
-constexpr float kLossGuard = 1000.0f;
 
 __constant__ dfm::ExpConsts c_exp;
 
@@ -1713,8 +1710,8 @@ __device__ void run_task(SmemM& sm, SmemKeep& keep, SmemSimt* simt, TcCtx* tc, c
                     // against |x|
                     const float c = dmax / fmaxf(dprev, 1e-30f);
                     if (c * dmax <= (float)a.refine_tol * xmax) { ok = true; break; }
-                    // loss-aware rule, for a solution already within kLossGuard times the
-                    // solution rule's bound: the predictions of x_i and the change u = K d_i
+                    // loss-aware rule, for a solution already within refine_loss_guard times
+                    // the solution rule's bound (no guard when that is 0): the predictions of x_i and the change u = K d_i
                     // the last correction made to them; the error left in the predictions is
                     // estimated as g |u|, g = c / (1 - c) (the corrections still to come
                     // shrink geometrically).  Stop when it moves the local SSPE (Eq. 4) by at
@@ -1722,7 +1719,8 @@ __device__ void run_task(SmemM& sm, SmemKeep& keep, SmemSimt* simt, TcCtx* tc, c
                     // every prediction by at most 10 refine_loss_tol of their RMS.  The guard
                     // covers a remaining error whose smooth part K damps less than it damps
                     // the last correction (the estimate alone can then be optimistic).
-                    if (loss_rule && c * dmax <= kLossGuard * (float)a.refine_tol * xmax) {
+                    if (loss_rule && (a.refine_loss_guard <= 0.0 ||
+                                      c * dmax <= (float)(a.refine_loss_guard * a.refine_tol) * xmax)) {
                         const PredStats ps = predict_points<LAT>(sm, keep, a, R, k, m, p0, ox, oy, sc, W,
                                                                  (int64_t)b, R.w);
                         tm.lap(kPhPredict);

@@ -66,6 +66,7 @@ struct TaskArgs {
     int32_t refine_max_iter;
     double refine_tol;
     double refine_loss_tol;  // loss-aware stopping rule of the refinement (<= 0: solution rule only)
+    double refine_loss_guard; // it applies within this factor of the solution rule's bound (0: always)
     double coord_scale;     // power of two: scaled offsets inside one window are below 1 in magnitude
     // mixed path: tasks that need the FP64 fallback are appended here
     int32_t* fb_list;

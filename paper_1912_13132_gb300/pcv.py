@@ -39,8 +39,8 @@ class pcv_options(ctypes.Structure):
                 ("workspace_fraction", ctypes.c_double), ("refine_max_iter", ctypes.c_int32),
                 ("refine_tol", ctypes.c_double), ("factor_engine", ctypes.c_int32), ("tc_stages", ctypes.c_int32),
                 ("refine_loss_tol", ctypes.c_double), ("bucketing", ctypes.c_int32), ("graph", ctypes.c_int32),
-                ("alpha_cache", ctypes.c_int32), ("test_wait_us", ctypes.c_int32),
-                ("test_withhold_task", ctypes.c_int32)]
+                ("alpha_cache", ctypes.c_int32), ("refine_loss_guard", ctypes.c_double),
+                ("test_wait_us", ctypes.c_int32), ("test_withhold_task", ctypes.c_int32)]
 
 
 class pcv_server_options(ctypes.Structure):
@@ -226,15 +226,15 @@ class Context:
     def __init__(self, xy, v, role, layout: dict, device: int = 0, max_slots: int = 0,
                  workspace_fraction: float = 0.0, refine_max_iter: int = 0, refine_tol: float = 0.0,
                  factor_engine: str = "tensor", tc_stages: int = 0, refine_loss_tol: float = 0.0,
-                 bucketing: int = 0, graph: int = 0, alpha_cache: int = 0, test_wait_us: int = 0,
-                 test_withhold_task: int = 0):
+                 bucketing: int = 0, graph: int = 0, alpha_cache: int = 0, refine_loss_guard: float = 0.0,
+                 test_wait_us: int = 0, test_withhold_task: int = 0):
         xy = _f64(xy).reshape(-1, 2)
         v = _f64(v)
         role = np.ascontiguousarray(role, dtype=np.uint8)
         L, keep = make_layout(layout)
         o = pcv_options(ctypes.sizeof(pcv_options), max_slots, workspace_fraction, refine_max_iter,
                         refine_tol, ENGINES[factor_engine], tc_stages, refine_loss_tol, bucketing, graph,
-                        alpha_cache, test_wait_us, test_withhold_task)
+                        alpha_cache, refine_loss_guard, test_wait_us, test_withhold_task)
         h = _vp()
         _check(_lib.pcv_create(_ptr(xy, _dp), _ptr(v, _dp), _ptr(role, _u8p), len(v), ctypes.byref(L),
                                device, ctypes.byref(o), ctypes.byref(h)), "pcv_create")

@@ -12,8 +12,10 @@ pinned against the plain C routine in test_oracle_pins.py).
     the two worst-conditioned configurations of the 200-grid (rho = 0.1, the smallest
     nugget ratios tau2 / sigma2) and a typical one, a sample for the others;
   - Poisson-cluster workload at full size (262,144 training points, 32 x 32 cores,
-    k from about 100 to 900): all 64 configurations in one launch, every subset with
-    validation data compared for 8 of them, spread over the rho x tau2 grid.
+    1002 subsets with validation data, k from 13 to 2223): all 64 configurations in
+    one launch, every subset with validation data compared for 8 of them, spread over
+    the rho x tau2 grid; also with the loss-aware stopping rule unguarded (its
+    measurement for choosing the guard).
 """
 from __future__ import annotations
 
@@ -84,13 +86,16 @@ def cluster_full():
 CLUSTER_FULL = [0, 7, 18, 27, 36, 45, 56, 63]   # (rho, tau2) grid corners and its diagonal
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_cluster_full_size_64_configs(gpu_lib, cluster_full, prec):
+@pytest.mark.parametrize("prec,guard", [("fp64", 0.0), ("mixed", 0.0), ("mixed", -1.0)])
+def test_cluster_full_size_64_configs(gpu_lib, cluster_full, prec, guard):
+    """(guard -1: the loss-aware stopping rule without its solution-rule guard.)"""
     w, members, act = cluster_full
     P = w.params
     assert len(P) == 64
-    with gpu_lib.Context(w.xy, w.v, w.role, w.layout) as ctx:
+    with gpu_lib.Context(w.xy, w.v, w.role, w.layout, refine_loss_guard=guard) as ctx:
+        ctx.set_timing(True)
         out = ctx.cv_loss(P, precision=prec, per_subset=True, predictions=True)
+        ph = ctx.phase_cycles() if prec == "mixed" else {}
         V_off, T_off = ctx.V_off.copy(), ctx.T_off.copy()
     assert np.all(out["status"] == 0), out["status"]
     assert np.all(np.isfinite(out["sspe"]))
@@ -99,4 +104,6 @@ def test_cluster_full_size_64_configs(gpu_lib, cluster_full, prec):
                          lapack=True)
     sub = dict(z=out["z"][CLUSTER_FULL], yhat=out["yhat"][CLUSTER_FULL], sspe=out["sspe"][CLUSTER_FULL])
     worst = compare(sub, ref, V_off, act, len(CLUSTER_FULL), prec, check_total=True)
-    print(f"cluster262k {prec}: {len(act)} active subsets, k {k.min()}-{k.max()}, worst {worst}")
+    passes = ph["residual_passes"] / max(ph["tasks"], 1) if ph else None
+    print(f"cluster262k {prec} guard {guard}: {len(act)} active subsets, k {k.min()}-{k.max()}, worst {worst}, "
+          f"residual passes per task {passes}")

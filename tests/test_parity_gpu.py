@@ -236,7 +236,7 @@ def test_grid_precision_stress(gpu_lib, prec, engine, rho, tau2):
     with gpu_lib.Context(w.xy, w.v, w.role, w.layout, factor_engine=engine) as ctx:
         ctx.set_timing(True)
         out = ctx.cv_loss(P, precision=prec, per_subset=True, predictions=True)
-        ph = ctx.phase_cycles() if prec == "mixed" else {}
+        ph = ctx.phase_cycles() if prec.startswith("mixed") else {}
         V_off = ctx.V_off.copy()
     assert out["status"][0] in (0, 7), out["status"]       # 7: some tasks recomputed in FP64
     cores = oracle.layout_cores(w.layout, w.xy)
@@ -311,8 +311,8 @@ def test_paper_recursive_sampled(gpu_lib, paper5m_recursive):
 # FP32-accurate factor, whose relative error grows with the condition number (measured:
 # 2e-6 at condition ~1e3, 5.5e-5 at ~1e5); refinement corrects solutions, not
 # determinants.  The corner case (rho = 0.2, tau2 = 0.001, condition ~1e6) records where
-# that leaves the mixed result; FP64 meets 1e-10 everywhere.
-LIK_MIXED_BAR = {"uniform": 1e-4, "grid-stress": 1e-4, "grid-corner": 2e-3}
+# that leaves the mixed result (measured 9.3e-5); FP64 meets 1e-10 everywhere.
+LIK_MIXED_BAR = {"uniform": 1e-4, "grid-stress": 1e-4, "grid-corner": 5e-4}
 
 
 @pytest.mark.parametrize("prec", PRECS)
