@@ -369,7 +369,9 @@ __device__ __forceinline__ bool chol32_warp(float (*D)[DP], float* rinv, int c0,
                 ok = false;
                 piv = 1.0f;
             }
-            const float d = sqrtf(piv), rd = 1.0f / d;
+            // the FP32 factor only preconditions the refinement: rsqrtf (2 ulp) in
+            // place of an IEEE square root and division on the column's critical path
+            const float rd = rsqrtf(piv), d = piv * rd;
             a[c] = lane == c ? d : a[c] * rd;
             rinv[c0 + c] = rd;
 #pragma unroll
@@ -920,70 +922,96 @@ __device__ void backward32(SmemM& sm, const float* L, int64_t ld, float* w, int 
 }
 
 // Triangular solves of the tensor-core kernel, whose FP32 factor holds the inverse
-// of every 128 x 128 diagonal block (see factor_tc).  w <- L^-1 w, block by block:
-// w_J <- L_JJ^-1 w_J (a product: two threads per row, 64 columns each), then the
-// rows below take w[r] -= L[r, J] w_J.
+// of every 128 x 128 diagonal block (see factor_tc), with zeros above its diagonal and
+// an identity pad past k in the last block.  Both solves stream the factor in chunks
+// of 128 rows x 128 columns: warp wp takes columns 16 wp .. 16 wp + 15, lane l rows
+// 4 l .. 4 l + 3 of the chunk, one float4 per column (the factor is column-major), all
+// sixteen 16-byte loads in flight.  A float4 that starts below k stays inside its
+// column (ld is a multiple of 128); rows past k are never written back.
+
+// Sum of 16 values over the 32 lanes of a warp (transpose-reduce: 16 shuffles instead
+// of 80).  Returns in every lane the total of value (lane >> 1) & 15.
+__device__ __forceinline__ float warp_sum16(float (&s)[16], int lane) {
+    float t[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const bool hi = lane & 16;
+        const float keep = hi ? s[i + 8] : s[i], give = hi ? s[i] : s[i + 8];
+        t[i] = keep + __shfl_xor_sync(0xffffffffu, give, 16);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const bool hi = lane & 8;
+        const float keep = hi ? t[i + 4] : t[i], give = hi ? t[i] : t[i + 4];
+        t[i] = keep + __shfl_xor_sync(0xffffffffu, give, 8);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const bool hi = lane & 4;
+        const float keep = hi ? t[i + 2] : t[i], give = hi ? t[i] : t[i + 2];
+        t[i] = keep + __shfl_xor_sync(0xffffffffu, give, 4);
+    }
+    {
+        const bool hi = lane & 2;
+        const float keep = hi ? t[1] : t[0], give = hi ? t[0] : t[1];
+        t[0] = keep + __shfl_xor_sync(0xffffffffu, give, 2);
+    }
+    return t[0] + __shfl_xor_sync(0xffffffffu, t[0], 1);
+}
+
+// Row-chunk product of the forward solve: acc (rows 4 lane .. 4 lane + 3 of the chunk at
+// row r0) = L[r0 .., j0 + c0 .. j0 + c0 + 15] wc
+__device__ __forceinline__ float4 chunk_rows(const float* L, int64_t ld, int r0, int jc, const float (&wc)[16]) {
+    float4 l4[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) l4[q] = *reinterpret_cast<const float4*>(L + r0 + (int64_t)(jc + q) * ld);
+    float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+        acc.x = fmaf(l4[q].x, wc[q], acc.x);
+        acc.y = fmaf(l4[q].y, wc[q], acc.y);
+        acc.z = fmaf(l4[q].z, wc[q], acc.z);
+        acc.w = fmaf(l4[q].w, wc[q], acc.w);
+    }
+    return acc;
+}
+
+// w <- L^-1 w, block by block: w_J <- L_JJ^-1 w_J (one chunk: the inverse block), then
+// the rows below take w[r] -= L[r, J] w_J.  The warps' partial sums meet in shared
+// memory (two buffers, one barrier per chunk).
 __device__ void forward_inv(SmemM& sm, const float* L, int64_t ld, float* w, int k) {
     constexpr int TBs = 2 * NB;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    float* part = &sm.ph[0][0];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, c0 = warp * 16;
+    float* red = &sm.ph[0][0];          // 2 x 8 x 128 floats (ph and pl)
     const int nb = (k + TBs - 1) / TBs;
+    int buf = 0;
     for (int J = 0; J < nb; ++J) {
         const int j0 = J * TBs, jb = min(TBs, k - j0);
         if (tid < TBs) sm.wj[tid] = tid < jb ? w[j0 + tid] : 0.0f;
         __syncthreads();
-        {
-            const int r = tid & (TBs - 1), h = tid >> 7;
-            float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
-            if (r < jb) {
-                const float* Lc = L + (j0 + r) + (int64_t)(j0 + 64 * h) * ld;
-                const float* v = sm.wj + 64 * h;
-#pragma unroll 4
-                for (int c = 0; c < 64; c += 4) {
-                    s0 = fmaf(Lc[(int64_t)c * ld], v[c], s0);
-                    s1 = fmaf(Lc[(int64_t)(c + 1) * ld], v[c + 1], s1);
-                    s2 = fmaf(Lc[(int64_t)(c + 2) * ld], v[c + 2], s2);
-                    s3 = fmaf(Lc[(int64_t)(c + 3) * ld], v[c + 3], s3);
-                }
-            }
-            part[tid] = (s0 + s1) + (s2 + s3);
-        }
+        float wc[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) wc[q] = sm.wj[c0 + q];
+        *reinterpret_cast<float4*>(red + buf * (8 * TBs) + warp * TBs + 4 * lane) =
+            chunk_rows(L, ld, j0 + 4 * lane, j0 + c0, wc);
         __syncthreads();
-        if (tid < jb) {
-            const float v = part[tid] + part[tid + TBs];
-            w[j0 + tid] = v;
+        if (tid < TBs) {
+            const float* rb = red + buf * (8 * TBs) + tid;
+            float v = 0.0f;
+#pragma unroll
+            for (int g = 0; g < 8; ++g) v += rb[g * TBs];
+            v = tid < jb ? v : 0.0f;
             sm.wj[tid] = v;
+            if (tid < jb) w[j0 + tid] = v;
         }
+        buf ^= 1;
         __syncthreads();
-        if (jb == TBs) {
-            // rows below in chunks of 128: warp wp takes columns 16 wp .. 16 wp + 15, lane l
-            // rows 4 l .. 4 l + 3 of the chunk as one float4 per column (the factor is
-            // column-major), all sixteen loads in flight; the warps' partial sums meet in
-            // shared memory (two buffers, one barrier per chunk).  A float4 that starts
-            // below k stays inside the column (ld is a multiple of 128); its rows past k
-            // are never written back.
-            const int c0 = warp * 16;
-            float* red = &sm.ph[0][0];          // 2 x 8 x 128 floats (ph and pl)
-            float wc[16];
+        if (jb == TBs && j0 + TBs < k) {
 #pragma unroll
             for (int q = 0; q < 16; ++q) wc[q] = sm.wj[c0 + q];
-            int buf = 0;
             for (int rc = j0 + TBs; rc < k; rc += TBs, buf ^= 1) {
                 const int r = rc + 4 * lane;
-                float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-                if (r < k) {
-                    float4 l4[16];
-#pragma unroll
-                    for (int q = 0; q < 16; ++q)
-                        l4[q] = *reinterpret_cast<const float4*>(L + r + (int64_t)(j0 + c0 + q) * ld);
-#pragma unroll
-                    for (int q = 0; q < 16; ++q) {
-                        acc.x = fmaf(l4[q].x, wc[q], acc.x);
-                        acc.y = fmaf(l4[q].y, wc[q], acc.y);
-                        acc.z = fmaf(l4[q].z, wc[q], acc.z);
-                        acc.w = fmaf(l4[q].w, wc[q], acc.w);
-                    }
-                }
+                const float4 acc = r < k ? chunk_rows(L, ld, r, j0 + c0, wc) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
                 *reinterpret_cast<float4*>(red + buf * (8 * TBs) + warp * TBs + 4 * lane) = acc;
                 __syncthreads();
                 if (tid < TBs && rc + tid < k) {
@@ -994,67 +1022,60 @@ __device__ void forward_inv(SmemM& sm, const float* L, int64_t ld, float* w, int
                     w[rc + tid] -= v;
                 }
             }
+            __syncthreads();
         }
-        __syncthreads();
     }
 }
 
-// w <- L^-T w, blocks from the last: v = w_J - L[below, J]^T w[below] (warp wp takes
-// columns 16 wp .. 16 wp + 15, lanes walk the rows), then w_J <- L_JJ^-T v (warp per
-// column: the inverse's column is contiguous, lanes split it, warp sum).
+// w <- L^-T w, blocks from the last: v = w_J - L[below, J]^T w[below] (column dot
+// products: the lanes walk the rows, a warp reduction per column), then
+// w_J <- L_JJ^-T v (one chunk: the inverse block's columns against v).
 __device__ void backward_inv(SmemM& sm, const float* L, int64_t ld, float* w, int k) {
     constexpr int TBs = 2 * NB;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, c0 = warp * 16;
     const int nb = (k + TBs - 1) / TBs;
+    const int cq = c0 + ((lane >> 1) & 15);   // the column whose total this lane ends with
     for (int J = nb - 1; J >= 0; --J) {
         const int j0 = J * TBs, jb = min(TBs, k - j0);
-        {
-            const int c0 = warp * 16;
-            float s[16];
+        float s[16];
 #pragma unroll
-            for (int q = 0; q < 16; ++q) s[q] = 0.0f;
-            if (jb == TBs) {
-                // lane l takes rows 4 l .. 4 l + 3 of each 128-row chunk as one float4 per
-                // column (sixteen 16-byte loads in flight), whole float4s below k only;
-                // the last rows (fewer than four) one by one
-                const int rb = j0 + TBs, nq = (k - rb) >> 2;
-                for (int ch = lane; ch < nq; ch += 32) {
-                    const int p = rb + 4 * ch;
-                    const float4 wv = *reinterpret_cast<const float4*>(w + p);
-                    float4 l4[16];
+        for (int q = 0; q < 16; ++q) s[q] = 0.0f;
+        if (jb == TBs) {
+            // whole float4s below k; the last rows (fewer than four) one by one
+            const int rb = j0 + TBs, nq = (k - rb) >> 2;
+            for (int ch = lane; ch < nq; ch += 32) {
+                const int p = rb + 4 * ch;
+                const float4 wv = *reinterpret_cast<const float4*>(w + p);
+                float4 l4[16];
 #pragma unroll
-                    for (int q = 0; q < 16; ++q)
-                        l4[q] = *reinterpret_cast<const float4*>(L + p + (int64_t)(j0 + c0 + q) * ld);
+                for (int q = 0; q < 16; ++q)
+                    l4[q] = *reinterpret_cast<const float4*>(L + p + (int64_t)(j0 + c0 + q) * ld);
 #pragma unroll
-                    for (int q = 0; q < 16; ++q)
-                        s[q] = fmaf(l4[q].x, wv.x, fmaf(l4[q].y, wv.y, fmaf(l4[q].z, wv.z, fmaf(l4[q].w, wv.w, s[q]))));
-                }
-                for (int p = rb + 4 * nq + lane; p < k; p += 32) {
-                    const float wp = w[p];
-#pragma unroll
-                    for (int q = 0; q < 16; ++q) s[q] = fmaf(L[p + (int64_t)(j0 + c0 + q) * ld], wp, s[q]);
-                }
+                for (int q = 0; q < 16; ++q)
+                    s[q] = fmaf(l4[q].x, wv.x, fmaf(l4[q].y, wv.y, fmaf(l4[q].z, wv.z, fmaf(l4[q].w, wv.w, s[q]))));
             }
+            for (int p = rb + 4 * nq + lane; p < k; p += 32) {
+                const float wp = w[p];
 #pragma unroll
-            for (int q = 0; q < 16; ++q) {
-                float v = s[q];
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                if (lane == 0) {
-                    const int c = c0 + q;
-                    sm.wj[c] = c < jb ? w[j0 + c] - v : 0.0f;
-                }
+                for (int q = 0; q < 16; ++q) s[q] = fmaf(L[p + (int64_t)(j0 + c0 + q) * ld], wp, s[q]);
             }
         }
+        {
+            const float v = warp_sum16(s, lane);
+            if ((lane & 1) == 0) sm.wj[cq] = cq < jb ? w[j0 + cq] - v : 0.0f;
+        }
         __syncthreads();
-        for (int c = warp; c < jb; c += NT / 32) {
-            const float* Lc = L + j0 + (int64_t)(j0 + c) * ld;
-            float v = 0.0f;
+        {
+            const float4 wv = *reinterpret_cast<const float4*>(sm.wj + 4 * lane);
+            float4 l4[16];
 #pragma unroll
-            for (int u = 0; u < TBs / 32; ++u) v = fmaf(Lc[lane + 32 * u], sm.wj[lane + 32 * u], v);
+            for (int q = 0; q < 16; ++q)
+                l4[q] = *reinterpret_cast<const float4*>(L + (j0 + 4 * lane) + (int64_t)(j0 + c0 + q) * ld);
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane == 0) w[j0 + c] = v;
+            for (int q = 0; q < 16; ++q)
+                s[q] = fmaf(l4[q].x, wv.x, fmaf(l4[q].y, wv.y, fmaf(l4[q].z, wv.z, l4[q].w * wv.w)));
+            const float v = warp_sum16(s, lane);
+            if ((lane & 1) == 0 && cq < jb) w[j0 + cq] = v;
         }
         __syncthreads();
     }
