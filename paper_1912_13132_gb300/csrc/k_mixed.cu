@@ -769,7 +769,7 @@ __device__ bool factor_tc(TcCtx& tc, const SlotM& S, int k, int64_t ld, unsigned
 #pragma unroll
                         for (int j = 0; j < 32; ++j) {
                             v[j] *= up;
-                            Lr[(int64_t)j * ld] = v[j];
+                            __stcs(Lr + (int64_t)j * ld, v[j]);   // read next by the solves: streaming
                         }
                         if (fw) {
 #pragma unroll
@@ -927,7 +927,8 @@ __device__ void backward32(SmemM& sm, const float* L, int64_t ld, float* w, int 
 // of 128 rows x 128 columns: warp wp takes columns 16 wp .. 16 wp + 15, lane l rows
 // 4 l .. 4 l + 3 of the chunk, one float4 per column (the factor is column-major), all
 // sixteen 16-byte loads in flight.  A float4 that starts below k stays inside its
-// column (ld is a multiple of 128); rows past k are never written back.
+// column (ld is a multiple of 128); rows past k are never written back.  The factor
+// is read with streaming (evict-first) loads: one pass per solve, nothing to keep in L2.
 
 // Sum of 16 values over the 32 lanes of a warp (transpose-reduce: 16 shuffles instead
 // of 80).  Returns in every lane the total of value (lane >> 1) & 15.
@@ -964,7 +965,7 @@ __device__ __forceinline__ float warp_sum16(float (&s)[16], int lane) {
 __device__ __forceinline__ float4 chunk_rows(const float* L, int64_t ld, int r0, int jc, const float (&wc)[16]) {
     float4 l4[16];
 #pragma unroll
-    for (int q = 0; q < 16; ++q) l4[q] = *reinterpret_cast<const float4*>(L + r0 + (int64_t)(jc + q) * ld);
+    for (int q = 0; q < 16; ++q) l4[q] = __ldcs(reinterpret_cast<const float4*>(L + r0 + (int64_t)(jc + q) * ld));
     float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
@@ -1049,7 +1050,7 @@ __device__ void backward_inv(SmemM& sm, const float* L, int64_t ld, float* w, in
                 float4 l4[16];
 #pragma unroll
                 for (int q = 0; q < 16; ++q)
-                    l4[q] = *reinterpret_cast<const float4*>(L + p + (int64_t)(j0 + c0 + q) * ld);
+                    l4[q] = __ldcs(reinterpret_cast<const float4*>(L + p + (int64_t)(j0 + c0 + q) * ld));
 #pragma unroll
                 for (int q = 0; q < 16; ++q)
                     s[q] = fmaf(l4[q].x, wv.x, fmaf(l4[q].y, wv.y, fmaf(l4[q].z, wv.z, fmaf(l4[q].w, wv.w, s[q]))));
@@ -1070,7 +1071,7 @@ __device__ void backward_inv(SmemM& sm, const float* L, int64_t ld, float* w, in
             float4 l4[16];
 #pragma unroll
             for (int q = 0; q < 16; ++q)
-                l4[q] = *reinterpret_cast<const float4*>(L + (j0 + 4 * lane) + (int64_t)(j0 + c0 + q) * ld);
+                l4[q] = __ldcs(reinterpret_cast<const float4*>(L + (j0 + 4 * lane) + (int64_t)(j0 + c0 + q) * ld));
 #pragma unroll
             for (int q = 0; q < 16; ++q)
                 s[q] = fmaf(l4[q].x, wv.x, fmaf(l4[q].y, wv.y, fmaf(l4[q].z, wv.z, l4[q].w * wv.w)));

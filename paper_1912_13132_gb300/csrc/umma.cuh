@@ -150,6 +150,21 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
         "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
         : "memory");
 }
+// the same with an L2 cache policy (createpolicy) for the loaded lines
+__device__ __forceinline__ void tma_load_3d_hint(void* dst, const CUtensorMap* map, int c0, int c1, int c2,
+                                                 uint64_t* bar, uint64_t policy) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+        " [%0], [%1, {%2, %3, %4}], [%5], %6;" ::"r"(smem_u32(dst)),
+        "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar)), "l"(policy)
+        : "memory");
+}
+// L2 policy: lines are the first candidates for eviction (data read once)
+__device__ __forceinline__ uint64_t policy_evict_first() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
 __device__ __forceinline__ void prefetch_map(const CUtensorMap* map) {
     asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)map) : "memory");
 }
@@ -340,6 +355,12 @@ __device__ __forceinline__ void load_box(void* dst, const CUtensorMap* map, int 
     if constexpr (TILED) tma_load_3d(dst, map, 0, 0, (row / kTileM) * nkc + kc, bar);
     else tma_load_2d(dst, map, kc * kChunkK, row, bar);
 }
+template <bool TILED>
+__device__ __forceinline__ void load_box_stream(void* dst, const CUtensorMap* map, int kc, int row, int nkc,
+                                                uint64_t* bar, uint64_t policy) {
+    if constexpr (TILED) tma_load_3d_hint(dst, map, 0, 0, (row / kTileM) * nkc + kc, bar, policy);
+    else tma_load_2d(dst, map, kc * kChunkK, row, bar);
+}
 
 template <bool TILED = false, int TPP = kTilesPerPass, class Sch = SplitBF16x3, int BN = kTileN, int NBUF = 2,
           class Epi>
@@ -360,9 +381,15 @@ __device__ bool block_column(Pipe& P, Phases& ph, uint8_t* stages, const CUtenso
         int32_t issued[kStages];   // last iteration whose loads went to each ring slot
 #pragma unroll
         for (int q = 0; q < kStages; ++q) issued[q] = -1;
+        const uint64_t stream = policy_evict_first();
         for (int p = 0; p < npass && ok; ++p) {
             const int t0 = p * TPP;
             const int nt = min(TPP, ntiles - t0);
+            // K chunks in ascending order for every tile.  In the left-looking update the first
+            // chunks (columns far from the rows updated) carry the smallest terms; reversing the
+            // order on alternate tiles, to reuse the B chunks while they are in L2, tripled the
+            // refinement passes of the paper-scale workload (1.43 -> 4.4 per task): the
+            // accumulation in TMEM is order-sensitive, and small terms go in first.
             for (int kc = 0; kc < nk; ++kc, ++it) {
                 const int s = it % P.nstages;
                 const uint32_t par = ((it / P.nstages) & 1) ^ 1;
@@ -378,9 +405,10 @@ __device__ bool block_column(Pipe& P, Phases& ph, uint8_t* stages, const CUtenso
                     for (int h = 0; h < BB; ++h)
                         load_box<TILED>(st + (pl * BB + h) * kTileBytes, maps[pl], kc0 + kc,
                                         row_base + b0 + h * kTileM, nkc, &P.full[s]);
-                    for (int t = 0; t < nt; ++t)
-                        load_box<TILED>(st + (Sch::kPlanes * BB + t * Sch::kPlanes + pl) * kTileBytes, maps[pl],
-                                        kc0 + kc, row_base + r0 + (t0 + t) * kTileM, nkc, &P.full[s]);
+                    for (int t = 0; t < nt; ++t)   // A: read once per block column
+                        load_box_stream<TILED>(st + (Sch::kPlanes * BB + t * Sch::kPlanes + pl) * kTileBytes,
+                                               maps[pl], kc0 + kc, row_base + r0 + (t0 + t) * kTileM, nkc,
+                                               &P.full[s], stream);
                 }
             }
         }
