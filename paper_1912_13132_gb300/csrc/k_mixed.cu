@@ -134,6 +134,7 @@ struct alignas(16) SmemSimt {
 struct alignas(8) SmemKeep {
     float tbl[2 * dfm::kExpTable]; // exp table (copy of c_exp.tbl)
     float fwj[2 * NB];             // w_J of the forward solve fused into the factorisation
+    int2 lij[2 * NB];              // lattice indices of the block column's points (update epilogue)
     int task;
 };
 
@@ -560,7 +561,8 @@ constexpr int kDiagBytes = kDiagRedOff + (NT / 32) * 4;
 // of earlier block columns have already subtracted their part), and the panel's
 // epilogue, which holds each row of L[below, J], subtracts L[r, J] w_J from w_r.  The
 // factor is then not streamed for that solve.  fwj: 128 floats of shared memory
-// outside the operand ring.
+// outside the operand ring; lij (lattice data): 128 index pairs of shared memory, the
+// block column's points for the update epilogue.
 struct LatView {
     const float2* tab;   // covariance table (hi, lo) by index offset, rows of length W
     const int* ti;       // lattice indices of the training points
@@ -573,7 +575,7 @@ struct LatView {
 
 template <class Sch, bool LAT = false>
 __device__ bool factor_tc(TcCtx& tc, const SlotM& S, int k, int64_t ld, unsigned long long* clk,
-                          float* fw = nullptr, float* fwj = nullptr, LatView lv = LatView{}) {
+                          float* fw = nullptr, float* fwj = nullptr, LatView lv = LatView{}, int2* lij = nullptr) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     PhaseTimer tm(clk);
     // the operand ring was written through the generic proxy since the last update
@@ -599,15 +601,26 @@ __device__ bool factor_tc(TcCtx& tc, const SlotM& S, int k, int64_t ld, unsigned
                     if (r < k) {
                         float* Lr = L + r + (int64_t)(j0 + c0) * ld;
                         if (diag_rows) {
+                            // all 32 loads before the stores (the compiler cannot tell that the
+                            // strided stores miss the later loads, and would otherwise wait
+                            // for one memory round trip per column)
+                            float cur[32];
+#pragma unroll
+                            for (int j = 0; j < 32; ++j) cur[j] = c0 + j < jb ? Lr[(int64_t)j * ld] : 0.0f;
 #pragma unroll
                             for (int j = 0; j < 32; ++j)
-                                if (c0 + j < jb) Lr[(int64_t)j * ld] -= v[j];
+                                if (c0 + j < jb) Lr[(int64_t)j * ld] = cur[j] - v[j];
                         } else {
                             if constexpr (LAT) {
+                                // the columns' lattice indices from shared memory: one memory
+                                // round trip (the table) per group instead of two
                                 const int ri = lv.ti[r], rj = lv.tj[r];
                                 float av[32];
 #pragma unroll
-                                for (int j = 0; j < 32; ++j) av[j] = lv.a(ri, rj, j0 + c0 + j);
+                                for (int j = 0; j < 32; ++j) {
+                                    const int2 c = lij[c0 + j];
+                                    av[j] = lv.tab[abs(ri - c.x) * lv.W + abs(rj - c.y)].x;
+                                }
 #pragma unroll
                                 for (int j = 0; j < 32; ++j) v[j] = av[j] - v[j];
                             } else {
@@ -621,6 +634,13 @@ __device__ bool factor_tc(TcCtx& tc, const SlotM& S, int k, int64_t ld, unsigned
                     }
                 }
             };
+            if constexpr (LAT) {
+                if (tid < TB) {
+                    const int c = min(j0 + tid, k - 1);
+                    lij[tid] = make_int2(lv.ti[c], lv.tj[c]);
+                }
+                __syncthreads();
+            }
             const bool ok = tc.sh->dead == 0 &&
                             umma::block_column<true, kTcTilesPerPass, Sch>(tc.sh->pipe, tc.ph, tc.stages, tc.m0, tc.m1, tc.m2,
                                                      tc.row_base, j0, k - j0, j0, j0 * kw<Sch>(), epi,
@@ -1590,7 +1610,7 @@ __device__ void run_task(SmemM& sm, SmemKeep& keep, SmemSimt* simt, TcCtx* tc, c
             LatView lv{};
             if constexpr (LAT)
                 lv = LatView{S.tab, reinterpret_cast<const int*>(S.xh), reinterpret_cast<const int*>(S.yh), W};
-            ok = factor_tc<Sch, LAT>(*tc, S, k, ld, a.phase_cycles, fuse_fw ? S.w : nullptr, keep.fwj, lv);
+            ok = factor_tc<Sch, LAT>(*tc, S, k, ld, a.phase_cycles, fuse_fw ? S.w : nullptr, keep.fwj, lv, keep.lij);
         }
         else ok = factor32(sm, *simt, S, k, ld);
     }
