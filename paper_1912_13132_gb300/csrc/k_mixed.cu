@@ -950,6 +950,13 @@ __device__ void backward32(SmemM& sm, const float* L, int64_t ld, float* w, int 
 // column (ld is a multiple of 128); rows past k are never written back.  The factor
 // is read with streaming (evict-first) loads: one pass per solve, nothing to keep in L2.
 
+// L2 prefetch of 128 rows (512 bytes) of a factor column from p (16-byte aligned: the row
+// is a multiple of 128, as is ld), a hint that keeps the next chunks' HBM reads in flight
+// without registers; callers stay below k, hence inside the column
+__device__ __forceinline__ void l2_prefetch_rows(const float* p) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], 512;" ::"l"(p) : "memory");
+}
+
 // Sum of 16 values over the 32 lanes of a warp (transpose-reduce: 16 shuffles instead
 // of 80).  Returns in every lane the total of value (lane >> 1) & 15.
 __device__ __forceinline__ float warp_sum16(float (&s)[16], int lane) {
@@ -1008,6 +1015,13 @@ __device__ void forward_inv(SmemM& sm, const float* L, int64_t ld, float* w, int
     int buf = 0;
     for (int J = 0; J < nb; ++J) {
         const int j0 = J * TBs, jb = min(TBs, k - j0);
+        // this block's first two chunks below and the next block's inverse, into L2
+        if (tid < TBs && j0 + TBs < k) {
+            const float* col = L + (int64_t)(j0 + tid) * ld;
+            l2_prefetch_rows(col + j0 + TBs);
+            if (j0 + 2 * TBs < k) l2_prefetch_rows(col + j0 + 2 * TBs);
+            l2_prefetch_rows(L + (j0 + TBs) + (int64_t)(j0 + TBs + tid) * ld);
+        }
         if (tid < TBs) sm.wj[tid] = tid < jb ? w[j0 + tid] : 0.0f;
         __syncthreads();
         float wc[16];
@@ -1031,6 +1045,7 @@ __device__ void forward_inv(SmemM& sm, const float* L, int64_t ld, float* w, int
 #pragma unroll
             for (int q = 0; q < 16; ++q) wc[q] = sm.wj[c0 + q];
             for (int rc = j0 + TBs; rc < k; rc += TBs, buf ^= 1) {
+                if (tid < TBs && rc + 2 * TBs < k) l2_prefetch_rows(L + (rc + 2 * TBs) + (int64_t)(j0 + tid) * ld);
                 const int r = rc + 4 * lane;
                 const float4 acc = r < k ? chunk_rows(L, ld, r, j0 + c0, wc) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
                 *reinterpret_cast<float4*>(red + buf * (8 * TBs) + warp * TBs + 4 * lane) = acc;
@@ -1061,11 +1076,21 @@ __device__ void backward_inv(SmemM& sm, const float* L, int64_t ld, float* w, in
         float s[16];
 #pragma unroll
         for (int q = 0; q < 16; ++q) s[q] = 0.0f;
+        // the next block's inverse into L2 (read after this block's rows below)
+        if (J > 0 && tid < TBs) l2_prefetch_rows(L + (j0 - TBs) + (int64_t)(j0 - TBs + tid) * ld);
         if (jb == TBs) {
-            // whole float4s below k; the last rows (fewer than four) one by one
+            // whole float4s below k; the last rows (fewer than four) one by one.  Lanes 0-15
+            // keep the warp's columns two chunks ahead in L2.
             const int rb = j0 + TBs, nq = (k - rb) >> 2;
+            const float* pcol = L + (int64_t)(j0 + c0 + (lane & 15)) * ld;
+            if (lane < 16 && rb < k) {
+                l2_prefetch_rows(pcol + rb);
+                if (rb + TBs < k) l2_prefetch_rows(pcol + rb + TBs);
+            }
             for (int ch = lane; ch < nq; ch += 32) {
                 const int p = rb + 4 * ch;
+                const int pf = rb + 4 * (ch - lane) + 2 * TBs;   // the warp's chunk two ahead
+                if (lane < 16 && pf < k) l2_prefetch_rows(pcol + pf);
                 const float4 wv = *reinterpret_cast<const float4*>(w + p);
                 float4 l4[16];
 #pragma unroll
