@@ -99,8 +99,8 @@ def test_alone_equals_mixed(gpu_lib, budget):
 @pytest.mark.parametrize("lanes", [2, 1])
 def test_arrival_during_a_running_batch(gpu_lib, lanes):
     """A CV request that arrives while a long batch of the same dataset runs: with two
-    lanes it is admitted at once and completes before the batch (its launch takes the
-    SMs the running launch leaves free); with one lane it waits for the batch.  Its
+    (warm) lanes it is admitted at once and completes before the batch (its launch takes
+    the SMs the running launch leaves free); with one lane it waits for the batch.  Its
     loss equals the solo evaluation bit for bit either way."""
     w = datagen.config_grid_1m(rho=0.05, tau2=0.02, fine=512, cells=32, buf=8, n_valid=8192, seed=505)
     big = [(1.0, 0.05 * (1.0 + 0.02 * q), 0.02) for q in range(16)]
@@ -111,7 +111,15 @@ def test_arrival_during_a_running_batch(gpu_lib, lanes):
     ctx = gpu_lib.Context(w.xy, w.v, w.role, w.layout, max_slots=24)
     ctx.cv_loss(big[:1])
     with gpu_lib.Server([ctx], max_batch=16, precision="mixed", lanes=lanes) as srv:
-        srv.wait(srv.submit_cv(0, big[0]))
+        # every lane runs once first: a lane's first call allocates its work memory, and
+        # the CUDA runtime orders a device allocation after the kernels already running
+        # in other streams (the second request is queued while the first lane is busy,
+        # so the other lane takes it)
+        first = srv.submit_cv(0, big[0])
+        time.sleep(0.005)
+        second = srv.submit_cv(0, late)
+        srv.wait(first)
+        srv.wait(second)
         t0 = time.perf_counter()
         ids = [srv.submit_cv(0, p) for p in big]
         time.sleep(0.05)
