@@ -388,6 +388,8 @@ bool lattice_axis(const std::vector<double>& v, double& v0, double& h, std::vect
 
 // ----------------------------------------------------------------- helpers for the server
 
+static pcv_status ensure_buckets(pcv_ctx* c, const double* d_params, int32_t B, cudaStream_t s);
+
 namespace pcv {
 
 int64_t ctx_workspace_estimate(pcv_ctx* c, int32_t prec) {
@@ -402,6 +404,43 @@ int64_t ctx_workspace_estimate(pcv_ctx* c, int32_t prec) {
         total += g * (sb + pb);
     }
     return total;
+}
+
+// Everything a CV call of up to Bmax configurations in precision prec allocates (work
+// memory, per-call buffers and, for PCV_PREC_MIXED, the size buckets with theirs),
+// allocated now, so that such a call allocates nothing: a device allocation is ordered
+// after the kernels already running in other streams, and a serving lane whose first
+// call allocated would wait for the other lanes' launches.  The buckets are built here
+// when the process holds the autotuner's choice for this context's subset sizes;
+// otherwise the first call builds them (tuning needs its parameters).
+pcv_status ctx_reserve(pcv_ctx* c, int32_t prec, int32_t Bmax) {
+    if (!c || bad_precision(prec) || Bmax < 1) return PCV_ERR_ARG;
+    CUDA_TRY(cudaSetDevice(c->device));
+    const int32_t N = c->plan.N;
+    CUDA_TRY(c->params.reserve((size_t)3 * Bmax));
+    CUDA_TRY(c->sspe.reserve(Bmax));
+    CUDA_TRY(c->status.reserve(Bmax));
+    CUDA_TRY(c->alpha_slot.reserve(Bmax));
+    CUDA_TRY(c->z.reserve((size_t)Bmax * N));
+    CUDA_TRY(c->tst.reserve((size_t)Bmax * N));
+    if (c->n_active == 0) return PCV_OK;
+    if (is_mixed(prec)) {
+        const int e = pcv::mixed_prepare(c->device);
+        if (e) return cuda_fail((cudaError_t)e, "mixed-path set-up");
+    }
+    if (prec == PCV_PREC_MIXED) {
+        if (ensure_buckets(c, nullptr, Bmax, nullptr) != PCV_OK) cudaGetLastError();   // the first call builds them
+    } else {
+        const pcv_status st = ensure_workspace(c, ws_of(c, prec));
+        if (st != PCV_OK) return st;
+    }
+    if (is_mixed(prec)) {
+        const pcv_status st = ensure_workspace(c, kFallbackWs);
+        if (st != PCV_OK) return st;
+        CUDA_TRY(c->fb_list.reserve((size_t)c->n_active * Bmax));
+        CUDA_TRY(c->fb_count.reserve(2));
+    }
+    return PCV_OK;
 }
 
 int64_t ctx_workspace_resident(pcv_ctx* c) {
@@ -896,6 +935,7 @@ static pcv_status build_buckets(pcv_ctx* c, const double* d_params, int32_t B, c
                 cached = true;
             }
         }
+        if (!cached && !d_params) return PCV_ERR_ARG;   // tuning needs the call's parameters
         if (!cached) {
             // the first valid parameter row of the call, repeated to fill the device
             std::vector<double> hp((size_t)3 * B);

@@ -144,6 +144,7 @@ void count_launch(int n = 1);
 int64_t ctx_workspace_estimate(pcv_ctx* c, int32_t prec);   // bytes still to allocate for `prec`
 int64_t ctx_workspace_resident(pcv_ctx* c);                  // bytes held now
 void ctx_release_workspace(pcv_ctx* c);                      // free all (context must be idle)
+pcv_status ctx_reserve(pcv_ctx* c, int32_t prec, int32_t Bmax); // allocate what CV calls of <= Bmax need
 int ctx_device(const pcv_ctx* c);
 pcv_ctx* ctx_clone(const pcv_ctx* c);                        // a serving lane over the same data
 void ctx_free(pcv_ctx* c);

@@ -288,6 +288,15 @@ PCV_API pcv_status pcv_server_create(pcv_ctx* const* ctxs, int32_t n_ctx, const 
             L->owned = l > 0;
             L->last_used = Clock::now();
             const bool ok = L->ctx && cudaStreamCreateWithPriority(&L->stream, cudaStreamNonBlocking, prio) == cudaSuccess;
+            if (ok) {
+                // the lane's work memory now, budget permitting: a lane whose first batch
+                // allocated it would wait for the launches already running on the device
+                const int64_t need = pcv::ctx_workspace_estimate(L->ctx, s->precision);
+                if (s->budget <= 0.0 ||
+                    (double)(s->used + pcv::ctx_workspace_resident(L->ctx) + need) <= s->budget)
+                    if (pcv::ctx_reserve(L->ctx, s->precision, s->max_batch) != PCV_OK)
+                        cudaGetLastError();   // the lane allocates at its first batch instead
+            }
             if (L->ctx) {
                 L->resident = pcv::ctx_workspace_resident(L->ctx);
                 s->used += L->resident;

@@ -96,12 +96,15 @@ def test_alone_equals_mixed(gpu_lib, budget):
         assert st["evictions"] > 0
 
 
-@pytest.mark.parametrize("lanes", [2, 1])
-def test_arrival_during_a_running_batch(gpu_lib, lanes):
+@pytest.mark.parametrize("lanes,warm", [(2, True), (2, False), (1, True)])
+def test_arrival_during_a_running_batch(gpu_lib, lanes, warm):
     """A CV request that arrives while a long batch of the same dataset runs: with two
-    (warm) lanes it is admitted at once and completes before the batch (its launch takes
-    the SMs the running launch leaves free); with one lane it waits for the batch.  Its
-    loss equals the solo evaluation bit for bit either way."""
+    lanes it is admitted at once and completes before the batch (its launch takes the
+    SMs the running launch leaves free); with one lane it waits for the batch.  Its
+    loss equals the solo evaluation bit for bit either way.  Cold (warm=False): no
+    request has run on the server before, so the late request is its lane's first call,
+    which must find its work memory reserved at server creation (an allocation then
+    would wait for the running launch)."""
     w = datagen.config_grid_1m(rho=0.05, tau2=0.02, fine=512, cells=32, buf=8, n_valid=8192, seed=505)
     big = [(1.0, 0.05 * (1.0 + 0.02 * q), 0.02) for q in range(16)]
     late = (1.2, 0.07, 0.03)
@@ -111,15 +114,14 @@ def test_arrival_during_a_running_batch(gpu_lib, lanes):
     ctx = gpu_lib.Context(w.xy, w.v, w.role, w.layout, max_slots=24)
     ctx.cv_loss(big[:1])
     with gpu_lib.Server([ctx], max_batch=16, precision="mixed", lanes=lanes) as srv:
-        # every lane runs once first: a lane's first call allocates its work memory, and
-        # the CUDA runtime orders a device allocation after the kernels already running
-        # in other streams (the second request is queued while the first lane is busy,
-        # so the other lane takes it)
-        first = srv.submit_cv(0, big[0])
-        time.sleep(0.005)
-        second = srv.submit_cv(0, late)
-        srv.wait(first)
-        srv.wait(second)
+        # warm: every lane runs once first (the second request is queued while the first
+        # lane is busy, so the other lane takes it)
+        if warm:
+            first = srv.submit_cv(0, big[0])
+            time.sleep(0.005)
+            second = srv.submit_cv(0, big[1])
+            srv.wait(first)
+            srv.wait(second)
         t0 = time.perf_counter()
         ids = [srv.submit_cv(0, p) for p in big]
         time.sleep(0.05)
@@ -135,4 +137,4 @@ def test_arrival_during_a_running_batch(gpu_lib, lanes):
         assert late_done < batch_done, (late_done - t0, batch_done - t0)
     else:
         assert late_done >= batch_done - 0.01, (late_done - t0, batch_done - t0)
-    print("lanes", lanes, "late request done at", late_done - t0, "batch done at", batch_done - t0)
+    print("lanes", lanes, "warm", warm, "late request done at", late_done - t0, "batch done at", batch_done - t0)
