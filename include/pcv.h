@@ -387,7 +387,12 @@ void pcv_destroy(pcv_ctx* ctx);
  * waiting launches of short jobs are scheduled first.  CV results do not depend on
  * batching or lane (every subset task is computed on its own, lanes are identical,
  * the sums have a fixed order); predictions agree within the precision's tolerance
- * whether they come from kept weights or a fresh solve.
+ * whether they come from kept weights or a fresh solve.  Creation reserves every
+ * lane's work memory for batches of max_batch CV requests, budget permitting (a
+ * device allocation waits for the kernels already running, so a lane that allocated
+ * at its first batch would wait for the other lanes' launches); the size buckets
+ * are built then when the process already holds the autotuner's choice for the
+ * dataset, else at the lane's first CV batch.
  *
  * The server takes the contexts over: while it exists, no other thread may use
  * them (their clones' device copies of the data are the server's and are freed with

@@ -15,6 +15,9 @@
 //   * predictions use the kriging weights that CV evaluations of the same
 //     configuration kept (the lanes of a dataset share that cache), so a prediction at
 //     a recently evaluated configuration factors nothing;
+//   * every lane's work memory is reserved when the server is created, budget
+//     permitting (a device allocation waits for the kernels already running, so a
+//     lane allocating at its first batch would wait for the other lanes' launches);
 //   * a batch is admitted only when its lane's work memory fits the server's HBM
 //     budget; idle lanes' work memory is released, least recently used first, to make
 //     room, otherwise the worker waits for running batches to finish;
